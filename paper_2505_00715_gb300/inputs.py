@@ -1,0 +1,197 @@
+"""Seeded synthetic inputs shared by the library's tests, the bench and the oracle checks.
+
+This module holds input generation only (meshes, random right-hand sides and
+time-step sequences) and none of the method's arithmetic.  It imports neither
+the CUDA binding nor the oracle.
+
+Meshes are flat-triangle surfaces with counter-clockwise triangles seen from
+outside (outward normals), vertices as float64 [nv, 3], triangles int32 [nt, 3].
+"""
+import math
+
+import numpy as np
+
+__all__ = ["icosahedron", "octahedron", "icosphere", "housing", "random_weights", "graded_steps"]
+
+
+def octahedron(R=1.0):
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)
+    t = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4],
+                  [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]], dtype=np.int32)
+    return R * v, t
+
+
+def icosahedron(R=1.0):
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array([[-1, p, 0], [1, p, 0], [-1, -p, 0], [1, -p, 0],
+                  [0, -1, p], [0, 1, p], [0, -1, -p], [0, 1, -p],
+                  [p, 0, -1], [p, 0, 1], [-p, 0, -1], [-p, 0, 1]], dtype=np.float64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    t = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+                  [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+                  [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+                  [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int32)
+    return R * v, _orient_outward(R * v, t)
+
+
+def _orient_outward(v, t):
+    """Flip triangles whose normal points towards the origin (star-shaped surfaces)."""
+    a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    n = np.cross(b - a, c - a)
+    flip = np.einsum("ij,ij->i", n, (a + b + c) / 3.0) < 0
+    t = t.copy()
+    t[flip] = t[flip][:, [0, 2, 1]]
+    return t
+
+
+def icosphere(level, R=1.0):
+    """Icosahedron subdivided 4-to-1 `level` times (midpoints cached by the
+    sorted vertex pair) and projected to the sphere of radius R:
+    20 * 4**level triangles, 10 * 4**level + 2 vertices."""
+    v, t = icosahedron(1.0)
+    verts = [tuple(x) for x in v]
+    tris = [tuple(x) for x in t]
+    for _ in range(level):
+        cache = {}
+        new = []
+
+        def mid(i, j):
+            key = (i, j) if i < j else (j, i)
+            k = cache.get(key)
+            if k is None:
+                m = (np.asarray(verts[i]) + np.asarray(verts[j])) * 0.5
+                m /= np.linalg.norm(m)
+                verts.append(tuple(m))
+                k = len(verts) - 1
+                cache[key] = k
+            return k
+
+        for (a, b, c) in tris:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        tris = new
+    V = np.array(verts, dtype=np.float64) * R
+    T = np.array(tris, dtype=np.int32)
+    return V, _orient_outward(V, T)
+
+
+def _outline(radius, nfins, fin_h, fin_t, n_arc):
+    """Closed polygon of a circle of `radius` with `nfins` radial fins of
+    height fin_h and thickness fin_t (counter-clockwise, z = 0)."""
+    pts = []
+    half = math.asin(min(0.99, fin_t / (2.0 * radius)))
+    for f in range(nfins):
+        th0 = 2.0 * math.pi * f / nfins
+        th1 = 2.0 * math.pi * (f + 1) / nfins
+        # fin at th0: left flank, tip, right flank (counter-clockwise order)
+        a0 = th0 + half
+        # flank points at the fin root (angle th0 +/- half) and tip
+        pts.append(((radius + fin_h) * math.cos(th0) + fin_t / 2 * math.sin(th0),
+                    (radius + fin_h) * math.sin(th0) - fin_t / 2 * math.cos(th0)))
+        pts.append(((radius + fin_h) * math.cos(th0) - fin_t / 2 * math.sin(th0),
+                    (radius + fin_h) * math.sin(th0) + fin_t / 2 * math.cos(th0)))
+        # arc from this fin's left root to the next fin's right root
+        a1 = th1 - half
+        for k in range(n_arc + 1):
+            th = a0 + (a1 - a0) * k / n_arc
+            pts.append((radius * math.cos(th), radius * math.sin(th)))
+    return np.array(pts, dtype=np.float64)
+
+
+def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005, jitter=0.01, seed=0):
+    """Synthetic electric-machine housing: a closed finned cylinder along z.
+
+    The cross-section is a circle with `nfins` radial fins; it is extruded
+    over `length` and closed by flat end caps triangulated in rings.  The
+    resolution is chosen so that the triangle count is close to `n_target`.
+    Every vertex is moved by a seeded uniform random offset in a ball of
+    radius `jitter` times the mean edge length (flat end caps and fins stay
+    closed because only vertex positions move)."""
+    # choose arc resolution and axial layers for ~n_target triangles
+    best = None
+    for n_arc in range(2, 400):
+        out = _outline(radius, nfins, fin_h, fin_t, n_arc)
+        P = len(out)
+        perim = np.sum(np.linalg.norm(np.roll(out, -1, axis=0) - out, axis=1))
+        h = perim / P
+        nz = max(2, int(round(length / h)))
+        nrings = max(1, int(round(radius / h)))
+        ntri = 2 * P * nz + 2 * (2 * P * nrings)
+        if best is None or abs(ntri - n_target) < abs(best[0] - n_target):
+            best = (ntri, n_arc, nz, nrings)
+        if ntri > 1.3 * n_target:
+            break
+    _, n_arc, nz, nrings = best
+    out = _outline(radius, nfins, fin_h, fin_t, n_arc)
+    P = len(out)
+    verts = []
+    tris = []
+    # side wall: layers k = 0..nz
+    for k in range(nz + 1):
+        z = -length / 2 + length * k / nz
+        for p in range(P):
+            verts.append((out[p, 0], out[p, 1], z))
+    def vid(k, p):
+        return k * P + (p % P)
+    for k in range(nz):
+        for p in range(P):
+            a, b, c, d = vid(k, p), vid(k, p + 1), vid(k + 1, p + 1), vid(k + 1, p)
+            tris.append((a, b, c))
+            tris.append((a, c, d))
+    # end caps: rings shrinking the outline to the axis; ring 0 = boundary layer
+    for cap, k in ((0, 0), (1, nz)):
+        z = -length / 2 + length * k / nz
+        ring_ids = [[vid(k, p) for p in range(P)]]
+        for r in range(1, nrings):
+            s = 1.0 - r / nrings
+            ids = []
+            for p in range(P):
+                verts.append((out[p, 0] * s, out[p, 1] * s, z))
+                ids.append(len(verts) - 1)
+            ring_ids.append(ids)
+        verts.append((0.0, 0.0, z))
+        centre = len(verts) - 1
+        for r in range(nrings):
+            outer = ring_ids[r]
+            if r + 1 < nrings:
+                inner = ring_ids[r + 1]
+                for p in range(P):
+                    a, b = outer[p], outer[(p + 1) % P]
+                    c, d = inner[(p + 1) % P], inner[p]
+                    if cap == 1:
+                        tris.append((a, b, c))
+                        tris.append((a, c, d))
+                    else:
+                        tris.append((a, c, b))
+                        tris.append((a, d, c))
+            else:
+                for p in range(P):
+                    a, b = outer[p], outer[(p + 1) % P]
+                    if cap == 1:
+                        tris.append((a, b, centre))
+                    else:
+                        tris.append((a, centre, b))
+    V = np.array(verts, dtype=np.float64)
+    T = np.array(tris, dtype=np.int32)
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        e = np.concatenate([T[:, [0, 1]], T[:, [1, 2]], T[:, [2, 0]]])
+        h = np.mean(np.linalg.norm(V[e[:, 0]] - V[e[:, 1]], axis=1))
+        d = rng.normal(size=V.shape)
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        rad = jitter * h * rng.random(len(V)) ** (1.0 / 3.0)
+        V = V + d * rad[:, None]
+    return V, T
+
+
+def random_weights(nf, n, nrhs, seed=1, dtype=np.complex128):
+    """Seeded complex Gaussian weights W[nf, n, nrhs] (unit variance per component)."""
+    rng = np.random.default_rng(seed)
+    W = rng.standard_normal((nf, n, nrhs)) + 1j * rng.standard_normal((nf, n, nrhs))
+    return W.astype(dtype)
+
+
+def graded_steps(N, ratio, T):
+    """N geometrically graded time steps dt_i = dt_1 ratio^(i-1) summing to T."""
+    dt1 = T * (ratio - 1.0) / (ratio ** N - 1.0) if ratio != 1.0 else T / N
+    return dt1 * ratio ** np.arange(N)
