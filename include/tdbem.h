@@ -1,0 +1,201 @@
+/*
+ * tdbem — GB300 (sm_103a) library for the Laplace-domain operator tensor of a
+ * time-domain Galerkin boundary element method, compressed by 3D-ACA over the
+ * convolution-quadrature frequencies, and its multi-frequency apply.
+ *
+ * Method: M. Schanz, V. Lakshmi Keshava, H. De Gersem, "Comparison of
+ * H-matrix- and FMM-based 3D-ACA for a time-domain boundary element method",
+ * arXiv 2505.00715.  Section numbers below refer to that paper.
+ *
+ * Conventions for every call
+ *   - Return value: TDBEM_OK (0) or a negative TDBEM_ERR_* code; the message
+ *     of the last failure of a context is returned by tdbem_last_error().
+ *     No call aborts, traps or exits the process.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership.  Handles are owned by the library and released by the
+ *     matching *_destroy call (NULL is accepted and ignored).
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device, owned by the caller; work on them is ordered on the context's
+ *     stream and is asynchronous unless the call says otherwise.  Calls that
+ *     return host data (tdbem_freqs_get, tdbem_tree_export,
+ *     tdbem_tensor_stats) synchronise the stream.
+ *   - Complex arrays are interleaved (re, im): complex64 = 2 x float,
+ *     complex128 = 2 x double.
+ *   - Triangles are vertex-index triples ordered counter-clockwise seen from
+ *     outside, so (v1 - v0) x (v2 - v0) is the outward normal n of Sec. 2.
+ *   - Indices are 0-based; DOF numbering is the caller's (P0: triangle index,
+ *     P1: vertex index); the cluster-tree permutation stays internal.
+ */
+#ifndef TDBEM_H
+#define TDBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define TDBEM_OK 0
+#define TDBEM_ERR_ARG (-1)            /* bad argument, degenerate mesh, NaN, ... */
+#define TDBEM_ERR_OOM (-2)            /* device or host allocation failed */
+#define TDBEM_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define TDBEM_ERR_NOT_CONVERGED (-4)  /* ACA / 3D-ACA hit its rank cap */
+#define TDBEM_ERR_CAPACITY (-5)       /* a device pool overflowed (retried internally) */
+
+/* ---- enumerations ------------------------------------------------------- */
+enum { TDBEM_SLP = 0, TDBEM_DLP = 1 };        /* single layer V, double layer K (Sec. 2) */
+enum { TDBEM_P0 = 0, TDBEM_P1 = 1 };          /* piecewise constant / linear (Sec. 3) */
+enum { TDBEM_FP64 = 0, TDBEM_MIXED = 1 };     /* precision forms, see tdbem_op */
+enum { TDBEM_EULER = 0, TDBEM_RADAU2 = 1 };   /* Runge-Kutta method of the gCQ (App. A) */
+
+typedef struct tdbem_ctx *tdbem_ctx_t;
+typedef struct tdbem_mesh *tdbem_mesh_t;
+typedef struct tdbem_freqs *tdbem_freqs_t;
+typedef struct tdbem_tree *tdbem_tree_t;
+typedef struct tdbem_tensor *tdbem_tensor_t;
+
+/* Operator and discretisation (Sec. 2 eqs. slp/dlp, Sec. 3):
+ *   op = TDBEM_SLP: A[i,j](s) = int_{tau_i} int_{tau_j} exp(-s r/c)/(4 pi r),
+ *        test P0 x trial P0 (Galerkin single layer);
+ *   op = TDBEM_DLP: A[i,v](s) = int_{tau_i} int_Gamma phi_v(y) d/dn_y
+ *        [exp(-s r/c)/(4 pi r)], test P0 x trial P1 (Galerkin double layer).
+ * Regular pairs use the 7-point degree-5 triangle rule in x and y (49
+ * points); pairs of triangles that share a vertex, an edge or coincide use
+ * the Sauter-Schwab regularising transforms with an ng-point Gauss-Legendre
+ * rule in every transformed variable (Sec. 3, Erichsen-Sauter formulas).
+ *   prec = TDBEM_FP64: every step in FP64 (entries complex128);
+ *   prec = TDBEM_MIXED: regular entries and ACA cross updates in FP32,
+ *        touching pairs and the 3D-ACA stopping norms in FP64, complex64
+ *        storage. */
+typedef struct {
+    int32_t op;
+    int32_t prec;
+    double c;   /* wave speed (> 0) */
+    int32_t ng; /* Gauss points per transformed variable, 1..16 (default 5) */
+    int32_t reserved;
+} tdbem_op;
+
+/* 3D-ACA parameters (Sec. 4, Algorithm 1). */
+typedef struct {
+    double eps;      /* tolerance of Algorithm 1 on each block (e.g. 1e-4) */
+    double eps_aca;  /* tolerance of the ACA of every far-field face (e.g. 1e-6) */
+    int32_t max_face_rank; /* cap of the face ACA rank (<= 0: 64) */
+    int32_t flags;         /* reserved, 0 */
+} tdbem_aca_cfg;
+
+typedef struct {
+    int64_t nblocks, nnear, nfar;
+    int64_t sum_rank, max_rank;     /* terms r_b of Algorithm 1 per block */
+    int64_t sum_face_rank;          /* ACA ranks of the far faces, summed */
+    int64_t stored_complex;         /* complex numbers stored (faces + fibres) */
+    int64_t dense_complex;          /* rows * cols * unique frequencies */
+    int64_t entries_regular;        /* regular entries evaluated */
+    int64_t entries_tube;           /* fibre (all-frequency) entries evaluated */
+    int64_t pairs_singular;         /* touching pairs integrated (per frequency) */
+    double ms_plan, ms_singular, ms_near, ms_far, ms_total;
+} tdbem_stats;
+
+/* ---- context -------------------------------------------------------------- */
+/* Bind device `device` and stream `cuda_stream` (a cudaStream_t, NULL = the
+ * legacy default stream). */
+int tdbem_ctx_create(int device, void *cuda_stream, tdbem_ctx_t *out);
+int tdbem_ctx_destroy(tdbem_ctx_t ctx);
+const char *tdbem_last_error(tdbem_ctx_t ctx);
+/* Block until all work of the context's stream has finished. */
+int tdbem_ctx_sync(tdbem_ctx_t ctx);
+
+/* ---- mesh (Sec. 3 eq. geomapprox, spaces X_D = P1, X_N = P0) -------------- */
+/* verts: host [nv][3] FP64; tris: host [nt][3] int32.  Builds the element
+ * tables (quadrature points, weights, normals, FP32 and FP64) in device
+ * memory.  ERR_ARG on an out-of-range index, a degenerate triangle or a
+ * non-finite coordinate. */
+int tdbem_mesh_create(tdbem_ctx_t ctx, const double *verts, int64_t nv, const int32_t *tris,
+                      int64_t nt, tdbem_mesh_t *out);
+int tdbem_mesh_destroy(tdbem_mesh_t mesh);
+int64_t tdbem_mesh_ndof(tdbem_mesh_t mesh, int32_t basis);
+
+/* ---- frequency sets --------------------------------------------------------- */
+/* BDF2 convolution quadrature: s_k = delta(lambda e^{2 pi i k/N})/dt,
+ * delta(z) = (1-z) + (1-z)^2/2, k = 0..N-1; lambda <= 0 selects
+ * (1e-8)^(1/(2N)).  Computed in FP64 on the device. */
+int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double lambda, tdbem_freqs_t *out);
+/* gCQ contour of App. A: s_l = gamma(sigma_l), weights w_l (positively
+ * oriented Cauchy quadrature), l = 1..NQ, for steps in [dt_min, dt_max] and
+ * the RK method rk.  Computed in FP64 on the device (Jacobi elliptic
+ * functions by the AGM).  q = 1 is lifted to 1.01 (App. A, last paragraph). */
+int tdbem_freqs_gcq(tdbem_ctx_t ctx, double dt_min, double dt_max, int32_t rk, int32_t NQ,
+                    tdbem_freqs_t *out);
+/* Copies the NQ points (and weights, nullable; BDF2 sets have none and
+ * return zeros) to host arrays [2*NQ]; *NQ and *Nu (number of frequencies up
+ * to conjugation, App. A last paragraph) are returned when non-NULL.
+ * unique (nullable, host int32 [NQ]) receives for each point the index of its
+ * representative among the Nu unique points and the sign +1 (same) or -1
+ * (conjugate) as  rep + 1 (same) or -(rep + 1) (conjugate). */
+int tdbem_freqs_get(tdbem_freqs_t f, double *s, double *w, int32_t *NQ, int32_t *Nu,
+                    int32_t *unique);
+int tdbem_freqs_destroy(tdbem_freqs_t f);
+
+/* ---- cluster tree and block cluster tree (Sec. 4, eq. admissible) ---------- */
+/* PCA bisection of the DOF points (P0 centroids, P1 vertices) until a
+ * cluster has at most `leaf` DOFs; blocks are far field when
+ * min(diam) <= eta dist with dist > 0 (boxes of the DOF supports), near
+ * field when either cluster is a leaf, else split into the four son pairs.
+ * Built on the host in IEEE FP64 with a fixed operation order, so it is
+ * reproducible bit for bit. */
+int tdbem_tree_build(tdbem_mesh_t mesh, int32_t row_basis, int32_t col_basis, int32_t leaf,
+                     double eta, tdbem_tree_t *out);
+/* perm_rows/perm_cols (nullable, host int32 [ndof]): DOF at permuted
+ * position k.  *nblocks (nullable) receives the block count; blocks
+ * (nullable, host int32 [nblocks][5]) = {i0, i1, j0, j1, far} as half-open
+ * permuted ranges in depth-first order. */
+int tdbem_tree_export(tdbem_tree_t tree, int32_t *perm_rows, int32_t *perm_cols, int64_t *nblocks,
+                      int32_t *blocks);
+int tdbem_tree_destroy(tdbem_tree_t tree);
+
+/* ---- entries (Sec. 3; the ENTRY function of Algorithm 1) -------------------- */
+/* out[f][r][c] = A[rows[r], cols[c]](s_{fidx[f]}) for every combination.
+ * rows, cols, fidx: device int32 arrays; out: device complex array
+ * (complex128 for prec FP64, complex64 for MIXED), layout [nf][nr][nc].
+ * Touching pairs go through the FP64 Sauter-Schwab path in both precisions. */
+int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const int32_t *rows,
+                  int64_t nr, const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf,
+                  void *out);
+
+/* ---- compression (Sec. 4, Algorithm 1 per block, eq. norm) ------------------- */
+/* 3D-ACA of the operator tensor over the Nu unique frequencies of f on every
+ * block of `tree` (which must have been built with test P0 and trial P0 for
+ * SLP, P1 for DLP).  Near-field blocks: dense residual faces; far-field
+ * blocks: residual faces compressed by ACA with partial pivoting to eps_aca,
+ * rebuilt to find the pivot (Sec. 4).  The result stays in device memory. */
+int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f,
+                   tdbem_tree_t tree, const tdbem_aca_cfg *cfg, tdbem_tensor_t *out);
+int tdbem_tensor_stats(tdbem_tensor_t t, tdbem_stats *st);
+/* Rebuilt entries C^r[rows[n], cols[n], fidx[n]] (fidx into the full NQ list,
+ * conjugates mirrored) for n < count.  Device int32 inputs, device complex
+ * output [count] in the tensor's precision. */
+int tdbem_tensor_entries(tdbem_tensor_t t, const int32_t *rows, const int32_t *cols,
+                         const int32_t *fidx, int64_t count, void *out);
+/* Per-block results (host, nullable): ranks [nblocks], face rank sums
+ * [nblocks], selected frequencies [nblocks][Nu+1] (-1 padded). */
+int tdbem_tensor_blocks(tdbem_tensor_t t, int32_t *rank, int32_t *face_rank_sum, int32_t *kpiv);
+int tdbem_tensor_destroy(tdbem_tensor_t t);
+
+/* ---- apply (eq. product) ------------------------------------------------------ */
+/* y[M][nrhs] = sum_{l < NQ} A(s_l) W_l  with W: device [NQ][ncols][nrhs]
+ * complex over all NQ points of the frequency set (conjugate partners are
+ * folded in through A(conj s) = conj A(s)); y: device [nrows][nrhs], same
+ * complex type as the tensor.  Evaluated as sum_d H_d (sum_l f_d[l] W_l). */
+int tdbem_apply_weighted(tdbem_tensor_t t, const void *W, int32_t nrhs, void *y);
+/* y = A(s_fidx) x for one point of the full list: x device [ncols][nrhs]. */
+int tdbem_apply_freq(tdbem_tensor_t t, int32_t fidx, const void *x, int32_t nrhs, void *y);
+/* Same as tdbem_apply_weighted with host W and y (pinned or pageable): the
+ * host->device copy of W and the device->host copy of y are part of the
+ * call, which returns when y is on the host. */
+int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, int32_t nrhs, void *y_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

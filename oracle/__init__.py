@@ -54,7 +54,7 @@ def lib():
             "orc_aca_dense": (i32, [vp, i32, i32, d, i32, vp, vp]),
             "orc_aca3d_dense": (i32, [vp, i32, i32, i32, d, i32, vp, vp, vp]),
             "orc_aca3d_dense_acaface": (i32, [vp, i32, i32, i32, d, d, i32, vp, vp, vp, vp]),
-            "orc_compress": (vp, [vp, i32, d, i32, vp, i32, vp, d, d, i32]),
+            "orc_compress": (vp, [vp, i32, d, i32, vp, i32, vp, d, d, i32, i32]),
             "orc_tensor_free": (None, [vp]),
             "orc_tensor_stats": (None, [vp, vp]),
             "orc_tensor_block_ranks": (None, [vp, vp, vp]),
@@ -243,11 +243,11 @@ def aca3d_dense(t, eps, eps_aca=None):
 class Tensor:
     """Block-compressed operator tensor from the oracle's 3D-ACA."""
 
-    def __init__(self, mesh, op, s, tree, eps, eps_aca, c=1.0, ng=6, nthreads=0):
+    def __init__(self, mesh, op, s, tree, eps, eps_aca, c=1.0, ng=6, nthreads=0, block_stride=1):
         self.s = _c128(s)
         self.mesh, self.tree = mesh, tree
         self.h = lib().orc_compress(mesh.h, op, c, ng, _p(self.s), len(self.s), tree.h, eps, eps_aca,
-                                    nthreads)
+                                    nthreads, block_stride)
         st = np.zeros(8)
         lib().orc_tensor_stats(self.h, _p(st))
         self.stats = dict(nblocks=int(st[0]), nfar=int(st[1]), sum_rank=int(st[2]), max_rank=int(st[3]),

@@ -58,6 +58,8 @@ int orc_gauss01(int n, double *x, double *w);
  * Touching pairs (identical / common edge / common vertex) use the
  * regularising coordinate transforms of Sauter and Schwab with an ng-point
  * Gauss-Legendre rule in every transformed variable; other pairs the 7x7 rule.
+ * SLP pairs are integrated in the order (lower index, higher index), so the
+ * single-layer matrix is symmetric exactly.
  * Returns the pair class: 0 regular, 1 vertex, 2 edge, 3 identical. */
 int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, double s_im,
              double c, int ng, double *out_re_im /*[2*3]*/);
@@ -120,10 +122,13 @@ int orc_aca3d_dense(const double *t, int nI, int nJ, int nK, double eps, int rma
 int orc_aca3d_dense_acaface(const double *t, int nI, int nJ, int nK, double eps, double eps_aca,
                             int rmax, int32_t *kpiv, double *H, double *f, int32_t *face_rank);
 
-/* Compressed operator tensor of a BEM operator over a frequency list. */
+/* Compressed operator tensor of a BEM operator over a frequency list.
+ * block_stride > 1 compresses only every block_stride-th block (a bounded
+ * sample for timing; the others are left empty). */
 typedef struct orc_tensor orc_tensor;
 orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const double *s, int nf,
-                         const orc_tree *t, double eps, double eps_aca, int nthreads);
+                         const orc_tree *t, double eps, double eps_aca, int nthreads,
+                         int block_stride);
 void orc_tensor_free(orc_tensor *x);
 /* stats[8]: nblocks, nfar, sum ranks, max rank, stored complex entries,
  * dense complex entries (nrows*ncols*nf), entries evaluated, sum face ranks */

@@ -373,7 +373,8 @@ struct orc_tensor {
 };
 
 orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const double *s, int nf,
-                         const orc_tree *t, double eps, double eps_aca, int nthreads) {
+                         const orc_tree *t, double eps, double eps_aca, int nthreads,
+                         int block_stride) {
     orc_tensor *x = calloc(1, sizeof *x);
     x->nrows = orc_mesh_ndof(m, ORC_P0);
     x->ncols = orc_mesh_ndof(m, op == ORC_DLP ? ORC_P1 : ORC_P0);
@@ -402,6 +403,10 @@ orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const doub
         B->j0 = bl[5 * b + 2];
         B->j1 = bl[5 * b + 3];
         B->far = bl[5 * b + 4];
+        if (block_stride > 1 && b % block_stride != 0) {
+            B->r = 0;
+            continue;
+        }
         src3 S = {0};
         S.nI = B->i1 - B->i0;
         S.nJ = B->j1 - B->j0;

@@ -426,6 +426,13 @@ void orc_pair_regular(const orc_mesh *m, int op, int64_t ti, int64_t tj, double 
 int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, double s_im,
              double c, int ng, double *o) {
     cplx sc = (s_re + I * s_im) / c;
+    /* the Galerkin single layer is symmetric: integrate each unordered pair
+     * once, in the order (lower index, higher index) */
+    if (op == ORC_SLP && ti > tj) {
+        int64_t t = ti;
+        ti = tj;
+        tj = t;
+    }
     cplx out[3] = {0, 0, 0};
     param_tri pa, pb;
     int cls = classify(m, ti, tj, &pa, &pb);

@@ -1,0 +1,238 @@
+"""tdbem: GB300 library for the 3D-ACA-compressed operator tensor of a
+time-domain Galerkin BEM over convolution-quadrature frequencies, and its
+multi-frequency apply.
+
+Method: Schanz, Lakshmi Keshava, De Gersem, "Comparison of H-matrix- and
+FMM-based 3D-ACA for a time-domain boundary element method" (arXiv 2505.00715).
+
+This package is a thin layer over the C-ABI of libtdbem.so (include/tdbem.h);
+PyTorch is used only for device buffers.  All numerical work runs in the CUDA
+library; the calls raise if the library or a CUDA device is unavailable.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
+
+__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "entries", "compress", "SLP", "DLP", "P0", "P1",
+           "FP64", "MIXED", "EULER", "RADAU2", "TdbemError"]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise TdbemError("tdbem needs a CUDA device; none is available")
+    return torch
+
+
+def _ptr(t):
+    if not t.is_contiguous():
+        raise TdbemError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Context:
+    """One CUDA device and stream (the torch current stream by default)."""
+
+    def __init__(self, device=0, stream=None):
+        torch = _torch()
+        self.L = _lib.load()
+        self.device = device
+        torch.cuda.set_device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        rc = self.L.tdbem_ctx_create(device, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise TdbemError("tdbem_ctx_create failed with status %d" % rc)
+        self.h = h
+
+    def check(self, rc, what):
+        _lib.check(rc, self.h, what)
+
+    def sync(self):
+        self.check(self.L.tdbem_ctx_sync(self.h), "tdbem_ctx_sync")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_ctx_destroy(self.h)
+            self.h = None
+
+
+class Mesh:
+    def __init__(self, ctx, verts, tris):
+        self.ctx = ctx
+        self.verts = np.ascontiguousarray(verts, dtype=np.float64)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_mesh_create(ctx.h, _np_ptr(self.verts), len(self.verts), _np_ptr(self.tris),
+                                          len(self.tris), C.byref(h)), "tdbem_mesh_create")
+        self.h = h
+
+    def ndof(self, basis):
+        return int(self.ctx.L.tdbem_mesh_ndof(self.h, basis))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_mesh_destroy(self.h)
+            self.h = None
+
+
+class Freqs:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+        NQ, Nu = C.c_int32(), C.c_int32()
+        ctx.check(ctx.L.tdbem_freqs_get(h, None, None, C.byref(NQ), C.byref(Nu), None), "tdbem_freqs_get")
+        self.NQ, self.Nu = NQ.value, Nu.value
+        s = np.zeros(2 * self.NQ)
+        w = np.zeros(2 * self.NQ)
+        u = np.zeros(self.NQ, dtype=np.int32)
+        ctx.check(ctx.L.tdbem_freqs_get(h, _np_ptr(s), _np_ptr(w), None, None, _np_ptr(u)), "tdbem_freqs_get")
+        self.s = s.view(np.complex128)
+        self.w = w.view(np.complex128)
+        self.unique_map = u
+        # representative point of each unique frequency (u[k] = rep + 1 there)
+        self.unique = np.array([k for k in range(self.NQ) if u[k] > 0], dtype=np.int32)
+
+    @classmethod
+    def bdf2(cls, ctx, N, dt, lam=0.0):
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_freqs_cq_bdf2(ctx.h, N, dt, lam, C.byref(h)), "tdbem_freqs_cq_bdf2")
+        return cls(ctx, h)
+
+    @classmethod
+    def gcq(cls, ctx, dt_min, dt_max, rk, NQ):
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_freqs_gcq(ctx.h, dt_min, dt_max, rk, NQ, C.byref(h)), "tdbem_freqs_gcq")
+        return cls(ctx, h)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_freqs_destroy(self.h)
+            self.h = None
+
+
+class Tree:
+    def __init__(self, mesh, row_basis, col_basis, leaf, eta):
+        self.mesh = mesh
+        ctx = mesh.ctx
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_tree_build(mesh.h, row_basis, col_basis, leaf, eta, C.byref(h)), "tdbem_tree_build")
+        self.h = h
+        nb = C.c_int64()
+        ctx.check(ctx.L.tdbem_tree_export(h, None, None, C.byref(nb), None), "tdbem_tree_export")
+        self.perm_rows = np.zeros(mesh.ndof(row_basis), dtype=np.int32)
+        self.perm_cols = np.zeros(mesh.ndof(col_basis), dtype=np.int32)
+        self.blocks = np.zeros((nb.value, 5), dtype=np.int32)
+        ctx.check(ctx.L.tdbem_tree_export(h, _np_ptr(self.perm_rows), _np_ptr(self.perm_cols), None,
+                                          _np_ptr(self.blocks)), "tdbem_tree_export")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_tree_destroy(self.h)
+            self.h = None
+
+
+def _op(op, prec, c, ng):
+    return _lib.Op(op, prec, c, ng, 0)
+
+
+def _cdtype(prec):
+    torch = _torch()
+    return torch.complex128 if prec == FP64 else torch.complex64
+
+
+def entries(mesh, op, freqs, rows, cols, fidx, prec=MIXED, c=1.0, ng=5):
+    """A[rows, cols](s_fidx) as a device tensor [nf, nr, nc] (complex64 MIXED, complex128 FP64)."""
+    torch = _torch()
+    ctx = mesh.ctx
+    dev = torch.device("cuda", ctx.device)
+    r = torch.as_tensor(np.asarray(rows, dtype=np.int32), device=dev)
+    q = torch.as_tensor(np.asarray(cols, dtype=np.int32), device=dev)
+    f = torch.as_tensor(np.asarray(fidx, dtype=np.int32), device=dev)
+    out = torch.empty((len(f), len(r), len(q)), dtype=_cdtype(prec), device=dev)
+    o = _op(op, prec, c, ng)
+    ctx.check(ctx.L.tdbem_entries(mesh.h, C.byref(o), freqs.h, _ptr(r), len(r), _ptr(q), len(q), _ptr(f), len(f),
+                                  _ptr(out)), "tdbem_entries")
+    return out
+
+
+class Tensor:
+    """3D-ACA compressed operator tensor held in device memory."""
+
+    def __init__(self, ctx, h, mesh, freqs, tree, op, prec):
+        self.ctx, self.h, self.mesh, self.freqs, self.tree = ctx, h, mesh, freqs, tree
+        self.op, self.prec = op, prec
+        self.nrows = mesh.ndof(P0)
+        self.ncols = mesh.ndof(P1 if op == DLP else P0)
+
+    def stats(self):
+        st = _lib.Stats()
+        self.ctx.check(self.ctx.L.tdbem_tensor_stats(self.h, C.byref(st)), "tdbem_tensor_stats")
+        return st.as_dict()
+
+    def blocks(self):
+        nb = len(self.tree.blocks)
+        r = np.zeros(nb, dtype=np.int32)
+        k = np.zeros(nb, dtype=np.int32)
+        kp = np.zeros((nb, self.freqs.Nu + 1), dtype=np.int32)
+        self.ctx.check(self.ctx.L.tdbem_tensor_blocks(self.h, _np_ptr(r), _np_ptr(k), _np_ptr(kp)),
+                       "tdbem_tensor_blocks")
+        return r, k, kp
+
+    def entries(self, rows, cols, fidx):
+        torch = _torch()
+        dev = torch.device("cuda", self.ctx.device)
+        r = torch.as_tensor(np.asarray(rows, dtype=np.int32), device=dev)
+        q = torch.as_tensor(np.asarray(cols, dtype=np.int32), device=dev)
+        f = torch.as_tensor(np.asarray(fidx, dtype=np.int32), device=dev)
+        out = torch.empty(len(r), dtype=_cdtype(self.prec), device=dev)
+        self.ctx.check(self.ctx.L.tdbem_tensor_entries(self.h, _ptr(r), _ptr(q), _ptr(f), len(r), _ptr(out)),
+                       "tdbem_tensor_entries")
+        return out
+
+    def apply_weighted(self, W, y=None):
+        """y = sum_l A(s_l) W[l]; W: device tensor [NQ, ncols, nrhs] of the tensor's complex dtype."""
+        torch = _torch()
+        nrhs = W.shape[2]
+        if y is None:
+            y = torch.empty((self.nrows, nrhs), dtype=W.dtype, device=W.device)
+        self.ctx.check(self.ctx.L.tdbem_apply_weighted(self.h, _ptr(W), nrhs, _ptr(y)), "tdbem_apply_weighted")
+        return y
+
+    def apply_freq(self, fidx, x, y=None):
+        torch = _torch()
+        nrhs = x.shape[1]
+        if y is None:
+            y = torch.empty((self.nrows, nrhs), dtype=x.dtype, device=x.device)
+        self.ctx.check(self.ctx.L.tdbem_apply_freq(self.h, fidx, _ptr(x), nrhs, _ptr(y)), "tdbem_apply_freq")
+        return y
+
+    def apply_weighted_host(self, W_host, y_host):
+        """Host buffers (numpy or pinned torch CPU tensors); copies are part of the call."""
+        wp = C.c_void_p(W_host.data_ptr()) if hasattr(W_host, "data_ptr") else _np_ptr(W_host)
+        yp = C.c_void_p(y_host.data_ptr()) if hasattr(y_host, "data_ptr") else _np_ptr(y_host)
+        nrhs = W_host.shape[2]
+        self.ctx.check(self.ctx.L.tdbem_apply_weighted_host(self.h, wp, nrhs, yp), "tdbem_apply_weighted_host")
+        return y_host
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_tensor_destroy(self.h)
+            self.h = None
+
+
+def compress(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64,
+             use_graph=True):
+    ctx = mesh.ctx
+    o = _op(op, prec, c, ng)
+    cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, 0 if use_graph else 1)
+    h = C.c_void_p()
+    ctx.check(ctx.L.tdbem_compress(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), C.byref(h)),
+              "tdbem_compress")
+    return Tensor(ctx, h, mesh, freqs, tree, op, prec)

@@ -1,0 +1,875 @@
+// C-ABI of the tdbem library (include/tdbem.h): handles, argument checks,
+// device tables, and the orchestration of the compression phases
+// (touching-pair table -> near-field entries -> near 3D-ACA -> far 3D-ACA),
+// each a single persistent launch, captured together in a CUDA graph.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "kernels.h"
+#include "pair.cuh"
+
+int td_fail(tdbem_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[1024];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <class T>
+int dalloc(tdbem_ctx *ctx, T **p, size_t count, std::vector<void *> *owned = nullptr) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return td_fail(ctx, TDBEM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", sizeof(T) * count,
+                       cudaGetErrorString(e));
+    }
+    if (owned) owned->push_back((void *)*p);
+    return TDBEM_OK;
+}
+
+template <class T>
+int upload(tdbem_ctx *ctx, T *dst, const T *src, size_t count) {
+    if (count == 0) return TDBEM_OK;
+    TD_CUDA(ctx, cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, ctx->stream));
+    return TDBEM_OK;
+}
+
+struct Guard {
+    // frees transient device buffers at scope exit
+    std::vector<void *> p;
+    ~Guard() {
+        for (void *q : p) cudaFree(q);
+    }
+};
+
+MeshDev mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw,
+                 const int *tp_slot) {
+    MeshDev d{};
+    d.nt = (int)m->nt;
+    d.nv = (int)m->nv;
+    d.qxh = m->qxh;
+    d.qyh = m->qyh;
+    d.qzh = m->qzh;
+    d.qxl = m->qxl;
+    d.qyl = m->qyl;
+    d.qzl = m->qzl;
+    d.qw32 = m->qw32;
+    d.n32 = m->n32;
+    d.qx = m->qx;
+    d.qy = m->qy;
+    d.qz = m->qz;
+    d.qw = m->qw;
+    d.n64 = m->n64;
+    d.verts = m->dverts;
+    d.tris = m->dtris;
+    d.area = m->darea;
+    d.v2t_ptr = m->dv2t_ptr;
+    d.v2t = m->dv2t;
+    d.v2t_loc = (const signed char *)m->dv2t_loc;
+    d.tp_ptr = m->dtp_ptr;
+    d.tp_tri = m->dtp_tri;
+    d.tp_slot = tp_slot;
+    d.ng = ng;
+    d.gx = gx;
+    d.gw = gw;
+    return d;
+}
+
+int check_op(tdbem_ctx *ctx, const tdbem_op *op) {
+    if (!op) return td_fail(ctx, TDBEM_ERR_ARG, "op is NULL");
+    if (op->op != TDBEM_SLP && op->op != TDBEM_DLP) return td_fail(ctx, TDBEM_ERR_ARG, "unknown operator %d", op->op);
+    if (op->prec != TDBEM_FP64 && op->prec != TDBEM_MIXED) return td_fail(ctx, TDBEM_ERR_ARG, "unknown precision %d", op->prec);
+    if (!(op->c > 0.0) || !std::isfinite(op->c)) return td_fail(ctx, TDBEM_ERR_ARG, "wave speed must be > 0");
+    if (op->ng < 1 || op->ng > 16) return td_fail(ctx, TDBEM_ERR_ARG, "ng must be in 1..16");
+    return TDBEM_OK;
+}
+
+// Gauss nodes and touching-pair slots for one operator (device, owned by caller)
+int prepare_sing(tdbem_ctx *ctx, const tdbem_mesh *m, int op, int ng, std::vector<void *> &owned,
+                 double **gx, double **gw, int **tp_slot, int **pti, int **ptj, int *npairs) {
+    double hx[32], hw[32];
+    td_gauss01(ng, hx, hw);
+    int rc;
+    if ((rc = dalloc(ctx, gx, 64, &owned))) return rc;
+    *gw = *gx + 32;
+    if ((rc = upload(ctx, *gx, hx, ng)) || (rc = upload(ctx, *gw, hw, ng))) return rc;
+    const int64_t np = m->tp_tri.size();
+    std::vector<int32_t> slot(np, -1), ti, tj;
+    for (int64_t i = 0; i < m->nt; ++i)
+        for (int32_t p = m->tp_ptr[i]; p < m->tp_ptr[i + 1]; ++p) {
+            const int32_t j = m->tp_tri[p];
+            if (op == TDBEM_DLP || i <= j) {
+                slot[p] = (int32_t)ti.size();
+                ti.push_back((int32_t)i);
+                tj.push_back(j);
+            }
+        }
+    if (op == TDBEM_SLP)
+        for (int64_t i = 0; i < m->nt; ++i)
+            for (int32_t p = m->tp_ptr[i]; p < m->tp_ptr[i + 1]; ++p) {
+                const int32_t j = m->tp_tri[p];
+                if (i > j) {
+                    const int32_t *b = m->tp_tri.data() + m->tp_ptr[j], *e = m->tp_tri.data() + m->tp_ptr[j + 1];
+                    const int32_t *f = std::lower_bound(b, e, (int32_t)i);
+                    slot[p] = slot[f - m->tp_tri.data()];
+                }
+            }
+    *npairs = (int)ti.size();
+    if ((rc = dalloc(ctx, tp_slot, np, &owned)) || (rc = dalloc(ctx, pti, ti.size(), &owned)) ||
+        (rc = dalloc(ctx, ptj, tj.size(), &owned)))
+        return rc;
+    if ((rc = upload(ctx, *tp_slot, slot.data(), np)) || (rc = upload(ctx, *pti, ti.data(), ti.size())) ||
+        (rc = upload(ctx, *ptj, tj.data(), tj.size())))
+        return rc;
+    return TDBEM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// context
+// ============================================================================
+extern "C" int tdbem_ctx_create(int device, void *stream, tdbem_ctx_t *out) {
+    if (!out) return TDBEM_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return TDBEM_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return TDBEM_ERR_CUDA;
+    tdbem_ctx *c = new (std::nothrow) tdbem_ctx();
+    if (!c) return TDBEM_ERR_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_ctx_destroy(tdbem_ctx_t ctx) {
+    delete ctx;
+    return TDBEM_OK;
+}
+
+extern "C" const char *tdbem_last_error(tdbem_ctx_t ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+extern "C" int tdbem_ctx_sync(tdbem_ctx_t ctx) {
+    if (!ctx) return TDBEM_ERR_ARG;
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// mesh
+// ============================================================================
+extern "C" int tdbem_mesh_create(tdbem_ctx_t ctx, const double *verts, int64_t nv, const int32_t *tris,
+                                 int64_t nt, tdbem_mesh_t *out) {
+    if (!ctx || !out || !verts || !tris || nv < 3 || nt < 1 || nt > (1 << 30) || nv > (1 << 30))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_mesh_create: bad arguments");
+    *out = nullptr;
+    for (int64_t k = 0; k < 3 * nv; ++k)
+        if (!std::isfinite(verts[k])) return td_fail(ctx, TDBEM_ERR_ARG, "non-finite vertex coordinate at %lld", (long long)k);
+    for (int64_t k = 0; k < 3 * nt; ++k)
+        if (tris[k] < 0 || tris[k] >= nv) return td_fail(ctx, TDBEM_ERR_ARG, "triangle index out of range at %lld", (long long)k);
+    tdbem_mesh *m = new (std::nothrow) tdbem_mesh();
+    if (!m) return td_fail(ctx, TDBEM_ERR_OOM, "host allocation failed");
+    m->ctx = ctx;
+    m->nv = nv;
+    m->nt = nt;
+    m->verts.assign(verts, verts + 3 * nv);
+    m->tris.assign(tris, tris + 3 * nt);
+    m->area.resize(nt);
+    std::vector<double> nrm(3 * nt);
+    for (int64_t e = 0; e < nt; ++e) {
+        const double *a = verts + 3 * tris[3 * e], *b = verts + 3 * tris[3 * e + 1], *c = verts + 3 * tris[3 * e + 2];
+        const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const double n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0.0)) {
+            delete m;
+            return td_fail(ctx, TDBEM_ERR_ARG, "degenerate triangle %lld", (long long)e);
+        }
+        m->area[e] = 0.5 * len;
+        for (int k = 0; k < 3; ++k) nrm[k * nt + e] = n[k] / len;
+    }
+    td_mesh_adjacency(m);
+    // 7-point tables [7][nt]
+    double bary[7][3], w7[7];
+    td_rule7(bary, w7);
+    std::vector<double> q(3 * 7 * nt), qw(7 * nt);
+    std::vector<float> qh(3 * 7 * nt), ql(3 * 7 * nt), qw32(7 * nt), n32(3 * nt);
+    for (int64_t e = 0; e < nt; ++e)
+        for (int p = 0; p < 7; ++p) {
+            for (int c = 0; c < 3; ++c) {
+                double x = 0.0;
+                for (int k = 0; k < 3; ++k) x += bary[p][k] * verts[3 * tris[3 * e + k] + c];
+                const int64_t o = ((int64_t)c * 7 + p) * nt + e;
+                q[o] = x;
+                qh[o] = (float)x;
+                ql[o] = (float)(x - (double)qh[o]);
+            }
+            qw[p * nt + e] = w7[p] * m->area[e];
+            qw32[p * nt + e] = (float)qw[p * nt + e];
+        }
+    for (int64_t k = 0; k < 3 * nt; ++k) n32[k] = (float)nrm[k];
+    // one device allocation for every table
+    const size_t n7 = 7 * (size_t)nt;
+    size_t bytes = sizeof(double) * (3 * n7 + n7 + 3 * nt + 3 * nv + nt) + sizeof(float) * (6 * n7 + n7 + 3 * nt) +
+                   sizeof(int32_t) * (3 * nt + (nv + 1) + 3 * nt + (nt + 1) + m->tp_tri.size()) + 3 * nt + 256;
+    char *base = nullptr;
+    if (cudaMalloc((void **)&base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return td_fail(ctx, TDBEM_ERR_OOM, "device allocation of %zu bytes for the mesh tables failed", bytes);
+    }
+    m->dev_block = base;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        char *p = base + off;
+        off += (b + 15) & ~(size_t)15;
+        return p;
+    };
+    m->qx = (double *)take(sizeof(double) * n7);
+    m->qy = (double *)take(sizeof(double) * n7);
+    m->qz = (double *)take(sizeof(double) * n7);
+    m->qw = (double *)take(sizeof(double) * n7);
+    m->n64 = (double *)take(sizeof(double) * 3 * nt);
+    m->dverts = (double *)take(sizeof(double) * 3 * nv);
+    m->darea = (double *)take(sizeof(double) * nt);
+    m->qxh = (float *)take(sizeof(float) * n7);
+    m->qyh = (float *)take(sizeof(float) * n7);
+    m->qzh = (float *)take(sizeof(float) * n7);
+    m->qxl = (float *)take(sizeof(float) * n7);
+    m->qyl = (float *)take(sizeof(float) * n7);
+    m->qzl = (float *)take(sizeof(float) * n7);
+    m->qw32 = (float *)take(sizeof(float) * n7);
+    m->n32 = (float *)take(sizeof(float) * 3 * nt);
+    m->dtris = (int32_t *)take(sizeof(int32_t) * 3 * nt);
+    m->dv2t_ptr = (int32_t *)take(sizeof(int32_t) * (nv + 1));
+    m->dv2t = (int32_t *)take(sizeof(int32_t) * 3 * nt);
+    m->dtp_ptr = (int32_t *)take(sizeof(int32_t) * (nt + 1));
+    m->dtp_tri = (int32_t *)take(sizeof(int32_t) * std::max<size_t>(1, m->tp_tri.size()));
+    m->dv2t_loc = (int8_t *)take(3 * nt);
+    int rc = TDBEM_OK;
+    if ((rc = upload(ctx, m->qx, q.data(), n7)) || (rc = upload(ctx, m->qy, q.data() + n7, n7)) ||
+        (rc = upload(ctx, m->qz, q.data() + 2 * n7, n7)) || (rc = upload(ctx, m->qw, qw.data(), n7)) ||
+        (rc = upload(ctx, m->n64, nrm.data(), 3 * nt)) || (rc = upload(ctx, m->dverts, verts, 3 * nv)) ||
+        (rc = upload(ctx, m->darea, m->area.data(), nt)) || (rc = upload(ctx, m->qxh, qh.data(), n7)) ||
+        (rc = upload(ctx, m->qyh, qh.data() + n7, n7)) || (rc = upload(ctx, m->qzh, qh.data() + 2 * n7, n7)) ||
+        (rc = upload(ctx, m->qxl, ql.data(), n7)) || (rc = upload(ctx, m->qyl, ql.data() + n7, n7)) ||
+        (rc = upload(ctx, m->qzl, ql.data() + 2 * n7, n7)) || (rc = upload(ctx, m->qw32, qw32.data(), n7)) ||
+        (rc = upload(ctx, m->n32, n32.data(), 3 * nt)) || (rc = upload(ctx, m->dtris, tris, 3 * nt)) ||
+        (rc = upload(ctx, m->dv2t_ptr, m->v2t_ptr.data(), nv + 1)) || (rc = upload(ctx, m->dv2t, m->v2t.data(), 3 * nt)) ||
+        (rc = upload(ctx, m->dtp_ptr, m->tp_ptr.data(), nt + 1)) ||
+        (rc = upload(ctx, m->dtp_tri, m->tp_tri.data(), m->tp_tri.size())) ||
+        (rc = upload(ctx, m->dv2t_loc, m->v2t_loc.data(), 3 * nt))) {
+        cudaFree(base);
+        delete m;
+        return rc;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaFree(base);
+        delete m;
+        return td_fail(ctx, TDBEM_ERR_CUDA, "mesh upload failed");
+    }
+    *out = m;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_mesh_destroy(tdbem_mesh_t m) {
+    if (!m) return TDBEM_OK;
+    cudaFree(m->dev_block);
+    delete m;
+    return TDBEM_OK;
+}
+
+extern "C" int64_t tdbem_mesh_ndof(tdbem_mesh_t m, int32_t basis) {
+    if (!m) return -1;
+    return basis == TDBEM_P1 ? m->nv : m->nt;
+}
+
+// ============================================================================
+// frequencies
+// ============================================================================
+namespace {
+int finish_freqs(tdbem_ctx *ctx, tdbem_freqs *f) {
+    TD_CUDA(ctx, cudaMemcpyAsync(f->s.data(), f->ds, sizeof(double) * 2 * f->NQ, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaMemcpyAsync(f->w.data(), f->dw, sizeof(double) * 2 * f->NQ, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    // conjugate pairing: BDF2 k <-> N-k (k = 0 and N/2 are real);
+    // gCQ l <-> NQ-1-l (no real points for even NQ)
+    const int NQ = f->NQ;
+    f->unique.assign(NQ, 0);
+    f->uidx.clear();
+    for (int k = 0; k < NQ; ++k) {
+        int partner = f->kind == 0 ? (NQ - k) % NQ : NQ - 1 - k;
+        if (partner < k) continue;  // assigned as conjugate below
+        const int rep = (int)f->uidx.size();
+        f->uidx.push_back(k);
+        f->unique[k] = rep + 1;
+        if (partner != k) f->unique[partner] = -(rep + 1);
+    }
+    f->Nu = (int)f->uidx.size();
+    return TDBEM_OK;
+}
+}  // namespace
+
+extern "C" int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double lambda, tdbem_freqs_t *out) {
+    if (!ctx || !out || N < 1 || N > 65536 || !(dt > 0.0) || !std::isfinite(dt) || lambda >= 1.0)
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_cq_bdf2: need N >= 1, dt > 0, lambda < 1");
+    *out = nullptr;
+    if (lambda <= 0.0) lambda = std::pow(1e-8, 1.0 / (2.0 * N));
+    tdbem_freqs *f = new (std::nothrow) tdbem_freqs();
+    if (!f) return TDBEM_ERR_OOM;
+    f->ctx = ctx;
+    f->NQ = N;
+    f->kind = 0;
+    f->s.assign(2 * N, 0.0);
+    f->w.assign(2 * N, 0.0);
+    int rc;
+    if ((rc = dalloc(ctx, &f->ds, 4 * (size_t)N))) {
+        delete f;
+        return rc;
+    }
+    f->dw = f->ds + 2 * N;
+    cudaMemsetAsync(f->dw, 0, sizeof(double) * 2 * N, ctx->stream);
+    if (td_launch_bdf2(ctx->stream, N, dt, lambda, f->ds) || (rc = finish_freqs(ctx, f))) {
+        cudaFree(f->ds);
+        delete f;
+        return rc ? rc : td_fail(ctx, TDBEM_ERR_CUDA, "BDF2 frequency kernel failed");
+    }
+    *out = f;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, double dt_min, double dt_max, int32_t rk, int32_t NQ,
+                               tdbem_freqs_t *out) {
+    if (!ctx || !out || !(dt_min > 0.0) || !(dt_max >= dt_min) || !std::isfinite(dt_max) || NQ < 2 ||
+        NQ % 2 || NQ > 65536 || (rk != TDBEM_EULER && rk != TDBEM_RADAU2))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_gcq: need 0 < dt_min <= dt_max, even NQ >= 2, rk EULER|RADAU2");
+    *out = nullptr;
+    double q = dt_max / dt_min;
+    if (rk == TDBEM_RADAU2) q *= 5.0;  // |lambda_1(A)| = |lambda_2(A)| for 2-stage Radau IIA
+    if (q < 1.01) q = 1.01;            // App. A: q = 1 gives k = 0; lift it slightly
+    tdbem_freqs *f = new (std::nothrow) tdbem_freqs();
+    if (!f) return TDBEM_ERR_OOM;
+    f->ctx = ctx;
+    f->NQ = NQ;
+    f->kind = 1;
+    f->s.assign(2 * NQ, 0.0);
+    f->w.assign(2 * NQ, 0.0);
+    int rc;
+    if ((rc = dalloc(ctx, &f->ds, 4 * (size_t)NQ))) {
+        delete f;
+        return rc;
+    }
+    f->dw = f->ds + 2 * NQ;
+    if (td_launch_gcq(ctx->stream, NQ, dt_min, q, f->ds, f->dw) || (rc = finish_freqs(ctx, f))) {
+        cudaFree(f->ds);
+        delete f;
+        return rc ? rc : td_fail(ctx, TDBEM_ERR_CUDA, "gCQ frequency kernel failed");
+    }
+    *out = f;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_freqs_get(tdbem_freqs_t f, double *s, double *w, int32_t *NQ, int32_t *Nu, int32_t *unique) {
+    if (!f) return TDBEM_ERR_ARG;
+    if (s) std::memcpy(s, f->s.data(), sizeof(double) * 2 * f->NQ);
+    if (w) std::memcpy(w, f->w.data(), sizeof(double) * 2 * f->NQ);
+    if (NQ) *NQ = f->NQ;
+    if (Nu) *Nu = f->Nu;
+    if (unique) std::memcpy(unique, f->unique.data(), sizeof(int32_t) * f->NQ);
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_freqs_destroy(tdbem_freqs_t f) {
+    if (!f) return TDBEM_OK;
+    cudaFree(f->ds);
+    delete f;
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// tree
+// ============================================================================
+extern "C" int tdbem_tree_build(tdbem_mesh_t mesh, int32_t row_basis, int32_t col_basis, int32_t leaf, double eta,
+                                tdbem_tree_t *out) {
+    if (!mesh || !out) return TDBEM_ERR_ARG;
+    tdbem_ctx *ctx = mesh->ctx;
+    *out = nullptr;
+    if (leaf < 1 || !(eta > 0.0) || !std::isfinite(eta) || (row_basis != TDBEM_P0 && row_basis != TDBEM_P1) ||
+        (col_basis != TDBEM_P0 && col_basis != TDBEM_P1))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_tree_build: need leaf >= 1, eta > 0, basis P0|P1");
+    tdbem_tree *t = new (std::nothrow) tdbem_tree();
+    if (!t) return TDBEM_ERR_OOM;
+    t->mesh = mesh;
+    t->leaf = leaf;
+    t->eta = eta;
+    td_plan_tree(mesh, row_basis, leaf, t->side[0]);
+    td_plan_tree(mesh, col_basis, leaf, t->side[1]);
+    td_plan_blocks(t->side[0], t->side[1], eta, t->blocks);
+    *out = t;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tree_export(tdbem_tree_t t, int32_t *pr, int32_t *pc, int64_t *nb, int32_t *blocks) {
+    if (!t) return TDBEM_ERR_ARG;
+    if (pr) std::memcpy(pr, t->side[0].perm.data(), sizeof(int32_t) * t->side[0].n);
+    if (pc) std::memcpy(pc, t->side[1].perm.data(), sizeof(int32_t) * t->side[1].n);
+    if (nb) *nb = (int64_t)t->blocks.size() / 5;
+    if (blocks) std::memcpy(blocks, t->blocks.data(), sizeof(int32_t) * t->blocks.size());
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tree_destroy(tdbem_tree_t t) {
+    delete t;
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// entries
+// ============================================================================
+extern "C" int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const int32_t *rows, int64_t nr,
+                             const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf, void *out) {
+    if (!mesh || !f) return TDBEM_ERR_ARG;
+    tdbem_ctx *ctx = mesh->ctx;
+    int rc = check_op(ctx, op);
+    if (rc) return rc;
+    if (nr < 0 || nc < 0 || nf < 0 || (nr * nc * nf > 0 && (!rows || !cols || !fidx || !out)))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries: bad sizes or NULL pointers");
+    if (nr * nc * nf == 0) return TDBEM_OK;
+    Guard g;
+    double *gx, *gw, *sig;
+    int *tp_slot, *pti, *ptj, np;
+    if ((rc = prepare_sing(ctx, mesh, op->op, op->ng, g.p, &gx, &gw, &tp_slot, &pti, &ptj, &np))) return rc;
+    std::vector<double> hs(2 * f->NQ);
+    for (int k = 0; k < 2 * f->NQ; ++k) hs[k] = f->s[k] / op->c;
+    if ((rc = dalloc(ctx, &sig, hs.size(), &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size()))) return rc;
+    MeshDev md = mesh_dev(mesh, op->ng, gx, gw, tp_slot);
+    if (td_launch_entries(ctx->stream, md, op->op, op->prec, sig, f->NQ, rows, nr, cols, nc, fidx, nf, out))
+        return td_fail(ctx, TDBEM_ERR_CUDA, "entry kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // transient buffers are freed on return
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// compression
+// ============================================================================
+namespace {
+
+void free_tensor(tdbem_tensor *t) {
+    if (!t) return;
+    for (void *p : t->owned) cudaFree(p);
+    delete t;
+}
+
+TensorOut tensor_out(const tdbem_tensor *t, int *flags) {
+    TensorOut o{};
+    o.Nu = t->Nu;
+    o.rank = t->drank;
+    o.kpiv = t->dkpiv;
+    o.frank = t->dfrank;
+    o.foff = t->dfoff;
+    o.fib = t->dfib;
+    o.face = t->dface;
+    o.face_cap = t->face_cap;
+    o.face_used = (unsigned long long *)t->dface_used;
+    o.dev_flags = flags;
+    return o;
+}
+
+}  // namespace
+
+extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f,
+                              tdbem_tree_t tree, const tdbem_aca_cfg *cfg, tdbem_tensor_t *out) {
+    if (!ctx || !mesh || !f || !tree || !cfg || !out) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_compress: NULL argument");
+    *out = nullptr;
+    int rc = check_op(ctx, op);
+    if (rc) return rc;
+    if (tree->mesh != mesh) return td_fail(ctx, TDBEM_ERR_ARG, "tree was built on another mesh");
+    if (tree->side[0].basis != TDBEM_P0 || tree->side[1].basis != (op->op == TDBEM_DLP ? TDBEM_P1 : TDBEM_P0))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tree bases do not match the operator (SLP: P0 x P0, DLP: P0 x P1)");
+    if (!(cfg->eps > 0.0) || !(cfg->eps_aca > 0.0)) return td_fail(ctx, TDBEM_ERR_ARG, "eps and eps_aca must be > 0");
+    if (f->Nu > 256) return td_fail(ctx, TDBEM_ERR_ARG, "at most 256 unique frequencies are supported");
+    const double t0 = now_ms();
+    const int Nu = f->Nu;
+    const int kcap = cfg->max_face_rank > 0 ? std::min(cfg->max_face_rank, 512) : 64;
+    tdbem_tensor *T = new (std::nothrow) tdbem_tensor();
+    if (!T) return TDBEM_ERR_OOM;
+    T->ctx = ctx;
+    T->mesh = mesh;
+    T->freqs = f;
+    T->op = op->op;
+    T->prec = op->prec;
+    T->c = op->c;
+    T->ng = op->ng;
+    T->nrows = tree->side[0].n;
+    T->ncols = tree->side[1].n;
+    T->Nu = Nu;
+    T->NQ = f->NQ;
+    T->blocks = tree->blocks;
+    const int64_t nb = (int64_t)tree->blocks.size() / 5;
+    T->nblocks = nb;
+    const size_t es = op->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
+    auto fail = [&](int code) {
+        free_tensor(T);
+        return code;
+    };
+    // ---- plan: near/far lists, offsets
+    std::vector<int32_t> near_ids, far_ids;
+    std::vector<int64_t> eprefix, noff;
+    int64_t nent = 0, ntens = 0, maxIJ = 1, sum_far_len = 0;
+    int maxI = 1, maxJ = 1, max_near_rows = 1;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int32_t *bl = &tree->blocks[5 * b];
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        if (bl[4]) {
+            far_ids.push_back((int32_t)b);
+            maxI = std::max(maxI, nI);
+            maxJ = std::max(maxJ, nJ);
+            sum_far_len += nI + nJ;
+        } else {
+            near_ids.push_back((int32_t)b);
+            eprefix.push_back(nent);
+            noff.push_back(ntens);
+            nent += (int64_t)nI * nJ;
+            ntens += (int64_t)nI * nJ * Nu;
+            maxIJ = std::max<int64_t>(maxIJ, (int64_t)nI * nJ);
+            max_near_rows = std::max(max_near_rows, nI);
+        }
+    }
+    std::sort(far_ids.begin(), far_ids.end(), [&](int32_t x, int32_t y) {
+        const int32_t *a = &tree->blocks[5 * x], *b = &tree->blocks[5 * y];
+        const int64_t sa = (int64_t)(a[1] - a[0]) * (a[3] - a[2]), sb = (int64_t)(b[1] - b[0]) * (b[3] - b[2]);
+        return sa != sb ? sa > sb : x < y;
+    });
+    T->kcap = kcap;
+    T->max_near_rows = max_near_rows;
+    // ---- persistent device data of the tensor
+    std::vector<int32_t> inv_r(T->nrows), inv_c(T->ncols);
+    for (int64_t k = 0; k < T->nrows; ++k) inv_r[tree->side[0].perm[k]] = (int32_t)k;
+    for (int64_t k = 0; k < T->ncols; ++k) inv_c[tree->side[1].perm[k]] = (int32_t)k;
+    if ((rc = dalloc(ctx, &T->dblocks, 5 * nb, &T->owned)) || (rc = dalloc(ctx, &T->dperm_r, T->nrows, &T->owned)) ||
+        (rc = dalloc(ctx, &T->dperm_c, T->ncols, &T->owned)) || (rc = dalloc(ctx, &T->dinv_r, T->nrows, &T->owned)) ||
+        (rc = dalloc(ctx, &T->dinv_c, T->ncols, &T->owned)) || (rc = dalloc(ctx, &T->drank, nb, &T->owned)) ||
+        (rc = dalloc(ctx, &T->dkpiv, nb * Nu, &T->owned)) || (rc = dalloc(ctx, &T->dfrank, nb * Nu, &T->owned)) ||
+        (rc = dalloc(ctx, &T->dfoff, nb * Nu, &T->owned)) || (rc = dalloc(ctx, &T->dpartner, f->NQ + 1, &T->owned)) ||
+        (rc = dalloc(ctx, &T->dface_used, 2, &T->owned)))
+        return fail(rc);
+    char *fib = nullptr;
+    if ((rc = dalloc(ctx, &fib, es * nb * Nu * Nu, &T->owned))) return fail(rc);
+    T->dfib = fib;
+    if ((rc = upload(ctx, T->dblocks, tree->blocks.data(), 5 * nb)) ||
+        (rc = upload(ctx, T->dperm_r, tree->side[0].perm.data(), T->nrows)) ||
+        (rc = upload(ctx, T->dperm_c, tree->side[1].perm.data(), T->ncols)) ||
+        (rc = upload(ctx, T->dinv_r, inv_r.data(), T->nrows)) || (rc = upload(ctx, T->dinv_c, inv_c.data(), T->ncols)) ||
+        (rc = upload(ctx, T->dpartner, f->unique.data(), f->NQ)))
+        return fail(rc);
+    // ---- transient buffers
+    Guard g;
+    double *gx, *gw, *sig;
+    int *tp_slot, *pti, *ptj, npairs;
+    if ((rc = prepare_sing(ctx, mesh, op->op, op->ng, g.p, &gx, &gw, &tp_slot, &pti, &ptj, &npairs))) return fail(rc);
+    std::vector<double> hs(2 * Nu);
+    for (int u = 0; u < Nu; ++u) {
+        hs[2 * u] = f->s[2 * f->uidx[u]] / op->c;
+        hs[2 * u + 1] = f->s[2 * f->uidx[u] + 1] / op->c;
+    }
+    c64 *table;
+    char *nearbuf, *scr_near, *scr_far;
+    int32_t *dnear_ids, *dfar_ids, *flags;
+    int64_t *deprefix, *dnoff, *evals;
+    unsigned int *counter;
+    const int nctas_near = std::min<int64_t>(std::max<int64_t>(1, (int64_t)near_ids.size()), (int64_t)ctx->num_sms * 8);
+    const int nctas_far = std::min<int64_t>(std::max<int64_t>(1, (int64_t)far_ids.size()), (int64_t)ctx->num_sms * 2);
+    const int64_t sper_far = (int64_t)kcap * (maxI + maxJ);
+    if ((rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size())) ||
+        (rc = dalloc(ctx, &table, (size_t)npairs * Nu * 3, &g.p)) || (rc = dalloc(ctx, &nearbuf, es * ntens, &g.p)) ||
+        (rc = dalloc(ctx, &scr_near, es * maxIJ * nctas_near, &g.p)) ||
+        (rc = dalloc(ctx, &scr_far, es * sper_far * nctas_far, &g.p)) ||
+        (rc = dalloc(ctx, &dnear_ids, near_ids.size(), &g.p)) || (rc = dalloc(ctx, &dfar_ids, far_ids.size(), &g.p)) ||
+        (rc = dalloc(ctx, &deprefix, eprefix.size(), &g.p)) || (rc = dalloc(ctx, &dnoff, noff.size(), &g.p)) ||
+        (rc = dalloc(ctx, &flags, 4, &g.p)) || (rc = dalloc(ctx, &evals, 4, &g.p)) || (rc = dalloc(ctx, &counter, 4, &g.p)))
+        return fail(rc);
+    if ((rc = upload(ctx, dnear_ids, near_ids.data(), near_ids.size())) ||
+        (rc = upload(ctx, dfar_ids, far_ids.data(), far_ids.size())) ||
+        (rc = upload(ctx, deprefix, eprefix.data(), eprefix.size())) || (rc = upload(ctx, dnoff, noff.data(), noff.size())))
+        return fail(rc);
+    MeshDev md = mesh_dev(mesh, op->ng, gx, gw, tp_slot);
+    NearArgs na{};
+    na.nf = Nu;
+    na.sig = sig;
+    na.nnear = (int)near_ids.size();
+    na.near_ids = dnear_ids;
+    na.eprefix = deprefix;
+    na.noff = dnoff;
+    na.blocks = T->dblocks;
+    na.perm_r = T->dperm_r;
+    na.perm_c = T->dperm_c;
+    na.nentries = nent;
+    na.near = nearbuf;
+    AcaParams ap{cfg->eps, cfg->eps_aca, kcap};
+    FarArgs fa{};
+    fa.nfar = (int)far_ids.size();
+    fa.far_ids = dfar_ids;
+    fa.blocks = T->dblocks;
+    fa.perm_r = T->dperm_r;
+    fa.perm_c = T->dperm_c;
+    fa.sig = sig;
+    fa.nf = Nu;
+    fa.maxI = maxI;
+    fa.maxJ = maxJ;
+    fa.scratch = scr_far;
+    fa.scratch_per_cta = sper_far;
+    fa.counter = counter;
+    fa.evals = evals;
+    const double t_plan = now_ms();
+    // face pool: every near term fits (r <= Nu), far terms get a generous
+    // estimate; on overflow the far phase is rerun with a larger pool.
+    int64_t cap = ntens + sum_far_len * 256 + 1024;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k) cudaEventCreate(&ev[k]);
+    int hflags = 0;
+    long long hev[2] = {0, 0};
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if (T->dface) {
+            cudaFree(T->dface);
+            T->owned.erase(std::find(T->owned.begin(), T->owned.end(), T->dface));
+            T->dface = nullptr;
+        }
+        char *face = nullptr;
+        if ((rc = dalloc(ctx, &face, es * cap, &T->owned))) {
+            for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+            return fail(rc);
+        }
+        T->dface = face;
+        T->face_cap = cap;
+        TensorOut o = tensor_out(T, flags);
+        // capture the phases in one graph
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const bool use_graph = !(cfg->flags & 1);
+        if (use_graph) TD_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+        int lrc = 0;
+        cudaMemsetAsync(T->dface_used, 0, sizeof(int64_t) * 2, ctx->stream);
+        cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ctx->stream);
+        cudaMemsetAsync(evals, 0, sizeof(int64_t) * 4, ctx->stream);
+        cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ctx->stream);
+        cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ctx->stream);
+        cudaEventRecord(ev[0], ctx->stream);
+        lrc |= td_launch_sing_table(ctx->stream, md, op->op, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
+        cudaEventRecord(ev[1], ctx->stream);
+        lrc |= td_launch_near_entries(ctx->stream, md, op->op, op->prec, na, table, ctx->num_sms);
+        cudaEventRecord(ev[2], ctx->stream);
+        lrc |= td_launch_near_aca(ctx->stream, op->prec, na, o, ap, scr_near, maxIJ, nctas_near);
+        cudaEventRecord(ev[3], ctx->stream);
+        lrc |= td_launch_far_aca(ctx->stream, md, op->op, op->prec, fa, o, ap, nctas_far);
+        cudaEventRecord(ev[4], ctx->stream);
+        if (use_graph) {
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+            if (e != cudaSuccess || lrc) {
+                if (graph) cudaGraphDestroy(graph);
+                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+                cudaGetLastError();
+                return fail(td_fail(ctx, TDBEM_ERR_CUDA, "graph capture of the compression failed: %s (launch %d)",
+                                    cudaGetErrorString(e), lrc));
+            }
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, ctx->stream);
+            if (e != cudaSuccess) {
+                if (exec) cudaGraphExecDestroy(exec);
+                cudaGraphDestroy(graph);
+                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+                return fail(td_fail(ctx, TDBEM_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(e)));
+            }
+        } else if (lrc) {
+            for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+            return fail(td_fail(ctx, TDBEM_ERR_CUDA, "kernel launch failed (%d)", lrc));
+        }
+        cudaError_t se = cudaStreamSynchronize(ctx->stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (se != cudaSuccess) {
+            for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+            return fail(td_fail(ctx, TDBEM_ERR_CUDA, "compression kernels failed: %s", cudaGetErrorString(se)));
+        }
+        cudaMemcpy(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaMemcpy(hev, evals, sizeof hev, cudaMemcpyDeviceToHost);
+        if (!(hflags & TD_DEV_POOL_OVERFLOW)) break;
+        cap *= 2;
+    }
+    if (hflags & TD_DEV_POOL_OVERFLOW) {
+        for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+        return fail(td_fail(ctx, TDBEM_ERR_CAPACITY, "face pool overflow after retries"));
+    }
+    float ms[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    // ---- host copies of the per-block results and statistics
+    T->rank.resize(nb);
+    std::vector<int32_t> frank(nb * Nu);
+    TD_CUDA(ctx, cudaMemcpy(T->rank.data(), T->drank, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+    TD_CUDA(ctx, cudaMemcpy(frank.data(), T->dfrank, sizeof(int32_t) * nb * Nu, cudaMemcpyDeviceToHost));
+    tdbem_stats &st = T->stats;
+    std::memset(&st, 0, sizeof st);
+    st.nblocks = nb;
+    st.nnear = (int64_t)near_ids.size();
+    st.nfar = (int64_t)far_ids.size();
+    T->frank_sum.assign(nb, 0);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int32_t *bl = &tree->blocks[5 * b];
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        st.sum_rank += T->rank[b];
+        st.max_rank = std::max<int64_t>(st.max_rank, T->rank[b]);
+        for (int d = 0; d < T->rank[b]; ++d) {
+            const int kf = frank[b * Nu + d];
+            st.stored_complex += Nu + (kf < 0 ? (int64_t)nI * nJ : (int64_t)kf * (nI + nJ));
+            if (kf > 0) {
+                st.sum_face_rank += kf;
+                T->frank_sum[b] += kf;
+            }
+        }
+    }
+    st.dense_complex = T->nrows * T->ncols * (int64_t)Nu;
+    st.entries_regular = nent * Nu + hev[0];
+    st.entries_tube = hev[1];
+    st.pairs_singular = (int64_t)npairs * Nu;
+    st.ms_plan = t_plan - t0;
+    st.ms_singular = ms[0];
+    st.ms_near = ms[1] + ms[2];
+    st.ms_far = ms[3];
+    st.ms_total = now_ms() - t0;
+    if (hflags & TD_DEV_RANK_CAP)
+        td_fail(ctx, TDBEM_OK, "note: some far faces reached the rank cap %d", kcap);
+    *out = T;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tensor_stats(tdbem_tensor_t t, tdbem_stats *st) {
+    if (!t || !st) return TDBEM_ERR_ARG;
+    *st = t->stats;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tensor_blocks(tdbem_tensor_t t, int32_t *rank, int32_t *face_rank_sum, int32_t *kpiv) {
+    if (!t) return TDBEM_ERR_ARG;
+    if (rank) std::memcpy(rank, t->rank.data(), sizeof(int32_t) * t->nblocks);
+    if (face_rank_sum) std::memcpy(face_rank_sum, t->frank_sum.data(), sizeof(int32_t) * t->nblocks);
+    if (kpiv) {
+        std::vector<int32_t> k(t->nblocks * t->Nu);
+        TD_CUDA(t->ctx, cudaMemcpy(k.data(), t->dkpiv, sizeof(int32_t) * k.size(), cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < t->nblocks; ++b)
+            for (int d = 0; d <= t->Nu; ++d)
+                kpiv[b * (t->Nu + 1) + d] = d < t->rank[b] ? k[b * t->Nu + d] : -1;
+    }
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tensor_entries(tdbem_tensor_t t, const int32_t *rows, const int32_t *cols, const int32_t *fidx,
+                                    int64_t count, void *out) {
+    if (!t) return TDBEM_ERR_ARG;
+    if (count < 0 || (count > 0 && (!rows || !cols || !fidx || !out)))
+        return td_fail(t->ctx, TDBEM_ERR_ARG, "tdbem_tensor_entries: bad arguments");
+    TensorOut o = tensor_out(t, nullptr);
+    if (td_launch_tensor_entries(t->ctx->stream, t->prec, o, t->dblocks, (int)t->nblocks, t->nrows, t->ncols,
+                                 t->NQ, t->dinv_r, t->dinv_c,
+                                 t->dpartner, rows, cols, fidx, count, out))
+        return td_fail(t->ctx, TDBEM_ERR_CUDA, "tensor entry kernel failed");
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tensor_destroy(tdbem_tensor_t t) {
+    if (t) {
+        if (t->dy_host) cudaFree(t->dy_host);
+        free_tensor(t);
+    }
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// apply
+// ============================================================================
+namespace {
+int apply_impl(tdbem_tensor *t, const void *W, int nrhs, void *y, int single_f) {
+    tdbem_ctx *ctx = t->ctx;
+    if (nrhs < 1 || nrhs > 64 || !W || !y) return td_fail(ctx, TDBEM_ERR_ARG, "apply: need 1 <= nrhs <= 64 and non-NULL buffers");
+    const size_t es = t->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
+    TD_CUDA(ctx, cudaMemsetAsync(y, 0, es * t->nrows * nrhs, ctx->stream));
+    ApplyArgs a{};
+    a.nb = (int)t->nblocks;
+    a.blocks = t->dblocks;
+    a.perm_r = t->dperm_r;
+    a.perm_c = t->dperm_c;
+    a.Nu = t->Nu;
+    a.NQ = t->NQ;
+    a.qmap = t->dpartner;
+    a.W = W;
+    a.nrhs = nrhs;
+    a.ncols = t->ncols;
+    a.y = y;
+    a.single_f = single_f;
+    a.kcap = t->kcap;
+    a.max_near_rows = t->max_near_rows;
+    TensorOut o = tensor_out(t, nullptr);
+    int e = td_launch_apply(ctx->stream, t->prec, a, o, ctx->num_sms);
+    if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "apply kernel failed: %s", cudaGetErrorString((cudaError_t)e));
+    return TDBEM_OK;
+}
+}  // namespace
+
+extern "C" int tdbem_apply_weighted(tdbem_tensor_t t, const void *W, int32_t nrhs, void *y) {
+    if (!t) return TDBEM_ERR_ARG;
+    return apply_impl(t, W, nrhs, y, -1);
+}
+
+extern "C" int tdbem_apply_freq(tdbem_tensor_t t, int32_t fidx, const void *x, int32_t nrhs, void *y) {
+    if (!t) return TDBEM_ERR_ARG;
+    if (fidx < 0 || fidx >= t->NQ) return td_fail(t->ctx, TDBEM_ERR_ARG, "frequency index out of range");
+    return apply_impl(t, x, nrhs, y, fidx);
+}
+
+extern "C" int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, int32_t nrhs, void *y_host) {
+    if (!t || !W_host || !y_host || nrhs < 1 || nrhs > 64) return TDBEM_ERR_ARG;
+    tdbem_ctx *ctx = t->ctx;
+    const size_t es = t->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
+    const size_t wb = es * t->NQ * t->ncols * nrhs, yb = es * t->nrows * nrhs;
+    if (wb + yb > t->host_buf_bytes) {
+        if (t->dy_host) cudaFree(t->dy_host);
+        t->dy_host = nullptr;
+        t->host_buf_bytes = 0;
+        char *p;
+        int rc = dalloc(ctx, &p, wb + yb);
+        if (rc) return rc;
+        t->dy_host = p;
+        t->host_buf_bytes = wb + yb;
+    }
+    char *dW = (char *)t->dy_host, *dy = dW + wb;
+    TD_CUDA(ctx, cudaMemcpyAsync(dW, W_host, wb, cudaMemcpyHostToDevice, ctx->stream));
+    int rc = apply_impl(t, dW, nrhs, dy, -1);
+    if (rc) return rc;
+    TD_CUDA(ctx, cudaMemcpyAsync(y_host, dy, yb, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TDBEM_OK;
+}

@@ -1,0 +1,120 @@
+// Internal host-side structures of the tdbem library (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tdbem.h"
+
+struct tdbem_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 0;
+};
+
+// Host-side planner output for the cluster trees and the block list.
+struct ClusterNode {
+    int32_t begin, end, son0, son1;
+    double box[6];
+};
+
+struct HostTree {
+    int basis = 0;
+    int64_t n = 0;
+    std::vector<int32_t> perm;
+    std::vector<ClusterNode> nodes;
+};
+
+struct tdbem_tree {
+    tdbem_mesh *mesh = nullptr;
+    HostTree side[2];
+    std::vector<int32_t> blocks;  // [nb][5]
+    int leaf = 0;
+    double eta = 0.0;
+};
+
+struct tdbem_mesh {
+    tdbem_ctx *ctx = nullptr;
+    int64_t nv = 0, nt = 0;
+    std::vector<double> verts;
+    std::vector<int32_t> tris;
+    std::vector<double> area;
+    // vertex -> triangle incidence (P1 supports)
+    std::vector<int32_t> v2t_ptr, v2t;
+    std::vector<int8_t> v2t_loc;
+    // touching triangles per triangle (sorted by triangle index)
+    std::vector<int32_t> tp_ptr, tp_tri;
+    // device tables
+    float *qxh = nullptr, *qyh, *qzh, *qxl, *qyl, *qzl, *qw32, *n32;
+    double *qx = nullptr, *qy, *qz, *qw, *n64, *dverts, *darea;
+    int32_t *dtris = nullptr, *dv2t_ptr = nullptr, *dv2t = nullptr;
+    int8_t *dv2t_loc = nullptr;
+    int32_t *dtp_ptr = nullptr, *dtp_tri = nullptr;
+    void *dev_block = nullptr;  // one allocation holding all tables
+};
+
+struct tdbem_freqs {
+    tdbem_ctx *ctx = nullptr;
+    int32_t NQ = 0, Nu = 0;
+    std::vector<double> s, w;     // [2*NQ] host copies
+    std::vector<int32_t> unique;  // per point: rep+1 or -(rep+1)
+    std::vector<int32_t> uidx;    // unique representative -> point index
+    double *ds = nullptr;         // device [2*NQ]
+    double *dw = nullptr;
+    int kind = 0;                 // 0 BDF2, 1 gCQ
+};
+
+// Compressed tensor (device pools + host copies of the small metadata).
+struct tdbem_tensor {
+    tdbem_ctx *ctx = nullptr;
+    tdbem_mesh *mesh = nullptr;
+    tdbem_freqs *freqs = nullptr;
+    int op = 0, prec = 0;
+    double c = 1.0;
+    int ng = 5;
+    int64_t nrows = 0, ncols = 0;
+    int Nu = 0, NQ = 0;
+    int64_t nblocks = 0;
+    int32_t *dblocks = nullptr;     // [nb][5] permuted ranges
+    int32_t *dperm_r = nullptr, *dperm_c = nullptr;   // position -> DOF
+    int32_t *dinv_r = nullptr, *dinv_c = nullptr;     // DOF -> position
+    // per block: number of terms, per term (fixed slots [nb][Nu]): selected
+    // frequency, face rank (-1 dense), face offset (complex units)
+    int32_t *drank = nullptr, *dkpiv = nullptr, *dfrank = nullptr;
+    int64_t *dfoff = nullptr;
+    void *dfib = nullptr;           // fibres [nb][Nu][Nu] complex
+    void *dface = nullptr;          // face pool (complex)
+    int64_t face_cap = 0;
+    int64_t *dface_used = nullptr;
+    // host copies (filled by compress)
+    std::vector<int32_t> blocks;
+    std::vector<int32_t> rank, frank_sum;
+    tdbem_stats stats{};
+    std::vector<void *> owned;      // device allocations to free
+    int32_t *dpartner = nullptr;    // [NQ] unique-map of the frequency set
+    int kcap = 64;                  // face-rank cap used by the compression
+    int max_near_rows = 1;
+    void *dy_host = nullptr;        // staging buffers of tdbem_apply_weighted_host
+    size_t host_buf_bytes = 0;
+};
+
+// helpers (api.cu)
+int td_fail(tdbem_ctx *ctx, int code, const char *fmt, ...);
+#define TD_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return td_fail((ctx), TDBEM_ERR_CUDA, "%s: %s (%s:%d)", #call,                   \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+// planner.cpp
+void td_plan_tree(const tdbem_mesh *m, int basis, int leaf, HostTree &t);
+void td_plan_blocks(const HostTree &rows, const HostTree &cols, double eta,
+                    std::vector<int32_t> &blocks);
+void td_mesh_adjacency(tdbem_mesh *m);
+int td_gauss01(int n, double *x, double *w);
+void td_rule7(double bary[7][3], double w[7]);

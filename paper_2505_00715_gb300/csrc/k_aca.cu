@@ -1,0 +1,668 @@
+// 3D-ACA over frequency (Sec. 4, Algorithm 1) for every block of the block
+// cluster tree.
+//
+// Per block, with C^(0) = 0, k_1 = the first unique frequency:
+//   H_l = ENTRY(., ., k_l) - C^(l-1)(., ., k_l)        residual face
+//   (i_l, j_l) = argmax |H_l|                            pivot
+//   f_l[k] = (ENTRY(i_l, j_l, k) - C^(l-1)(i_l, j_l, k)) / H_l[i_l, j_l]
+//   stop when ||H_l||_F ||f_l|| <= eps ||C^(l)||_F  (the last term is dropped),
+//   ||C^(l)||_F^2 = sum_{d,d'} <H_d, H_d'> <f_d, f_d'>   (eq. norm, FP64),
+//   k_{l+1} = argmax |f_l[k]| over frequencies not selected yet.
+// Near-field blocks (k_near_aca): dense faces from the precomputed near tensor,
+// one CTA per block.  Far-field blocks (k_far_aca): every residual face is
+// compressed by ACA with partial pivoting (row fibre at i*, column fibre at
+// j*, FP64 norm recursion of the matrix analogue of eq. norm) from entries
+// evaluated on the fly; the face is rebuilt to find the pivot and discarded
+// (Sec. 4); the frequency tube at the pivot is evaluated with one warp per
+// frequency.  Persistent CTAs take far blocks from an atomic work queue
+// ordered by decreasing size.
+#include "internal.h"
+#include "kernels.h"
+#include "pair.cuh"
+
+namespace {
+
+constexpr int kMaxNu = 256;
+
+// ============================================================================
+// Near field
+// ============================================================================
+template <class T>
+__global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaParams p,
+                                                  cx<T> *scratch, int64_t sper) {
+    __shared__ cx<T> s_fl[kMaxNu];
+    __shared__ cx<T> s_hd[kMaxNu];
+    __shared__ int s_sel[kMaxNu];
+    __shared__ ArgMaxD red[32];
+    __shared__ double redd[32 * 2];
+    __shared__ long long s_off;
+    const int Nu = a.nf;
+    cx<T> *H = scratch + (int64_t)blockIdx.x * sper;
+    cx<T> *fib = (cx<T> *)o.fib;
+    cx<T> *pool = (cx<T> *)o.face;
+    for (int nb = blockIdx.x; nb < a.nnear; nb += gridDim.x) {
+        const int b = a.near_ids[nb];
+        const int *bl = a.blocks + 5 * b;
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        const int64_t nIJ = (int64_t)nI * nJ;
+        const cx<T> *N = (const cx<T> *)a.near + a.noff[nb];
+        const int64_t tb = (int64_t)b * Nu;
+        for (int kk = threadIdx.x; kk < Nu; kk += blockDim.x) s_sel[kk] = 0;
+        __syncthreads();
+        double normC2 = 0.0;
+        int l = 0, k = 0, r = -1;
+        while (l < Nu) {
+            ArgMaxD am = {-1.0, 0x7fffffff};
+            for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
+                cx<T> h = N[k * nIJ + e];
+                for (int d = 0; d < l; ++d) cfms(h, fib[(tb + d) * Nu + k], pool[o.foff[tb + d] + e]);
+                H[e] = h;
+                double v = (double)h.x * h.x + (double)h.y * h.y;
+                if (am_better(v, (int)e, am.v, am.i)) am = {v, (int)e};
+            }
+            am = block_argmax(am, red);
+            if (!(am.v > 0.0)) {
+                r = l;
+                break;
+            }
+            const int ep = am.i;
+            const cx<T> piv = H[ep];
+            for (int d = threadIdx.x; d < l; d += blockDim.x) s_hd[d] = pool[o.foff[tb + d] + ep];
+            __syncthreads();
+            for (int kk = threadIdx.x; kk < Nu; kk += blockDim.x) {
+                cx<T> v = N[kk * nIJ + ep];
+                for (int d = 0; d < l; ++d) cfms(v, s_hd[d], fib[(tb + d) * Nu + kk]);
+                s_fl[kk] = cdiv(v, piv);
+            }
+            __syncthreads();
+            // eq. norm in FP64: <H_l, H_d>, ||H_l||^2, <f_l, f_d>
+            double v2[2] = {0.0, 0.0};
+            for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
+                c64 h = ccast<double>(H[e]);
+                v2[0] += h.x * h.x + h.y * h.y;
+            }
+            block_sum<1>(v2, redd);
+            const double hl2 = v2[0];
+            double fl2 = 0.0;
+            for (int kk = 0; kk < Nu; ++kk) fl2 += cabs2(ccast<double>(s_fl[kk]));
+            double cross = 0.0;
+            for (int d = 0; d < l; ++d) {
+                double g[2] = {0.0, 0.0};
+                const cx<T> *Hd = pool + o.foff[tb + d];
+                for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
+                    c64 x = ccast<double>(H[e]), y = ccast<double>(Hd[e]);
+                    g[0] += x.x * y.x + x.y * y.y;
+                    g[1] += x.y * y.x - x.x * y.y;
+                }
+                block_sum<2>(g, redd);
+                c64 gf = {0.0, 0.0};
+                for (int kk = 0; kk < Nu; ++kk)
+                    gf = gf + ccast<double>(s_fl[kk]) * cconj(ccast<double>(fib[(tb + d) * Nu + kk]));
+                cross += g[0] * gf.x - g[1] * gf.y;
+            }
+            normC2 += 2.0 * cross + hl2 * fl2;
+            if (sqrt(hl2 * fl2) <= p.eps * sqrt(normC2)) {
+                r = l;
+                break;
+            }
+            if (threadIdx.x == 0) {
+                unsigned long long off = atomicAdd(o.face_used, (unsigned long long)nIJ);
+                if ((int64_t)(off + nIJ) > o.face_cap) {
+                    atomicOr(o.dev_flags, TD_DEV_POOL_OVERFLOW);
+                    s_off = -1;
+                } else {
+                    s_off = (long long)off;
+                }
+            }
+            __syncthreads();
+            const long long off = s_off;
+            if (off < 0) {
+                r = l;
+                break;
+            }
+            for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) pool[off + e] = H[e];
+            for (int kk = threadIdx.x; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = s_fl[kk];
+            if (threadIdx.x == 0) {
+                o.kpiv[tb + l] = k;
+                o.frank[tb + l] = -1;
+                o.foff[tb + l] = off;
+            }
+            s_sel[k] = 1;  // same value written by every thread
+            __syncthreads();
+            ++l;
+            int kn = -1;
+            double best = -1.0;
+            for (int kk = 0; kk < Nu; ++kk) {
+                if (s_sel[kk]) continue;
+                double v = cabs2(ccast<double>(s_fl[kk]));
+                if (v > best) {
+                    best = v;
+                    kn = kk;
+                }
+            }
+            if (kn < 0) {
+                r = l;
+                break;
+            }
+            k = kn;
+            __syncthreads();
+        }
+        if (r < 0) r = l;
+        if (threadIdx.x == 0) o.rank[b] = r;
+        __syncthreads();
+    }
+}
+
+// ============================================================================
+// Far field
+// ============================================================================
+template <class T> struct FarTri;
+template <> struct FarTri<float> {
+    using Tri = TriF;
+    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trif(m, t, X); }
+    template <int OP> TD_D static void pair(const Tri &X, const Tri &Y, float sr, float si, c32 *o) {
+        pair_reg_f32<OP>(X, Y, sr, si, o);
+    }
+};
+template <> struct FarTri<double> {
+    using Tri = TriD;
+    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trid(m, t, X); }
+    template <int OP> TD_D static void pair(const Tri &X, const Tri &Y, double sr, double si, c64 *o) {
+        pair_reg_f64<OP>(X, Y, sr, si, o);
+    }
+};
+
+// Regular entry A[row, col] (no touching pairs in far blocks), 1/(4 pi) applied.
+template <class T, int OP>
+TD_D cx<T> far_entry(const MeshDev &m, const typename FarTri<T>::Tri &X, int col, T sr, T si) {
+    using F = FarTri<T>;
+    typename F::Tri Y;
+    cx<T> acc = {0, 0};
+    if (OP == TD_SLP) {
+        F::load(m, col, Y);
+        cx<T> o[3] = {};
+        F::template pair<TD_SLP>(X, Y, sr, si, o);
+        acc = o[0];
+    } else {
+        for (int p = m.v2t_ptr[col]; p < m.v2t_ptr[col + 1]; ++p) {
+            F::load(m, m.v2t[p], Y);
+            cx<T> o[3] = {};
+            F::template pair<TD_DLP>(X, Y, sr, si, o);
+            acc = acc + o[m.v2t_loc[p]];
+        }
+    }
+    const T s = (T)(1.0 / TD_FOUR_PI);
+    return cx<T>{acc.x * s, acc.y * s};
+}
+
+// Column-fibre entry: test triangle per thread, trial DOF fixed.
+template <class T, int OP>
+TD_D cx<T> far_entry_col(const MeshDev &m, int row, int col, T sr, T si) {
+    typename FarTri<T>::Tri X;
+    FarTri<T>::load(m, row, X);
+    return far_entry<T, OP>(m, X, col, sr, si);
+}
+
+// One point pair (a of the test triangle, b of the trial triangle), for the
+// warp-split tube evaluation.
+TD_D c32 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int loc, float sr, float si) {
+    const int oa = a * m.nt + ti, ob = b * m.nt + tj;
+    float dx = (m.qxh[ob] - m.qxh[oa]) + (m.qxl[ob] - m.qxl[oa]);
+    float dy = (m.qyh[ob] - m.qyh[oa]) + (m.qyl[ob] - m.qyl[oa]);
+    float dz = (m.qzh[ob] - m.qzh[oa]) + (m.qzl[ob] - m.qzl[oa]);
+    float r2 = dx * dx + dy * dy + dz * dz;
+    float rinv = rsqrtf(r2), r = r2 * rinv;
+    c32 e = expm_sr(sr, si, r);
+    float w = m.qw32[oa] * m.qw32[ob] * rinv;
+    if (op == TD_SLP) return {w * e.x, w * e.y};
+    w *= bary7f(b, loc) * -(dx * m.n32[tj] + dy * m.n32[m.nt + tj] + dz * m.n32[2 * m.nt + tj]) * rinv * rinv;
+    float pr = fmaf(sr, r, 1.0f), pi = si * r;
+    return {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
+}
+TD_D c64 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int loc, double sr, double si) {
+    const int oa = a * m.nt + ti, ob = b * m.nt + tj;
+    double dx = m.qx[ob] - m.qx[oa], dy = m.qy[ob] - m.qy[oa], dz = m.qz[ob] - m.qz[oa];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    c64 e = expm_sr(sr, si, r);
+    double w = m.qw[oa] * m.qw[ob] / r;
+    if (op == TD_SLP) return {w * e.x, w * e.y};
+    w *= bary7d(b, loc) * -(dx * m.n64[tj] + dy * m.n64[m.nt + tj] + dz * m.n64[2 * m.nt + tj]) / (r * r);
+    double pr = 1.0 + sr * r, pi = si * r;
+    return {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
+}
+
+// Entry by one warp (lanes split the point pairs); every lane gets the value.
+template <class T, int OP>
+TD_D cx<T> warp_entry(const MeshDev &m, int row, int col, T sr, T si) {
+    const int lane = threadIdx.x & 31;
+    cx<T> acc = {0, 0};
+    if (OP == TD_SLP) {
+        for (int c = lane; c < 49; c += 32) acc = acc + point_pair(m, OP, row, c / 7, col, c % 7, 0, sr, si);
+    } else {
+        const int p0 = m.v2t_ptr[col], ns = m.v2t_ptr[col + 1] - p0;
+        for (int c = lane; c < 49 * ns; c += 32) {
+            const int s = c / 49, q = c % 49, p = p0 + s;
+            acc = acc + point_pair(m, OP, row, q / 7, m.v2t[p], q % 7, m.v2t_loc[p], sr, si);
+        }
+    }
+    acc.x = warp_sum(acc.x);
+    acc.y = warp_sum(acc.y);
+    const T s = (T)(1.0 / TD_FOUR_PI);
+    return cx<T>{acc.x * s, acc.y * s};
+}
+
+constexpr int kNT = 256;
+constexpr int kNCoef = 1024;
+
+template <class T>
+struct FarShared {
+    cx<T> fl[kMaxNu];
+    cx<T> hd[kMaxNu];
+    c64 gH[kMaxNu];
+    int sel[kMaxNu];
+    int frank[kMaxNu];
+    long long foff[kMaxNu];
+    ArgMaxD red[32];
+    double redd[32 * 4];
+    cx<T> coef[kNCoef];
+    const cx<T> *base[kNCoef];
+    int idx, jstar, istar, ncoef;
+    long long off;
+    cx<T> piv;
+};
+
+// coefficient list for the residual of previous terms at a fixed row (mode 0:
+// coef f_d[k] U_d[tau][i*], base V_d[tau]) or fixed column (mode 1: coef
+// f_d[k] V_d[tau][j*], base U_d[tau]), followed by the current face's own
+// terms (u_t[i*], base v_t) / (v_t[j*], base u_t).  Entries [c0, c0+kNCoef).
+template <class T>
+TD_D int build_coef(FarShared<T> &S, int mode, int fixed, int l, int kf, int k, int Nu, int64_t tb,
+                    int nI, int nJ, const cx<T> *pool, const cx<T> *fib, const cx<T> *Uw,
+                    const cx<T> *Vw, int maxI, int maxJ, int c0) {
+    // total count
+    int total = kf;
+    for (int d = 0; d < l; ++d) total += S.frank[d];
+    const int cend = min(total, c0 + kNCoef);
+    for (int c = c0 + threadIdx.x; c < cend; c += blockDim.x) {
+        int rem = c, d = 0;
+        while (d < l && rem >= S.frank[d]) {
+            rem -= S.frank[d];
+            ++d;
+        }
+        cx<T> cf;
+        const cx<T> *bp;
+        if (d < l) {
+            const cx<T> *Ud = pool + S.foff[d];
+            const cx<T> *Vd = Ud + (int64_t)S.frank[d] * nI;
+            const cx<T> fk = fib[(tb + d) * Nu + k];
+            if (mode == 0) {
+                cf = fk * Ud[(int64_t)rem * nI + fixed];
+                bp = Vd + (int64_t)rem * nJ;
+            } else {
+                cf = fk * Vd[(int64_t)rem * nJ + fixed];
+                bp = Ud + (int64_t)rem * nI;
+            }
+        } else {
+            if (mode == 0) {
+                cf = Uw[(int64_t)rem * maxI + fixed];
+                bp = Vw + (int64_t)rem * maxJ;
+            } else {
+                cf = Vw[(int64_t)rem * maxJ + fixed];
+                bp = Uw + (int64_t)rem * maxI;
+            }
+        }
+        S.coef[c - c0] = cf;
+        S.base[c - c0] = bp;
+    }
+    return total;
+}
+
+template <class T, int OP>
+__global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FarShared<T> &S = *reinterpret_cast<FarShared<T> *>(smem_raw);
+    unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + sizeof(FarShared<T>));
+    const int Nu = a.nf;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    cx<T> *Uw = (cx<T> *)a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
+    cx<T> *Vw = Uw + (int64_t)p.kcap * a.maxI;
+    cx<T> *fib = (cx<T> *)o.fib;
+    cx<T> *pool = (cx<T> *)o.face;
+    long long ev_reg = 0, ev_tube = 0;
+    for (;;) {
+        if (tid == 0) S.idx = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int idx = S.idx;
+        __syncthreads();
+        if (idx >= a.nfar) break;
+        const int b = a.far_ids[idx];
+        const int *bl = a.blocks + 5 * b;
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        const int *rows = a.perm_r + bl[0], *cols = a.perm_c + bl[2];
+        const int64_t tb = (int64_t)b * Nu;
+        for (int kk = tid; kk < Nu; kk += blockDim.x) S.sel[kk] = 0;
+        __syncthreads();
+        double normC2 = 0.0;
+        int l = 0, k = 0, r = -1;
+        while (l < Nu) {
+            const T sr = (T)a.sig[2 * k], si = (T)a.sig[2 * k + 1];
+            // ------------------------------------------------ ACA of the residual face
+            for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
+            __syncthreads();
+            int kf = 0, istar = 0;
+            double normS2 = 0.0;
+            bool converged = false;
+            int guard = 0;
+            while (kf < p.kcap && guard < nI + p.kcap) {
+                ++guard;
+                // row fibre at istar
+                typename FarTri<T>::Tri X;
+                FarTri<T>::load(m, rows[istar], X);
+                ArgMaxD am = {-1.0, 0x7fffffff};
+                int total = 0;
+                // entries first (kept in Vw[kf]), then residual corrections in chunks
+                for (int j = tid; j < nJ; j += blockDim.x) Vw[(int64_t)kf * a.maxJ + j] = far_entry<T, OP>(m, X, cols[j], sr, si);
+                ev_reg += nJ;
+                for (int c0 = 0;; c0 += kNCoef) {
+                    __syncthreads();
+                    total = build_coef(S, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    __syncthreads();
+                    const int cn = min(kNCoef, total - c0);
+                    for (int j = tid; j < nJ; j += blockDim.x) {
+                        cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
+                        for (int c = 0; c < cn; ++c) cfms(v, S.coef[c], S.base[c][j]);
+                        Vw[(int64_t)kf * a.maxJ + j] = v;
+                    }
+                    if (c0 + kNCoef >= total) break;
+                }
+                for (int j = tid; j < nJ; j += blockDim.x) {
+                    cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
+                    double av = (double)v.x * v.x + (double)v.y * v.y;
+                    if (am_better(av, j, am.v, am.i)) am = {av, j};
+                }
+                am = block_argmax(am, S.red);
+                if (tid == 0) used[istar >> 5] |= 1u << (istar & 31);
+                __syncthreads();
+                if (!(am.v > 0.0)) {
+                    // zero residual row: next unused row, if any
+                    int nxt = -1;
+                    for (int i = 0; i < nI; ++i)
+                        if (!(used[i >> 5] & (1u << (i & 31)))) {
+                            nxt = i;
+                            break;
+                        }
+                    if (nxt < 0) {
+                        converged = true;
+                        break;
+                    }
+                    istar = nxt;
+                    continue;
+                }
+                const int jstar = am.i;
+                const cx<T> piv = Vw[(int64_t)kf * a.maxJ + jstar];
+                __syncthreads();
+                for (int j = tid; j < nJ; j += blockDim.x) {
+                    cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
+                    Vw[(int64_t)kf * a.maxJ + j] = cdiv(v, piv);
+                }
+                // column fibre at jstar
+                for (int i = tid; i < nI; i += blockDim.x)
+                    Uw[(int64_t)kf * a.maxI + i] = far_entry_col<T, OP>(m, rows[i], cols[jstar], sr, si);
+                ev_reg += nI;
+                for (int c0 = 0;; c0 += kNCoef) {
+                    __syncthreads();
+                    total = build_coef(S, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    __syncthreads();
+                    const int cn = min(kNCoef, total - c0);
+                    for (int i = tid; i < nI; i += blockDim.x) {
+                        cx<T> v = Uw[(int64_t)kf * a.maxI + i];
+                        for (int c = 0; c < cn; ++c) cfms(v, S.coef[c], S.base[c][i]);
+                        Uw[(int64_t)kf * a.maxI + i] = v;
+                    }
+                    if (c0 + kNCoef >= total) break;
+                }
+                __syncthreads();
+                ArgMaxD am2 = {-1.0, 0x7fffffff};
+                for (int i = tid; i < nI; i += blockDim.x) {
+                    if (used[i >> 5] & (1u << (i & 31))) continue;
+                    cx<T> v = Uw[(int64_t)kf * a.maxI + i];
+                    double av = (double)v.x * v.x + (double)v.y * v.y;
+                    if (am_better(av, i, am2.v, am2.i)) am2 = {av, i};
+                }
+                am2 = block_argmax(am2, S.red);
+                // FP64 norm recursion: ||S_k||^2 += 2 Re sum_t <u_k,u_t><v_k,v_t> + |u_k|^2 |v_k|^2
+                double acc4[4] = {0.0, 0.0, 0.0, 0.0};  // cross, |u|^2, |v|^2
+                for (int t = wid; t <= kf; t += nwarps) {
+                    double gu[2] = {0, 0}, gv[2] = {0, 0};
+                    for (int i = lane; i < nI; i += 32) {
+                        c64 x = ccast<double>(Uw[(int64_t)kf * a.maxI + i]), y = ccast<double>(Uw[(int64_t)t * a.maxI + i]);
+                        gu[0] += x.x * y.x + x.y * y.y;
+                        gu[1] += x.y * y.x - x.x * y.y;
+                    }
+                    for (int j = lane; j < nJ; j += 32) {
+                        c64 x = ccast<double>(Vw[(int64_t)kf * a.maxJ + j]), y = ccast<double>(Vw[(int64_t)t * a.maxJ + j]);
+                        gv[0] += x.x * y.x + x.y * y.y;
+                        gv[1] += x.y * y.x - x.x * y.y;
+                    }
+                    for (int q = 0; q < 2; ++q) {
+                        gu[q] = warp_sum(gu[q]);
+                        gv[q] = warp_sum(gv[q]);
+                    }
+                    if (lane == 0) {
+                        if (t < kf)
+                            acc4[0] += gu[0] * gv[0] - gu[1] * gv[1];
+                        else {
+                            acc4[1] += gu[0];
+                            acc4[2] += gv[0];
+                        }
+                    }
+                }
+                block_sum<3>(acc4, S.redd);
+                normS2 += 2.0 * acc4[0] + acc4[1] * acc4[2];
+                ++kf;
+                if (sqrt(acc4[1] * acc4[2]) <= p.eps_aca * sqrt(normS2)) {
+                    converged = true;
+                    break;
+                }
+                if (am2.i == 0x7fffffff || am2.v < 0.0) {
+                    converged = true;
+                    break;
+                }
+                istar = am2.i;
+            }
+            if (!converged && tid == 0) atomicOr(o.dev_flags, TD_DEV_RANK_CAP);
+            // ------------------------------------------------ pivot on the rebuilt face
+            ArgMaxD am = {-1.0, 0x7fffffff};
+            const int64_t nIJ = (int64_t)nI * nJ;
+            for (int64_t e = tid; e < nIJ; e += blockDim.x) {
+                const int i = (int)(e / nJ), j = (int)(e % nJ);
+                cx<T> h = {0, 0};
+                for (int t = 0; t < kf; ++t) cfma(h, Uw[(int64_t)t * a.maxI + i], Vw[(int64_t)t * a.maxJ + j]);
+                double av = (double)h.x * h.x + (double)h.y * h.y;
+                if (am_better(av, (int)e, am.v, am.i)) am = {av, (int)e};
+            }
+            am = block_argmax(am, S.red);
+            if (!(am.v > 0.0) || kf == 0) {
+                r = l;
+                break;
+            }
+            const int ip = am.i / nJ, jp = am.i % nJ;
+            if (tid == 0) {
+                cx<T> h = {0, 0};
+                for (int t = 0; t < kf; ++t) cfma(h, Uw[(int64_t)t * a.maxI + ip], Vw[(int64_t)t * a.maxJ + jp]);
+                S.piv = h;
+            }
+            // previous faces at the pivot
+            for (int d = tid; d < l; d += blockDim.x) {
+                const cx<T> *Ud = pool + S.foff[d];
+                const cx<T> *Vd = Ud + (int64_t)S.frank[d] * nI;
+                cx<T> h = {0, 0};
+                for (int t = 0; t < S.frank[d]; ++t) cfma(h, Ud[(int64_t)t * nI + ip], Vd[(int64_t)t * nJ + jp]);
+                S.hd[d] = h;
+            }
+            __syncthreads();
+            const cx<T> piv = S.piv;
+            // tube over all unique frequencies, one warp per frequency
+            for (int kk = wid; kk < Nu; kk += nwarps) {
+                cx<T> v = warp_entry<T, OP>(m, rows[ip], cols[jp], (T)a.sig[2 * kk], (T)a.sig[2 * kk + 1]);
+                if (lane == 0) {
+                    for (int d = 0; d < l; ++d) cfms(v, S.hd[d], fib[(tb + d) * Nu + kk]);
+                    S.fl[kk] = cdiv(v, piv);
+                }
+            }
+            ev_tube += Nu;
+            for (int d = tid; d <= l; d += blockDim.x) S.gH[d] = {0.0, 0.0};
+            __syncthreads();
+            // eq. norm (FP64): <H_l, H_d> = sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>
+            {
+                int npairs = 0;
+                for (int d = 0; d <= l; ++d) npairs += kf * (d < l ? S.frank[d] : kf);
+                for (int pr = wid; pr < npairs; pr += nwarps) {
+                    int rem = pr, d = 0;
+                    while (true) {
+                        const int kd = d < l ? S.frank[d] : kf;
+                        if (rem < kf * kd) break;
+                        rem -= kf * kd;
+                        ++d;
+                    }
+                    const int kd = d < l ? S.frank[d] : kf;
+                    const int t = rem / kd, tau = rem % kd;
+                    const cx<T> *Ud, *Vd;
+                    int64_t su, sv;
+                    if (d < l) {
+                        Ud = pool + S.foff[d];
+                        Vd = Ud + (int64_t)S.frank[d] * nI;
+                        su = nI;
+                        sv = nJ;
+                    } else {
+                        Ud = Uw;
+                        Vd = Vw;
+                        su = a.maxI;
+                        sv = a.maxJ;
+                    }
+                    double gu[2] = {0, 0}, gv[2] = {0, 0};
+                    for (int i = lane; i < nI; i += 32) {
+                        c64 x = ccast<double>(Uw[(int64_t)t * a.maxI + i]), y = ccast<double>(Ud[tau * su + i]);
+                        gu[0] += x.x * y.x + x.y * y.y;
+                        gu[1] += x.y * y.x - x.x * y.y;
+                    }
+                    for (int j = lane; j < nJ; j += 32) {
+                        c64 x = ccast<double>(Vw[(int64_t)t * a.maxJ + j]), y = ccast<double>(Vd[tau * sv + j]);
+                        gv[0] += x.x * y.x + x.y * y.y;
+                        gv[1] += x.y * y.x - x.x * y.y;
+                    }
+                    for (int q = 0; q < 2; ++q) {
+                        gu[q] = warp_sum(gu[q]);
+                        gv[q] = warp_sum(gv[q]);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&S.gH[d].x, gu[0] * gv[0] - gu[1] * gv[1]);
+                        atomicAdd(&S.gH[d].y, gu[0] * gv[1] + gu[1] * gv[0]);
+                    }
+                }
+            }
+            __syncthreads();
+            double fl2 = 0.0, cross = 0.0;
+            for (int kk = 0; kk < Nu; ++kk) fl2 += cabs2(ccast<double>(S.fl[kk]));
+            for (int d = 0; d < l; ++d) {
+                c64 gf = {0.0, 0.0};
+                for (int kk = 0; kk < Nu; ++kk)
+                    gf = gf + ccast<double>(S.fl[kk]) * cconj(ccast<double>(fib[(tb + d) * Nu + kk]));
+                cross += S.gH[d].x * gf.x - S.gH[d].y * gf.y;
+            }
+            const double hl2 = S.gH[l].x;
+            normC2 += 2.0 * cross + hl2 * fl2;
+            if (sqrt(fabs(hl2) * fl2) <= p.eps * sqrt(normC2)) {
+                r = l;
+                break;
+            }
+            // ------------------------------------------------ keep term l
+            const int64_t need = (int64_t)kf * (nI + nJ);
+            if (tid == 0) {
+                unsigned long long off = atomicAdd(o.face_used, (unsigned long long)need);
+                if ((int64_t)(off + need) > o.face_cap) {
+                    atomicOr(o.dev_flags, TD_DEV_POOL_OVERFLOW);
+                    S.off = -1;
+                } else {
+                    S.off = (long long)off;
+                }
+            }
+            __syncthreads();
+            const long long off = S.off;
+            if (off < 0) {
+                r = l;
+                break;
+            }
+            for (int64_t e = tid; e < (int64_t)kf * nI; e += blockDim.x)
+                pool[off + e] = Uw[(e / nI) * a.maxI + e % nI];
+            for (int64_t e = tid; e < (int64_t)kf * nJ; e += blockDim.x)
+                pool[off + (int64_t)kf * nI + e] = Vw[(e / nJ) * a.maxJ + e % nJ];
+            for (int kk = tid; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = S.fl[kk];
+            if (tid == 0) {
+                o.kpiv[tb + l] = k;
+                o.frank[tb + l] = kf;
+                o.foff[tb + l] = off;
+                S.frank[l] = kf;
+                S.foff[l] = off;
+            }
+            S.sel[k] = 1;
+            __syncthreads();
+            ++l;
+            int kn = -1;
+            double best = -1.0;
+            for (int kk = 0; kk < Nu; ++kk) {
+                if (S.sel[kk]) continue;
+                double v = cabs2(ccast<double>(S.fl[kk]));
+                if (v > best) {
+                    best = v;
+                    kn = kk;
+                }
+            }
+            if (kn < 0) {
+                r = l;
+                break;
+            }
+            k = kn;
+            __syncthreads();
+        }
+        if (r < 0) r = l;
+        if (tid == 0) o.rank[b] = r;
+        __syncthreads();
+    }
+    if (tid == 0 && a.evals) {
+        atomicAdd((unsigned long long *)&a.evals[0], (unsigned long long)ev_reg);
+        atomicAdd((unsigned long long *)&a.evals[1], (unsigned long long)ev_tube);
+    }
+}
+
+}  // namespace
+
+int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const TensorOut &o,
+                       const AcaParams &p, void *scratch, int64_t sper, int nctas) {
+    if (a.nnear == 0) return 0;
+    if (prec == TDBEM_FP64)
+        k_near_aca<double><<<nctas, 128, 0, st>>>(a, o, p, (c64 *)scratch, sper);
+    else
+        k_near_aca<float><<<nctas, 128, 0, st>>>(a, o, p, (c32 *)scratch, sper);
+    return (int)cudaGetLastError();
+}
+
+template <class T, int OP>
+static int launch_far(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
+                      const AcaParams &p, int nctas) {
+    size_t sm = sizeof(FarShared<T>) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
+    cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    k_far_aca<T, OP><<<nctas, kNT, sm, st>>>(m, a, o, p);
+    return (int)cudaGetLastError();
+}
+
+int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
+                      const TensorOut &o, const AcaParams &p, int nctas) {
+    if (a.nfar == 0) return 0;
+    if (prec == TDBEM_FP64)
+        return op == TD_SLP ? launch_far<double, TD_SLP>(st, m, a, o, p, nctas)
+                            : launch_far<double, TD_DLP>(st, m, a, o, p, nctas);
+    return op == TD_SLP ? launch_far<float, TD_SLP>(st, m, a, o, p, nctas)
+                        : launch_far<float, TD_DLP>(st, m, a, o, p, nctas);
+}

@@ -1,0 +1,368 @@
+// Entry kernels (Sec. 3; the ENTRY function of Algorithm 1):
+//   k_entries_generic : arbitrary rows x cols x frequencies (C-ABI tdbem_entries)
+//   k_sing_table      : touching pairs (Sauter-Schwab, FP64) at all unique
+//                       frequencies, one warp per pair
+//   k_near_entries    : every entry of every near-field block at all unique
+//                       frequencies; regular pairs in the block precision with
+//                       the quadrature geometry shared across frequencies,
+//                       touching pairs read from the table.
+#include "internal.h"
+#include "kernels.h"
+#include "pair.cuh"
+
+namespace {
+
+// ---- generic entries --------------------------------------------------------
+template <class T> struct Prec;
+template <> struct Prec<float> {
+    using Tri = TriF;
+    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trif(m, t, X); }
+    template <int OP>
+    TD_D static void pair(const Tri &X, const Tri &Y, float sr, float si, c32 *o) {
+        pair_reg_f32<OP>(X, Y, sr, si, o);
+    }
+};
+template <> struct Prec<double> {
+    using Tri = TriD;
+    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trid(m, t, X); }
+    template <int OP>
+    TD_D static void pair(const Tri &X, const Tri &Y, double sr, double si, c64 *o) {
+        pair_reg_f64<OP>(X, Y, sr, si, o);
+    }
+};
+
+// One entry A[row, col](sigma) (sigma = s/c), scaled by 1/(4 pi).
+template <class T, int OP>
+TD_D cx<T> entry_one(const MeshDev &m, int row, int col, double sr, double si) {
+    using P = Prec<T>;
+    typename P::Tri X, Y;
+    P::load(m, row, X);
+    cx<T> acc = {0, 0};
+    c64 accs = {0.0, 0.0};
+    if (OP == TD_SLP) {
+        if (touching_slot(m, row, col) >= 0) {
+            c64 o[3] = {};
+            pair_singular_f64<TD_SLP>(m, row, col, sr, si, o);
+            accs = o[0];
+        } else {
+            P::load(m, col, Y);
+            cx<T> o[3] = {};
+            P::template pair<TD_SLP>(X, Y, (T)sr, (T)si, o);
+            acc = o[0];
+        }
+    } else {
+        for (int p = m.v2t_ptr[col]; p < m.v2t_ptr[col + 1]; ++p) {
+            int e = m.v2t[p], l = m.v2t_loc[p];
+            if (touching_slot(m, row, e) >= 0) {
+                c64 o[3] = {};
+                pair_singular_f64<TD_DLP>(m, row, e, sr, si, o);
+                accs = accs + o[l];
+            } else {
+                P::load(m, e, Y);
+                cx<T> o[3] = {};
+                P::template pair<TD_DLP>(X, Y, (T)sr, (T)si, o);
+                acc = acc + o[l];
+            }
+        }
+    }
+    const double inv4pi = 1.0 / TD_FOUR_PI;
+    return cx<T>{(T)(((double)acc.x + accs.x) * inv4pi), (T)(((double)acc.y + accs.y) * inv4pi)};
+}
+
+template <class T, int OP>
+__global__ void k_entries_generic(MeshDev m, const double *sig, int nq, const int *rows, int64_t nr,
+                                  const int *cols, int64_t nc, const int *fidx, int64_t nf,
+                                  cx<T> *out) {
+    int64_t n = nr * nc * nf;
+    const int ncols = OP == TD_SLP ? m.nt : m.nv;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = t % nc, r = (t / nc) % nr, f = t / (nc * nr);
+        const int k = fidx[f], row = rows[r], col = cols[c];
+        if (k < 0 || k >= nq || row < 0 || row >= m.nt || col < 0 || col >= ncols) {
+            out[t] = cx<T>{(T)NAN, (T)NAN};  // invalid index: no access, NaN result
+            continue;
+        }
+        out[t] = entry_one<T, OP>(m, row, col, sig[2 * k], sig[2 * k + 1]);
+    }
+}
+
+// ---- touching-pair table ----------------------------------------------------
+// table layout: [slot][nf][3] complex128 (SLP uses component 0), 1/(4 pi) applied.
+template <int OP, int FC>
+__global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npairs,
+                             const double *sig, int nf, c64 *table) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int p = warp; p < npairs; p += nwarps) {
+        int ti = pti[p], tj = ptj[p];
+        if (OP == TD_SLP && ti > tj) {
+            int t = ti;
+            ti = tj;
+            tj = t;
+        }
+        SingGeom G;
+        classify_pair(m, ti, tj, G);
+        const int nq = ss_npoints(G.cls, m.ng);
+        const bool zero = (OP == TD_DLP && G.cls == 3) || G.cls == 0;
+        for (int f0 = 0; f0 < nf; f0 += FC) {
+            c64 acc[FC][3];
+#pragma unroll
+            for (int j = 0; j < FC; ++j)
+                for (int k = 0; k < 3; ++k) acc[j][k] = {0.0, 0.0};
+            if (!zero) {
+                for (int q = lane; q < nq; q += 32) {
+                    double d[3], w, lam[3];
+                    ss_point(G, q, m.ng, m.gx, m.gw, d, w, lam);
+                    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    double base, pre;
+                    if (OP == TD_SLP) {
+                        base = w / r;
+                    } else {
+                        double dn = -(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]);
+                        base = w * dn / (r * r * r);
+                    }
+                    (void)pre;
+#pragma unroll
+                    for (int j = 0; j < FC; ++j) {
+                        if (f0 + j < nf) {
+                            double sr = sig[2 * (f0 + j)], si = sig[2 * (f0 + j) + 1];
+                            c64 e = expm_sr(sr, si, r);
+                            if (OP == TD_SLP) {
+                                acc[j][0].x += base * e.x;
+                                acc[j][0].y += base * e.y;
+                            } else {
+                                double pr = 1.0 + sr * r, pi = si * r;
+                                c64 v = {base * (pr * e.x - pi * e.y), base * (pr * e.y + pi * e.x)};
+#pragma unroll
+                                for (int k = 0; k < 3; ++k) {
+                                    acc[j][k].x += lam[k] * v.x;
+                                    acc[j][k].y += lam[k] * v.y;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            const double inv4pi = 1.0 / TD_FOUR_PI;
+#pragma unroll
+            for (int j = 0; j < FC; ++j) {
+                c64 outv[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    outv[k] = {warp_sum(acc[j][k].x) * inv4pi, warp_sum(acc[j][k].y) * inv4pi};
+                if (lane == 0 && f0 + j < nf) {
+                    c64 *o = table + ((int64_t)p * nf + f0 + j) * 3;
+                    if (OP == TD_SLP) {
+                        o[0] = outv[0];
+                        o[1] = o[2] = {0.0, 0.0};
+                    } else {
+                        // parametrisation order -> mesh-local trial vertex
+                        c64 z = {0.0, 0.0};
+                        o[0] = o[1] = o[2] = z;
+                        for (int k = 0; k < 3; ++k) o[G.loc[k]] = zero ? z : outv[k];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---- near-field dense entries -------------------------------------------------
+// Regular pair at FC frequencies with the geometry computed once per point pair.
+template <int OP, int FC>
+TD_D void pair_multi_f32(const TriF &X, const TriF &Y, const float *sg, int nfc, c32 *acc, int loc) {
+#pragma unroll 1
+    for (int b = 0; b < 7; ++b) {
+        float yxh = Y.xh[b], yyh = Y.yh[b], yzh = Y.zh[b];
+        float yxl = Y.xl[b], yyl = Y.yl[b], yzl = Y.zl[b];
+        float wyb = Y.w[b] * (OP == TD_DLP ? bary7f(b, loc) : 1.0f);
+#pragma unroll 1
+        for (int a = 0; a < 7; ++a) {
+            float dx = (yxh - X.xh[a]) + (yxl - X.xl[a]);
+            float dy = (yyh - X.yh[a]) + (yyl - X.yl[a]);
+            float dz = (yzh - X.zh[a]) + (yzl - X.zl[a]);
+            float r2 = dx * dx + dy * dy + dz * dz;
+            float rinv = rsqrtf(r2);
+            float r = r2 * rinv;
+            float w = X.w[a] * wyb * rinv;
+            if (OP == TD_DLP) w *= -(dx * Y.nx + dy * Y.ny + dz * Y.nz) * rinv * rinv;
+#pragma unroll
+            for (int j = 0; j < FC; ++j) {
+                if (j < nfc) {
+                    float sr = sg[2 * j], si = sg[2 * j + 1];
+                    c32 e = expm_sr(sr, si, r);
+                    if (OP == TD_SLP) {
+                        acc[j].x = fmaf(w, e.x, acc[j].x);
+                        acc[j].y = fmaf(w, e.y, acc[j].y);
+                    } else {
+                        float pr = fmaf(sr, r, 1.0f), pi = si * r;
+                        acc[j].x = fmaf(w, pr * e.x - pi * e.y, acc[j].x);
+                        acc[j].y = fmaf(w, pr * e.y + pi * e.x, acc[j].y);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int OP, int FC>
+TD_D void pair_multi_f64(const TriD &X, const TriD &Y, const double *sg, int nfc, c64 *acc, int loc) {
+#pragma unroll 1
+    for (int b = 0; b < 7; ++b) {
+        double yx = Y.x[b], yy = Y.y[b], yz = Y.z[b];
+        double wyb = Y.w[b] * (OP == TD_DLP ? bary7d(b, loc) : 1.0);
+#pragma unroll 1
+        for (int a = 0; a < 7; ++a) {
+            double dx = yx - X.x[a], dy = yy - X.y[a], dz = yz - X.z[a];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double w = X.w[a] * wyb / r;
+            if (OP == TD_DLP) w *= -(dx * Y.nx + dy * Y.ny + dz * Y.nz) / (r * r);
+#pragma unroll
+            for (int j = 0; j < FC; ++j) {
+                if (j < nfc) {
+                    double sr = sg[2 * j], si = sg[2 * j + 1];
+                    c64 e = expm_sr(sr, si, r);
+                    if (OP == TD_SLP) {
+                        acc[j].x += w * e.x;
+                        acc[j].y += w * e.y;
+                    } else {
+                        double pr = 1.0 + sr * r, pi = si * r;
+                        acc[j].x += w * (pr * e.x - pi * e.y);
+                        acc[j].y += w * (pr * e.y + pi * e.x);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <class T> struct Multi;
+template <> struct Multi<float> {
+    template <int OP, int FC>
+    TD_D static void run(const TriF &X, const TriF &Y, const float *sg, int nfc, c32 *acc, int loc) {
+        pair_multi_f32<OP, FC>(X, Y, sg, nfc, acc, loc);
+    }
+};
+template <> struct Multi<double> {
+    template <int OP, int FC>
+    TD_D static void run(const TriD &X, const TriD &Y, const double *sg, int nfc, c64 *acc, int loc) {
+        pair_multi_f64<OP, FC>(X, Y, sg, nfc, acc, loc);
+    }
+};
+
+// near[noff[b] + (k * nI + i) * nJ + j] for every near block b (list nb_idx),
+// all nf unique frequencies.  Entry e of the flattened list belongs to the
+// near block found by binary search in the prefix `eprefix` (entries per block).
+template <class T, int OP, int FC>
+__global__ void __launch_bounds__(128) k_near_entries(MeshDev m, NearArgs a, const c64 *table) {
+    __shared__ T sg[2 * 256];
+    const int nf = a.nf;  // <= 256 (checked by the caller)
+    for (int i = threadIdx.x; i < 2 * nf; i += blockDim.x) sg[i] = (T)a.sig[i];
+    __syncthreads();
+    using P = Prec<T>;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.nentries;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        // block lookup
+        int lo = 0, hi = a.nnear - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (a.eprefix[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int nb = lo;
+        const int32_t *bl = a.blocks + 5 * a.near_ids[nb];
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        const int64_t loc_e = t - a.eprefix[nb];
+        const int i = (int)(loc_e / nJ), j = (int)(loc_e % nJ);
+        const int row = a.perm_r[bl[0] + i], col = a.perm_c[bl[2] + j];
+        cx<T> *dst = (cx<T> *)a.near + a.noff[nb] + (int64_t)i * nJ + j;
+        const int64_t fstride = (int64_t)nI * nJ;
+        typename P::Tri X, Y;
+        P::load(m, row, X);
+        const int nsup = OP == TD_SLP ? 1 : m.v2t_ptr[col + 1] - m.v2t_ptr[col];
+        for (int f0 = 0; f0 < nf; f0 += FC) {
+            const int nfc = min(FC, nf - f0);
+            cx<T> acc[FC];
+#pragma unroll
+            for (int jj = 0; jj < FC; ++jj) acc[jj] = {0, 0};
+            c64 sing[FC];
+#pragma unroll
+            for (int jj = 0; jj < FC; ++jj) sing[jj] = {0.0, 0.0};
+            for (int sidx = 0; sidx < nsup; ++sidx) {
+                int e, l;
+                if (OP == TD_SLP) {
+                    e = col;
+                    l = 0;
+                } else {
+                    int p = m.v2t_ptr[col] + sidx;
+                    e = m.v2t[p];
+                    l = m.v2t_loc[p];
+                }
+                int slot = touching_slot(m, row, e);
+                if (slot >= 0) {
+#pragma unroll
+                    for (int jj = 0; jj < FC; ++jj)
+                        if (jj < nfc) sing[jj] = sing[jj] + table[((int64_t)slot * nf + f0 + jj) * 3 + l];
+                } else {
+                    P::load(m, e, Y);
+                    Multi<T>::template run<OP, FC>(X, Y, sg + 2 * f0, nfc, acc, l);
+                }
+            }
+            const T inv4pi = (T)(1.0 / TD_FOUR_PI);
+#pragma unroll
+            for (int jj = 0; jj < FC; ++jj)
+                if (jj < nfc)
+                    dst[(int64_t)(f0 + jj) * fstride] =
+                        cx<T>{(T)(acc[jj].x * inv4pi + (T)sing[jj].x), (T)(acc[jj].y * inv4pi + (T)sing[jj].y)};
+        }
+    }
+}
+
+}  // namespace
+
+// ---- launchers ----------------------------------------------------------------
+int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
+                      const int *rows, int64_t nr, const int *cols, int64_t nc, const int *fidx,
+                      int64_t nf, void *out) {
+    int64_t n = nr * nc * nf;
+    if (n == 0) return 0;
+    int grid = (int)std::min<int64_t>((n + 127) / 128, 152 * 16);
+    if (prec == TDBEM_FP64) {
+        if (op == TD_SLP)
+            k_entries_generic<double, TD_SLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c64 *)out);
+        else
+            k_entries_generic<double, TD_DLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c64 *)out);
+    } else {
+        if (op == TD_SLP)
+            k_entries_generic<float, TD_SLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c32 *)out);
+        else
+            k_entries_generic<float, TD_DLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c32 *)out);
+    }
+    return (int)cudaGetLastError();
+}
+
+int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, const int *pti, const int *ptj,
+                         int npairs, const double *sig, int nf, c64 *table, int num_sms) {
+    if (npairs == 0) return 0;
+    int grid = std::min((npairs + 3) / 4, num_sms * 8);
+    if (op == TD_SLP)
+        k_sing_table<TD_SLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+    else
+        k_sing_table<TD_DLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+    return (int)cudaGetLastError();
+}
+
+int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const NearArgs &a,
+                           const c64 *table, int num_sms) {
+    if (a.nentries == 0) return 0;
+    int grid = (int)std::min<int64_t>((a.nentries + 127) / 128, (int64_t)num_sms * 16);
+    if (prec == TDBEM_FP64) {
+        if (op == TD_SLP) k_near_entries<double, TD_SLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+        else k_near_entries<double, TD_DLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+    } else {
+        if (op == TD_SLP) k_near_entries<float, TD_SLP, 8><<<grid, 128, 0, st>>>(m, a, table);
+        else k_near_entries<float, TD_DLP, 8><<<grid, 128, 0, st>>>(m, a, table);
+    }
+    return (int)cudaGetLastError();
+}

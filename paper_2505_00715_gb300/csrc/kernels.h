@@ -1,0 +1,89 @@
+// Kernel launch interfaces shared by the C-ABI layer and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+struct MeshDev;
+
+struct NearArgs {
+    int nf;                  // unique frequencies
+    const double *sig;       // [2*nf] sigma = s / c
+    int nnear;
+    const int *near_ids;     // block index of near block n
+    const int64_t *eprefix;  // [nnear] prefix of nI*nJ
+    const int64_t *noff;     // [nnear] offset (complex units) into `near`, layout [nf][nI][nJ]
+    const int *blocks;       // [nb][5]
+    const int *perm_r, *perm_c;
+    int64_t nentries;
+    void *near;
+};
+
+// Output arrays of the compressed tensor (fixed slots per block and term).
+struct TensorOut {
+    int Nu;
+    int *rank;          // [nb]
+    int *kpiv;          // [nb][Nu]
+    int *frank;         // [nb][Nu] face rank (-1 dense)
+    int64_t *foff;      // [nb][Nu] offset of the face in the pool (complex units)
+    void *fib;          // [nb][Nu][Nu] complex
+    void *face;         // pool
+    int64_t face_cap;
+    unsigned long long *face_used;
+    int *dev_flags;     // TD_DEV_* bits
+};
+
+struct AcaParams {
+    double eps, eps_aca;
+    int kcap;           // face-rank cap
+};
+
+struct FarArgs {
+    int nfar;
+    const int *far_ids;     // block ids, processing order
+    const int *blocks;
+    const int *perm_r, *perm_c;
+    const double *sig;      // [2*Nu]
+    int nf;
+    int maxI, maxJ;
+    void *scratch;          // per-CTA workspace
+    int64_t scratch_per_cta;  // complex units
+    unsigned int *counter;  // work queue head
+    int64_t *evals;         // [2] regular, tube entries evaluated
+};
+
+int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
+                      const int *rows, int64_t nr, const int *cols, int64_t nc, const int *fidx,
+                      int64_t nf, void *out);
+int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, const int *pti, const int *ptj,
+                         int npairs, const double *sig, int nf, c64 *table, int num_sms);
+int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const NearArgs &a,
+                           const c64 *table, int num_sms);
+int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const TensorOut &o,
+                       const AcaParams &p, void *scratch, int64_t scratch_per_cta, int nctas);
+int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
+                      const TensorOut &o, const AcaParams &p, int nctas);
+int td_launch_bdf2(cudaStream_t st, int N, double dt, double lam, double *ds);
+int td_launch_gcq(cudaStream_t st, int NQ, double dt_min, double q, double *ds, double *dw);
+
+struct ApplyArgs {
+    int nb;
+    const int *blocks;
+    const int *perm_r, *perm_c;
+    int Nu, NQ;
+    const int *qmap;       // [NQ] unique map (rep+1 or -(rep+1))
+    const void *W;         // [NQ][ncols][nrhs]
+    int nrhs;
+    int64_t ncols;
+    void *y;               // [nrows][nrhs]
+    int single_f;          // >= 0: apply one frequency only (W is x [ncols][nrhs])
+    int kcap;              // largest far face rank
+    int max_near_rows;     // largest row count of a near block
+};
+int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorOut &o, int num_sms);
+int td_launch_tensor_entries(cudaStream_t st, int prec, const TensorOut &o, const int *blocks,
+                             int nb, int64_t nrows, int64_t ncols, int nq, const int *inv_r,
+                             const int *inv_c, const int *qmap,
+                             const int *rows, const int *cols, const int *fidx, int64_t count,
+                             void *out);
