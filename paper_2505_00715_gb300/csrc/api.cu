@@ -15,6 +15,7 @@
 #include "pair.cuh"
 
 int td_fail(tdbem_ctx *ctx, int code, const char *fmt, ...) {
+    if (code == TDBEM_ERR_CUDA || code == TDBEM_ERR_OOM) cudaGetLastError();  // clear non-sticky errors
     if (ctx) {
         char buf[1024];
         va_list ap;
@@ -162,11 +163,19 @@ extern "C" int tdbem_ctx_create(int device, void *stream, tdbem_ctx_t *out) {
     c->device = device;
     c->stream = (cudaStream_t)stream;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    // graphs cannot be captured on the legacy default stream: capture on a
+    // private stream and launch the instantiated graph on the caller's stream
+    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TDBEM_ERR_CUDA;
+    }
     *out = c;
     return TDBEM_OK;
 }
 
 extern "C" int tdbem_ctx_destroy(tdbem_ctx_t ctx) {
+    if (ctx && ctx->capture) cudaStreamDestroy(ctx->capture);
     delete ctx;
     return TDBEM_OK;
 }
@@ -336,6 +345,7 @@ int finish_freqs(tdbem_ctx *ctx, tdbem_freqs *f) {
 }  // namespace
 
 extern "C" int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double lambda, tdbem_freqs_t *out) {
+    cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
     if (!ctx || !out || N < 1 || N > 65536 || !(dt > 0.0) || !std::isfinite(dt) || lambda >= 1.0)
         return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_cq_bdf2: need N >= 1, dt > 0, lambda < 1");
     *out = nullptr;
@@ -365,6 +375,7 @@ extern "C" int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double
 
 extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, double dt_min, double dt_max, int32_t rk, int32_t NQ,
                                tdbem_freqs_t *out) {
+    cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
     if (!ctx || !out || !(dt_min > 0.0) || !(dt_max >= dt_min) || !std::isfinite(dt_max) || NQ < 2 ||
         NQ % 2 || NQ > 65536 || (rk != TDBEM_EULER && rk != TDBEM_RADAU2))
         return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_gcq: need 0 < dt_min <= dt_max, even NQ >= 2, rk EULER|RADAU2");
@@ -453,6 +464,7 @@ extern "C" int tdbem_tree_destroy(tdbem_tree_t t) {
 // ============================================================================
 extern "C" int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const int32_t *rows, int64_t nr,
                              const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf, void *out) {
+    cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
     if (!mesh || !f) return TDBEM_ERR_ARG;
     tdbem_ctx *ctx = mesh->ctx;
     int rc = check_op(ctx, op);
@@ -504,6 +516,7 @@ TensorOut tensor_out(const tdbem_tensor *t, int *flags) {
 
 extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f,
                               tdbem_tree_t tree, const tdbem_aca_cfg *cfg, tdbem_tensor_t *out) {
+    cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
     if (!ctx || !mesh || !f || !tree || !cfg || !out) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_compress: NULL argument");
     *out = nullptr;
     int rc = check_op(ctx, op);
@@ -667,50 +680,50 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         T->dface = face;
         T->face_cap = cap;
         TensorOut o = tensor_out(T, flags);
-        // capture the phases in one graph
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
+        // One captured graph per phase (touching table, near entries, near
+        // 3D-ACA, far 3D-ACA), launched back to back on the caller's stream
+        // with timing events between them.
         const bool use_graph = !(cfg->flags & 1);
-        if (use_graph) TD_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
         int lrc = 0;
-        cudaMemsetAsync(T->dface_used, 0, sizeof(int64_t) * 2, ctx->stream);
-        cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ctx->stream);
-        cudaMemsetAsync(evals, 0, sizeof(int64_t) * 4, ctx->stream);
-        cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ctx->stream);
-        cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ctx->stream);
-        cudaEventRecord(ev[0], ctx->stream);
-        lrc |= td_launch_sing_table(ctx->stream, md, op->op, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
-        cudaEventRecord(ev[1], ctx->stream);
-        lrc |= td_launch_near_entries(ctx->stream, md, op->op, op->prec, na, table, ctx->num_sms);
-        cudaEventRecord(ev[2], ctx->stream);
-        lrc |= td_launch_near_aca(ctx->stream, op->prec, na, o, ap, scr_near, maxIJ, nctas_near);
-        cudaEventRecord(ev[3], ctx->stream);
-        lrc |= td_launch_far_aca(ctx->stream, md, op->op, op->prec, fa, o, ap, nctas_far);
-        cudaEventRecord(ev[4], ctx->stream);
-        if (use_graph) {
-            cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-            if (e != cudaSuccess || lrc) {
+        cudaError_t ge = cudaSuccess;
+        for (int ph = 0; ph < 4 && !lrc && ge == cudaSuccess; ++ph) {
+            cudaStream_t ls = use_graph ? ctx->capture : ctx->stream;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            if (ph == 0) cudaEventRecord(ev[0], ctx->stream);
+            if (use_graph) {
+                ge = cudaStreamBeginCapture(ls, cudaStreamCaptureModeRelaxed);
+                if (ge != cudaSuccess) break;
+            }
+            if (ph == 0) {
+                cudaMemsetAsync(T->dface_used, 0, sizeof(int64_t) * 2, ls);
+                cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ls);
+                cudaMemsetAsync(evals, 0, sizeof(int64_t) * 4, ls);
+                cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ls);
+                cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ls);
+                lrc |= td_launch_sing_table(ls, md, op->op, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
+            } else if (ph == 1) {
+                lrc |= td_launch_near_entries(ls, md, op->op, op->prec, na, table, ctx->num_sms);
+            } else if (ph == 2) {
+                lrc |= td_launch_near_aca(ls, op->prec, na, o, ap, scr_near, maxIJ, nctas_near);
+            } else {
+                lrc |= td_launch_far_aca(ls, md, op->op, op->prec, fa, o, ap, nctas_far);
+            }
+            if (use_graph) {
+                ge = cudaStreamEndCapture(ls, &graph);
+                if (ge == cudaSuccess && !lrc) ge = cudaGraphInstantiate(&exec, graph, 0);
+                if (ge == cudaSuccess && !lrc) ge = cudaGraphLaunch(exec, ctx->stream);
+                if (exec) cudaGraphExecDestroy(exec);  // destruction is deferred until the launch completes
                 if (graph) cudaGraphDestroy(graph);
-                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
-                cudaGetLastError();
-                return fail(td_fail(ctx, TDBEM_ERR_CUDA, "graph capture of the compression failed: %s (launch %d)",
-                                    cudaGetErrorString(e), lrc));
             }
-            e = cudaGraphInstantiate(&exec, graph, 0);
-            if (e == cudaSuccess) e = cudaGraphLaunch(exec, ctx->stream);
-            if (e != cudaSuccess) {
-                if (exec) cudaGraphExecDestroy(exec);
-                cudaGraphDestroy(graph);
-                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
-                return fail(td_fail(ctx, TDBEM_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(e)));
-            }
-        } else if (lrc) {
+            cudaEventRecord(ev[ph + 1], ctx->stream);
+        }
+        if (ge != cudaSuccess || lrc) {
             for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
-            return fail(td_fail(ctx, TDBEM_ERR_CUDA, "kernel launch failed (%d)", lrc));
+            return fail(td_fail(ctx, TDBEM_ERR_CUDA, "compression launch failed: %s (launch status %d)",
+                                cudaGetErrorString(ge), lrc));
         }
         cudaError_t se = cudaStreamSynchronize(ctx->stream);
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
         if (se != cudaSuccess) {
             for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
             return fail(td_fail(ctx, TDBEM_ERR_CUDA, "compression kernels failed: %s", cudaGetErrorString(se)));
@@ -725,7 +738,11 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         return fail(td_fail(ctx, TDBEM_ERR_CAPACITY, "face pool overflow after retries"));
     }
     float ms[4] = {0, 0, 0, 0};
-    for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            ms[k] = -1.0f;
+        }
     for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
     // ---- host copies of the per-block results and statistics
     T->rank.resize(nb);
@@ -813,6 +830,7 @@ extern "C" int tdbem_tensor_destroy(tdbem_tensor_t t) {
 // ============================================================================
 namespace {
 int apply_impl(tdbem_tensor *t, const void *W, int nrhs, void *y, int single_f) {
+    cudaGetLastError();
     tdbem_ctx *ctx = t->ctx;
     if (nrhs < 1 || nrhs > 64 || !W || !y) return td_fail(ctx, TDBEM_ERR_ARG, "apply: need 1 <= nrhs <= 64 and non-NULL buffers");
     const size_t es = t->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);

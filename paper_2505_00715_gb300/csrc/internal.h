@@ -11,6 +11,7 @@
 struct tdbem_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;  // side stream used only to capture graphs
     std::string err;
     int num_sms = 0;
 };

@@ -156,38 +156,18 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
 // ============================================================================
 // Far field
 // ============================================================================
-template <class T> struct FarTri;
-template <> struct FarTri<float> {
-    using Tri = TriF;
-    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trif(m, t, X); }
-    template <int OP> TD_D static void pair(const Tri &X, const Tri &Y, float sr, float si, c32 *o) {
-        pair_reg_f32<OP>(X, Y, sr, si, o);
-    }
-};
-template <> struct FarTri<double> {
-    using Tri = TriD;
-    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trid(m, t, X); }
-    template <int OP> TD_D static void pair(const Tri &X, const Tri &Y, double sr, double si, c64 *o) {
-        pair_reg_f64<OP>(X, Y, sr, si, o);
-    }
-};
-
 // Regular entry A[row, col] (no touching pairs in far blocks), 1/(4 pi) applied.
 template <class T, int OP>
-TD_D cx<T> far_entry(const MeshDev &m, const typename FarTri<T>::Tri &X, int col, T sr, T si) {
-    using F = FarTri<T>;
-    typename F::Tri Y;
+TD_D cx<T> far_entry(const MeshDev &m, const typename Reg<T>::Test &X, int col, T sr, T si) {
     cx<T> acc = {0, 0};
     if (OP == TD_SLP) {
-        F::load(m, col, Y);
         cx<T> o[3] = {};
-        F::template pair<TD_SLP>(X, Y, sr, si, o);
+        Reg<T>::template pair<TD_SLP>(X, m, col, sr, si, o);
         acc = o[0];
     } else {
         for (int p = m.v2t_ptr[col]; p < m.v2t_ptr[col + 1]; ++p) {
-            F::load(m, m.v2t[p], Y);
             cx<T> o[3] = {};
-            F::template pair<TD_DLP>(X, Y, sr, si, o);
+            Reg<T>::template pair<TD_DLP>(X, m, m.v2t[p], sr, si, o);
             acc = acc + o[m.v2t_loc[p]];
         }
     }
@@ -198,8 +178,8 @@ TD_D cx<T> far_entry(const MeshDev &m, const typename FarTri<T>::Tri &X, int col
 // Column-fibre entry: test triangle per thread, trial DOF fixed.
 template <class T, int OP>
 TD_D cx<T> far_entry_col(const MeshDev &m, int row, int col, T sr, T si) {
-    typename FarTri<T>::Tri X;
-    FarTri<T>::load(m, row, X);
+    typename Reg<T>::Test X;
+    load_test(m, row, X);
     return far_entry<T, OP>(m, X, col, sr, si);
 }
 
@@ -356,8 +336,8 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
             while (kf < p.kcap && guard < nI + p.kcap) {
                 ++guard;
                 // row fibre at istar
-                typename FarTri<T>::Tri X;
-                FarTri<T>::load(m, rows[istar], X);
+                typename Reg<T>::Test X;
+                load_test(m, rows[istar], X);
                 ArgMaxD am = {-1.0, 0x7fffffff};
                 int total = 0;
                 // entries first (kept in Vw[kf]), then residual corrections in chunks

@@ -13,30 +13,12 @@
 namespace {
 
 // ---- generic entries --------------------------------------------------------
-template <class T> struct Prec;
-template <> struct Prec<float> {
-    using Tri = TriF;
-    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trif(m, t, X); }
-    template <int OP>
-    TD_D static void pair(const Tri &X, const Tri &Y, float sr, float si, c32 *o) {
-        pair_reg_f32<OP>(X, Y, sr, si, o);
-    }
-};
-template <> struct Prec<double> {
-    using Tri = TriD;
-    TD_D static void load(const MeshDev &m, int t, Tri &X) { load_trid(m, t, X); }
-    template <int OP>
-    TD_D static void pair(const Tri &X, const Tri &Y, double sr, double si, c64 *o) {
-        pair_reg_f64<OP>(X, Y, sr, si, o);
-    }
-};
-
 // One entry A[row, col](sigma) (sigma = s/c), scaled by 1/(4 pi).
 template <class T, int OP>
 TD_D cx<T> entry_one(const MeshDev &m, int row, int col, double sr, double si) {
-    using P = Prec<T>;
-    typename P::Tri X, Y;
-    P::load(m, row, X);
+    using R = Reg<T>;
+    typename R::Test X;
+    load_test(m, row, X);
     cx<T> acc = {0, 0};
     c64 accs = {0.0, 0.0};
     if (OP == TD_SLP) {
@@ -45,9 +27,8 @@ TD_D cx<T> entry_one(const MeshDev &m, int row, int col, double sr, double si) {
             pair_singular_f64<TD_SLP>(m, row, col, sr, si, o);
             accs = o[0];
         } else {
-            P::load(m, col, Y);
             cx<T> o[3] = {};
-            P::template pair<TD_SLP>(X, Y, (T)sr, (T)si, o);
+            R::template pair<TD_SLP>(X, m, col, (T)sr, (T)si, o);
             acc = o[0];
         }
     } else {
@@ -58,9 +39,8 @@ TD_D cx<T> entry_one(const MeshDev &m, int row, int col, double sr, double si) {
                 pair_singular_f64<TD_DLP>(m, row, e, sr, si, o);
                 accs = accs + o[l];
             } else {
-                P::load(m, e, Y);
                 cx<T> o[3] = {};
-                P::template pair<TD_DLP>(X, Y, (T)sr, (T)si, o);
+                R::template pair<TD_DLP>(X, m, e, (T)sr, (T)si, o);
                 acc = acc + o[l];
             }
         }
@@ -170,34 +150,42 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
 }
 
 // ---- near-field dense entries -------------------------------------------------
-// Regular pair at FC frequencies with the geometry computed once per point pair.
+// Regular pair at FC frequencies with the geometry computed once per point
+// pair (test triangle in registers, trial points streamed from the tables).
 template <int OP, int FC>
-TD_D void pair_multi_f32(const TriF &X, const TriF &Y, const float *sg, int nfc, c32 *acc, int loc) {
+TD_D void pair_multi(const TestF &X, const MeshDev &m, int tj, const float *sg, int nfc, c32 *acc, int loc) {
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (OP == TD_DLP) {
+        nx = m.n32[tj];
+        ny = m.n32[m.nt + tj];
+        nz = m.n32[2 * m.nt + tj];
+    }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
-        float yxh = Y.xh[b], yyh = Y.yh[b], yzh = Y.zh[b];
-        float yxl = Y.xl[b], yyl = Y.yl[b], yzl = Y.zl[b];
-        float wyb = Y.w[b] * (OP == TD_DLP ? bary7f(b, loc) : 1.0f);
-#pragma unroll 1
+        const int ob = b * m.nt + tj;
+        const float yxh = m.qxh[ob], yyh = m.qyh[ob], yzh = m.qzh[ob];
+        const float yxl = m.qxl[ob], yyl = m.qyl[ob], yzl = m.qzl[ob];
+        const float wyb = m.qw32[ob] * (OP == TD_DLP ? bary7f(b, loc) : 1.0f);
+#pragma unroll
         for (int a = 0; a < 7; ++a) {
-            float dx = (yxh - X.xh[a]) + (yxl - X.xl[a]);
-            float dy = (yyh - X.yh[a]) + (yyl - X.yl[a]);
-            float dz = (yzh - X.zh[a]) + (yzl - X.zl[a]);
-            float r2 = dx * dx + dy * dy + dz * dz;
-            float rinv = rsqrtf(r2);
-            float r = r2 * rinv;
+            const float dx = (yxh - X.xh[a]) + (yxl - X.xl[a]);
+            const float dy = (yyh - X.yh[a]) + (yyl - X.yl[a]);
+            const float dz = (yzh - X.zh[a]) + (yzl - X.zl[a]);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
             float w = X.w[a] * wyb * rinv;
-            if (OP == TD_DLP) w *= -(dx * Y.nx + dy * Y.ny + dz * Y.nz) * rinv * rinv;
+            if (OP == TD_DLP) w *= -(dx * nx + dy * ny + dz * nz) * rinv * rinv;
 #pragma unroll
             for (int j = 0; j < FC; ++j) {
                 if (j < nfc) {
-                    float sr = sg[2 * j], si = sg[2 * j + 1];
-                    c32 e = expm_sr(sr, si, r);
+                    const float sr = sg[2 * j], si = sg[2 * j + 1];
+                    const c32 e = expm_sr(sr, si, r);
                     if (OP == TD_SLP) {
                         acc[j].x = fmaf(w, e.x, acc[j].x);
                         acc[j].y = fmaf(w, e.y, acc[j].y);
                     } else {
-                        float pr = fmaf(sr, r, 1.0f), pi = si * r;
+                        const float pr = fmaf(sr, r, 1.0f), pi = si * r;
                         acc[j].x = fmaf(w, pr * e.x - pi * e.y, acc[j].x);
                         acc[j].y = fmaf(w, pr * e.y + pi * e.x, acc[j].y);
                     }
@@ -208,27 +196,34 @@ TD_D void pair_multi_f32(const TriF &X, const TriF &Y, const float *sg, int nfc,
 }
 
 template <int OP, int FC>
-TD_D void pair_multi_f64(const TriD &X, const TriD &Y, const double *sg, int nfc, c64 *acc, int loc) {
+TD_D void pair_multi(const TestD &X, const MeshDev &m, int tj, const double *sg, int nfc, c64 *acc, int loc) {
+    double nx = 0.0, ny = 0.0, nz = 0.0;
+    if (OP == TD_DLP) {
+        nx = m.n64[tj];
+        ny = m.n64[m.nt + tj];
+        nz = m.n64[2 * m.nt + tj];
+    }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
-        double yx = Y.x[b], yy = Y.y[b], yz = Y.z[b];
-        double wyb = Y.w[b] * (OP == TD_DLP ? bary7d(b, loc) : 1.0);
+        const int ob = b * m.nt + tj;
+        const double yx = m.qx[ob], yy = m.qy[ob], yz = m.qz[ob];
+        const double wyb = m.qw[ob] * (OP == TD_DLP ? bary7d(b, loc) : 1.0);
 #pragma unroll 1
         for (int a = 0; a < 7; ++a) {
-            double dx = yx - X.x[a], dy = yy - X.y[a], dz = yz - X.z[a];
-            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            const double dx = yx - X.x[a], dy = yy - X.y[a], dz = yz - X.z[a];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
             double w = X.w[a] * wyb / r;
-            if (OP == TD_DLP) w *= -(dx * Y.nx + dy * Y.ny + dz * Y.nz) / (r * r);
+            if (OP == TD_DLP) w *= -(dx * nx + dy * ny + dz * nz) / (r * r);
 #pragma unroll
             for (int j = 0; j < FC; ++j) {
                 if (j < nfc) {
-                    double sr = sg[2 * j], si = sg[2 * j + 1];
-                    c64 e = expm_sr(sr, si, r);
+                    const double sr = sg[2 * j], si = sg[2 * j + 1];
+                    const c64 e = expm_sr(sr, si, r);
                     if (OP == TD_SLP) {
                         acc[j].x += w * e.x;
                         acc[j].y += w * e.y;
                     } else {
-                        double pr = 1.0 + sr * r, pi = si * r;
+                        const double pr = 1.0 + sr * r, pi = si * r;
                         acc[j].x += w * (pr * e.x - pi * e.y);
                         acc[j].y += w * (pr * e.y + pi * e.x);
                     }
@@ -237,20 +232,6 @@ TD_D void pair_multi_f64(const TriD &X, const TriD &Y, const double *sg, int nfc
         }
     }
 }
-
-template <class T> struct Multi;
-template <> struct Multi<float> {
-    template <int OP, int FC>
-    TD_D static void run(const TriF &X, const TriF &Y, const float *sg, int nfc, c32 *acc, int loc) {
-        pair_multi_f32<OP, FC>(X, Y, sg, nfc, acc, loc);
-    }
-};
-template <> struct Multi<double> {
-    template <int OP, int FC>
-    TD_D static void run(const TriD &X, const TriD &Y, const double *sg, int nfc, c64 *acc, int loc) {
-        pair_multi_f64<OP, FC>(X, Y, sg, nfc, acc, loc);
-    }
-};
 
 // near[noff[b] + (k * nI + i) * nJ + j] for every near block b (list nb_idx),
 // all nf unique frequencies.  Entry e of the flattened list belongs to the
@@ -261,7 +242,6 @@ __global__ void __launch_bounds__(128) k_near_entries(MeshDev m, NearArgs a, con
     const int nf = a.nf;  // <= 256 (checked by the caller)
     for (int i = threadIdx.x; i < 2 * nf; i += blockDim.x) sg[i] = (T)a.sig[i];
     __syncthreads();
-    using P = Prec<T>;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.nentries;
          t += (int64_t)gridDim.x * blockDim.x) {
         // block lookup
@@ -278,8 +258,8 @@ __global__ void __launch_bounds__(128) k_near_entries(MeshDev m, NearArgs a, con
         const int row = a.perm_r[bl[0] + i], col = a.perm_c[bl[2] + j];
         cx<T> *dst = (cx<T> *)a.near + a.noff[nb] + (int64_t)i * nJ + j;
         const int64_t fstride = (int64_t)nI * nJ;
-        typename P::Tri X, Y;
-        P::load(m, row, X);
+        typename Reg<T>::Test X;
+        load_test(m, row, X);
         const int nsup = OP == TD_SLP ? 1 : m.v2t_ptr[col + 1] - m.v2t_ptr[col];
         for (int f0 = 0; f0 < nf; f0 += FC) {
             const int nfc = min(FC, nf - f0);
@@ -305,8 +285,7 @@ __global__ void __launch_bounds__(128) k_near_entries(MeshDev m, NearArgs a, con
                     for (int jj = 0; jj < FC; ++jj)
                         if (jj < nfc) sing[jj] = sing[jj] + table[((int64_t)slot * nf + f0 + jj) * 3 + l];
                 } else {
-                    P::load(m, e, Y);
-                    Multi<T>::template run<OP, FC>(X, Y, sg + 2 * f0, nfc, acc, l);
+                    pair_multi<OP, FC>(X, m, e, sg + 2 * f0, nfc, acc, l);
                 }
             }
             const T inv4pi = (T)(1.0 / TD_FOUR_PI);

@@ -63,17 +63,19 @@ TD_HD float bary7f(int b, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 regular pairs
+// Regular pairs.  The test triangle's 7 points are held in registers (the
+// loop over them is fully unrolled); the trial triangle's points are read
+// one at a time from the [7][nt] tables (coalesced when threads take
+// different trial triangles, broadcast when they share one).
 // ---------------------------------------------------------------------------
-struct TriF {
+struct TestF {
     float xh[7], yh[7], zh[7], xl[7], yl[7], zl[7], w[7];
-    float nx, ny, nz;
 };
 
-TD_D void load_trif(const MeshDev &m, int t, TriF &T) {
+TD_D void load_test(const MeshDev &m, int t, TestF &T) {
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        int o = q * m.nt + t;
+        const int o = q * m.nt + t;
         T.xh[q] = m.qxh[o];
         T.yh[q] = m.qyh[o];
         T.zh[q] = m.qzh[o];
@@ -82,9 +84,6 @@ TD_D void load_trif(const MeshDev &m, int t, TriF &T) {
         T.zl[q] = m.qzl[o];
         T.w[q] = m.qw32[o];
     }
-    T.nx = m.n32[t];
-    T.ny = m.n32[m.nt + t];
-    T.nz = m.n32[2 * m.nt + t];
 }
 
 // e^{-sigma r} for sigma = (sr, si): returns (ea cos, -ea sin)
@@ -95,45 +94,52 @@ TD_D c32 expm_sr(float sr, float si, float r) {
     return {ea * cs, -ea * sn};
 }
 
-// out (SLP: out[0]; DLP: out[0..2] per trial-local vertex) += pair integral,
-// X = test triangle, Y = trial triangle, sigma = s / c.  Unscaled by 1/(4 pi).
+// out (SLP: out[0]; DLP: out[0..2] per trial-local vertex) += pair integral
+// over test X and trial triangle tj, sigma = s / c.  Unscaled by 1/(4 pi).
 template <int OP>
-TD_D void pair_reg_f32(const TriF &X, const TriF &Y, float sr, float si, c32 *out) {
+TD_D void pair_f32(const TestF &X, const MeshDev &m, int tj, float sr, float si, c32 *out) {
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (OP == TD_DLP) {
+        nx = m.n32[tj];
+        ny = m.n32[m.nt + tj];
+        nz = m.n32[2 * m.nt + tj];
+    }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
-        float yxh = Y.xh[b], yyh = Y.yh[b], yzh = Y.zh[b];
-        float yxl = Y.xl[b], yyl = Y.yl[b], yzl = Y.zl[b];
+        const int ob = b * m.nt + tj;
+        const float yxh = m.qxh[ob], yyh = m.qyh[ob], yzh = m.qzh[ob];
+        const float yxl = m.qxl[ob], yyl = m.qyl[ob], yzl = m.qzl[ob];
+        const float wy = m.qw32[ob];
         c32 acc = {0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 7; ++a) {
-            float dx = (yxh - X.xh[a]) + (yxl - X.xl[a]);
-            float dy = (yyh - X.yh[a]) + (yyl - X.yl[a]);
-            float dz = (yzh - X.zh[a]) + (yzl - X.zl[a]);
-            float r2 = dx * dx + dy * dy + dz * dz;
-            float rinv = rsqrtf(r2);
-            float r = r2 * rinv;
-            c32 e = expm_sr(sr, si, r);
+            const float dx = (yxh - X.xh[a]) + (yxl - X.xl[a]);
+            const float dy = (yyh - X.yh[a]) + (yyl - X.yl[a]);
+            const float dz = (yzh - X.zh[a]) + (yzl - X.zl[a]);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const c32 e = expm_sr(sr, si, r);
             if (OP == TD_SLP) {
-                float w = X.w[a] * rinv;
+                const float w = X.w[a] * rinv;
                 acc.x = fmaf(w, e.x, acc.x);
                 acc.y = fmaf(w, e.y, acc.y);
             } else {
                 // (1 + sigma r) e^{-sigma r} (-d.n) / r^3
-                float dn = -(dx * Y.nx + dy * Y.ny + dz * Y.nz);
-                float w = X.w[a] * dn * rinv * rinv * rinv;
-                float pr = fmaf(sr, r, 1.0f), pi = si * r;
+                const float dn = -(dx * nx + dy * ny + dz * nz);
+                const float w = X.w[a] * dn * rinv * rinv * rinv;
+                const float pr = fmaf(sr, r, 1.0f), pi = si * r;
                 acc.x = fmaf(w, pr * e.x - pi * e.y, acc.x);
                 acc.y = fmaf(w, pr * e.y + pi * e.x, acc.y);
             }
         }
-        float wy = Y.w[b];
         if (OP == TD_SLP) {
             out[0].x = fmaf(wy, acc.x, out[0].x);
             out[0].y = fmaf(wy, acc.y, out[0].y);
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                float f = wy * bary7f(b, k);
+                const float f = wy * bary7f(b, k);
                 out[k].x = fmaf(f, acc.x, out[k].x);
                 out[k].y = fmaf(f, acc.y, out[k].y);
             }
@@ -141,26 +147,19 @@ TD_D void pair_reg_f32(const TriF &X, const TriF &Y, float sr, float si, c32 *ou
     }
 }
 
-// ---------------------------------------------------------------------------
-// FP64 regular pairs
-// ---------------------------------------------------------------------------
-struct TriD {
+struct TestD {
     double x[7], y[7], z[7], w[7];
-    double nx, ny, nz;
 };
 
-TD_D void load_trid(const MeshDev &m, int t, TriD &T) {
+TD_D void load_test(const MeshDev &m, int t, TestD &T) {
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        int o = q * m.nt + t;
+        const int o = q * m.nt + t;
         T.x[q] = m.qx[o];
         T.y[q] = m.qy[o];
         T.z[q] = m.qz[o];
         T.w[q] = m.qw[o];
     }
-    T.nx = m.n64[t];
-    T.ny = m.n64[m.nt + t];
-    T.nz = m.n64[2 * m.nt + t];
 }
 
 TD_D c64 expm_sr(double sr, double si, double r) {
@@ -171,42 +170,63 @@ TD_D c64 expm_sr(double sr, double si, double r) {
 }
 
 template <int OP>
-TD_D void pair_reg_f64(const TriD &X, const TriD &Y, double sr, double si, c64 *out) {
+TD_D void pair_f64(const TestD &X, const MeshDev &m, int tj, double sr, double si, c64 *out) {
+    double nx = 0.0, ny = 0.0, nz = 0.0;
+    if (OP == TD_DLP) {
+        nx = m.n64[tj];
+        ny = m.n64[m.nt + tj];
+        nz = m.n64[2 * m.nt + tj];
+    }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
-        double yx = Y.x[b], yy = Y.y[b], yz = Y.z[b];
+        const int ob = b * m.nt + tj;
+        const double yx = m.qx[ob], yy = m.qy[ob], yz = m.qz[ob], wy = m.qw[ob];
         c64 acc = {0.0, 0.0};
-#pragma unroll 1
+#pragma unroll
         for (int a = 0; a < 7; ++a) {
-            double dx = yx - X.x[a], dy = yy - X.y[a], dz = yz - X.z[a];
-            double r = sqrt(dx * dx + dy * dy + dz * dz);
-            c64 e = expm_sr(sr, si, r);
+            const double dx = yx - X.x[a], dy = yy - X.y[a], dz = yz - X.z[a];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            const c64 e = expm_sr(sr, si, r);
             if (OP == TD_SLP) {
-                double w = X.w[a] / r;
+                const double w = X.w[a] / r;
                 acc.x += w * e.x;
                 acc.y += w * e.y;
             } else {
-                double dn = -(dx * Y.nx + dy * Y.ny + dz * Y.nz);
-                double w = X.w[a] * dn / (r * r * r);
-                double pr = 1.0 + sr * r, pi = si * r;
+                const double dn = -(dx * nx + dy * ny + dz * nz);
+                const double w = X.w[a] * dn / (r * r * r);
+                const double pr = 1.0 + sr * r, pi = si * r;
                 acc.x += w * (pr * e.x - pi * e.y);
                 acc.y += w * (pr * e.y + pi * e.x);
             }
         }
-        double wy = Y.w[b];
         if (OP == TD_SLP) {
             out[0].x += wy * acc.x;
             out[0].y += wy * acc.y;
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                double f = wy * bary7d(b, k);
+                const double f = wy * bary7d(b, k);
                 out[k].x += f * acc.x;
                 out[k].y += f * acc.y;
             }
         }
     }
 }
+
+// Precision dispatch used by the kernels.
+template <class T> struct Reg;
+template <> struct Reg<float> {
+    using Test = TestF;
+    template <int OP> TD_D static void pair(const Test &X, const MeshDev &m, int tj, float sr, float si, c32 *o) {
+        pair_f32<OP>(X, m, tj, sr, si, o);
+    }
+};
+template <> struct Reg<double> {
+    using Test = TestD;
+    template <int OP> TD_D static void pair(const Test &X, const MeshDev &m, int tj, double sr, double si, c64 *o) {
+        pair_f64<OP>(X, m, tj, sr, si, o);
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Touching pairs: classification and Sauter-Schwab quadrature points (FP64)
