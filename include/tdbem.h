@@ -55,6 +55,7 @@ typedef struct tdbem_mesh *tdbem_mesh_t;
 typedef struct tdbem_freqs *tdbem_freqs_t;
 typedef struct tdbem_tree *tdbem_tree_t;
 typedef struct tdbem_tensor *tdbem_tensor_t;
+typedef struct tdbem_model *tdbem_model_t;
 
 /* Operator and discretisation (Sec. 2 eqs. slp/dlp, Sec. 3):
  *   op = TDBEM_SLP: A[i,j](s) = int_{tau_i} int_{tau_j} exp(-s r/c)/(4 pi r),
@@ -81,8 +82,9 @@ typedef struct {
 typedef struct {
     double eps;      /* tolerance of Algorithm 1 on each block (e.g. 1e-4) */
     double eps_aca;  /* tolerance of the ACA of every far-field face (e.g. 1e-6) */
-    int32_t max_face_rank; /* cap of the face ACA rank (<= 0: 64) */
-    int32_t flags;         /* reserved, 0 */
+    int32_t max_face_rank; /* cap of the face ACA rank, 1..64 (<= 0: 64) */
+    int32_t flags;         /* bit 0: launch the phases without graph capture */
+    tdbem_model_t model;   /* nullable: rank predictor (see the rank-predictor section) */
 } tdbem_aca_cfg;
 
 typedef struct {
@@ -194,6 +196,53 @@ int tdbem_apply_freq(tdbem_tensor_t t, int32_t fidx, const void *x, int32_t nrhs
  * host->device copy of W and the device->host copy of y are part of the
  * call, which returns when y is on the host. */
 int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, int32_t nrhs, void *y_host);
+
+/* ---- rank predictor (learned presizing; not part of the paper) ------------
+ * A small MLP (6 features -> 64 -> 64 -> 16 rank bins, GELU) predicts, for a
+ * far-field block and a frequency, the bin of the rank that the ACA of the
+ * plain face reaches at eps_aca.  With cfg->model set, tdbem_compress uses
+ * the prediction to order the far blocks by predicted cost, to presize the
+ * face pool and to run the first (lower bin edge) ACA steps of each face
+ * without per-step norm checks; their norms are then formed in one batch and
+ * the adaptive stopping rule picks the same rank it would have picked step by
+ * step (it stays the judge; under-predicted faces simply continue).
+ * Bins: rank <= 1, 2, 3, 4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64, > 64.
+ * Features (dimensionless): log(diam_I/dist), log(diam_J/dist), log(dist/h),
+ * min(diam)/dist, log(1 + Re(s) dist/c), log(1 + |Im(s)| dist/c), h the mean
+ * edge length.  Parameters (FP32 master, BF16 copy for inference) in the
+ * order W1[64][6] b1[64] W2[64][64] b2[64] W3[16][64] b3[16]. */
+#define TDBEM_MLP_NPARAMS 5648
+#define TDBEM_NFEAT 6
+#define TDBEM_NBINS 16
+int tdbem_rank_bin(int32_t rank);
+/* Seeded initialisation (uniform +-sqrt(6/fan_in), zero biases), on the device. */
+int tdbem_model_create(tdbem_ctx_t ctx, uint64_t seed, tdbem_model_t *out);
+int tdbem_model_destroy(tdbem_model_t m);
+/* Host copies of the FP32 master parameters [TDBEM_MLP_NPARAMS]; set also
+ * resets the Adam moments. */
+int tdbem_model_get_params(tdbem_model_t m, float *host);
+int tdbem_model_set_params(tdbem_model_t m, const float *host);
+/* Mean softmax cross-entropy over n samples and its gradient (FP32):
+ * x device [n][6], labels device [n] (bins), grad device [NPARAMS], loss
+ * device [1]. */
+int tdbem_model_loss_grad(tdbem_model_t m, const float *x, const int32_t *labels, int64_t n, float *grad,
+                          float *loss);
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8) with step counter t >= 1. */
+int tdbem_model_adam_step(tdbem_model_t m, const float *grad, double lr, int32_t t);
+/* Minibatch Adam over a seeded shuffle of (x, labels) (device arrays);
+ * final_loss (nullable, host) receives the loss over the whole set. */
+int tdbem_model_train(tdbem_model_t m, const float *x, const int32_t *labels, int64_t n, int32_t epochs,
+                      int32_t batch, double lr, uint64_t seed, double *final_loss);
+/* BF16-weight inference: bins device [n] (nullable), logits device [n][16]
+ * (nullable). */
+int tdbem_model_predict(tdbem_model_t m, const float *x, int64_t n, int32_t *bins, float *logits);
+/* Training samples from the plain method: for every far block of `tree`
+ * (tree order) and every unique frequency, the features (device float
+ * [count][6]) and the rank of the ACA of the plain face at cfg->eps_aca
+ * (device int32 [count]; max_face_rank + 1 when the cap was hit).  With
+ * feats or ranks NULL only *count is returned; ERR_ARG if capacity < count. */
+int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, tdbem_tree_t tree,
+                  const tdbem_aca_cfg *cfg, float *feats, int32_t *ranks, int64_t capacity, int64_t *count);
 
 #ifdef __cplusplus
 }

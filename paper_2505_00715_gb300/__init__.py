@@ -16,8 +16,9 @@ import numpy as np
 from . import _lib
 from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
 
-__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "entries", "compress", "SLP", "DLP", "P0", "P1",
-           "FP64", "MIXED", "EULER", "RADAU2", "TdbemError"]
+__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "compress", "harvest", "rank_bin",
+           "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError"]
+NPARAMS = 5648
 
 
 def _torch():
@@ -228,11 +229,82 @@ class Tensor:
 
 
 def compress(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64,
-             use_graph=True):
+             use_graph=True, model=None):
     ctx = mesh.ctx
     o = _op(op, prec, c, ng)
-    cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, 0 if use_graph else 1)
+    cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, 0 if use_graph else 1, model.h if model is not None else None)
     h = C.c_void_p()
     ctx.check(ctx.L.tdbem_compress(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), C.byref(h)),
               "tdbem_compress")
     return Tensor(ctx, h, mesh, freqs, tree, op, prec)
+
+
+def rank_bin(rank):
+    return int(_lib.load().tdbem_rank_bin(int(rank)))
+
+
+class Model:
+    """Rank-predictor MLP (6 -> 64 -> 64 -> 16) held on the device."""
+
+    def __init__(self, ctx, seed=2):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_model_create(ctx.h, seed, C.byref(h)), "tdbem_model_create")
+        self.h = h
+
+    def params(self):
+        p = np.zeros(NPARAMS, dtype=np.float32)
+        self.ctx.check(self.ctx.L.tdbem_model_get_params(self.h, _np_ptr(p)), "tdbem_model_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self.ctx.check(self.ctx.L.tdbem_model_set_params(self.h, _np_ptr(p)), "tdbem_model_set_params")
+
+    def loss_grad(self, x, labels):
+        torch = _torch()
+        g = torch.empty(NPARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        self.ctx.check(self.ctx.L.tdbem_model_loss_grad(self.h, _ptr(x), _ptr(labels), x.shape[0], _ptr(g), _ptr(loss)),
+                       "tdbem_model_loss_grad")
+        return loss, g
+
+    def adam_step(self, grad, lr, t):
+        self.ctx.check(self.ctx.L.tdbem_model_adam_step(self.h, _ptr(grad), lr, t), "tdbem_model_adam_step")
+
+    def train(self, x, labels, epochs=10, batch=4096, lr=3e-3, seed=3):
+        fl = C.c_double()
+        self.ctx.check(self.ctx.L.tdbem_model_train(self.h, _ptr(x), _ptr(labels), x.shape[0], epochs, batch, lr, seed,
+                                                    C.byref(fl)), "tdbem_model_train")
+        return fl.value
+
+    def predict(self, x, logits=False):
+        torch = _torch()
+        bins = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+        lg = torch.empty((x.shape[0], 16), dtype=torch.float32, device=x.device) if logits else None
+        self.ctx.check(self.ctx.L.tdbem_model_predict(self.h, _ptr(x), x.shape[0], _ptr(bins),
+                                                      _ptr(lg) if logits else None), "tdbem_model_predict")
+        return (bins, lg) if logits else bins
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_model_destroy(self.h)
+            self.h = None
+
+
+def harvest(mesh, op, freqs, tree, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64):
+    """(features [n, 6] float32, face-ACA ranks [n] int32) device tensors for
+    every (far block, unique frequency) of the tree."""
+    torch = _torch()
+    ctx = mesh.ctx
+    o = _op(op, prec, c, ng)
+    cfg = _lib.AcaCfg(1e-4, eps_aca, max_face_rank, 0, None)
+    n = C.c_int64()
+    ctx.check(ctx.L.tdbem_harvest(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), None, None, 0, C.byref(n)),
+              "tdbem_harvest")
+    dev = torch.device("cuda", ctx.device)
+    x = torch.empty((n.value, 6), dtype=torch.float32, device=dev)
+    r = torch.empty(n.value, dtype=torch.int32, device=dev)
+    ctx.check(ctx.L.tdbem_harvest(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), _ptr(x), _ptr(r), n.value,
+                                  C.byref(n)), "tdbem_harvest")
+    return x, r

@@ -30,7 +30,7 @@ class Op(C.Structure):
 
 class AcaCfg(C.Structure):
     _fields_ = [("eps", C.c_double), ("eps_aca", C.c_double), ("max_face_rank", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("model", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -75,6 +75,18 @@ EXPORTS = {
     "tdbem_apply_weighted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_freq": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_weighted_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "tdbem_rank_bin": (C.c_int, [C.c_int32]),
+    "tdbem_model_create": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "tdbem_model_destroy": (C.c_int, [C.c_void_p]),
+    "tdbem_model_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tdbem_model_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "tdbem_model_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "tdbem_model_adam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32]),
+    "tdbem_model_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                    C.c_double, C.c_uint64, C.POINTER(C.c_double)]),
+    "tdbem_model_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "tdbem_harvest": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.POINTER(AcaCfg),
+                                C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
 }
 
 

@@ -528,7 +528,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     if (f->Nu > 256) return td_fail(ctx, TDBEM_ERR_ARG, "at most 256 unique frequencies are supported");
     const double t0 = now_ms();
     const int Nu = f->Nu;
-    const int kcap = cfg->max_face_rank > 0 ? std::min(cfg->max_face_rank, 512) : 64;
+    const int kcap = cfg->max_face_rank > 0 ? std::min(cfg->max_face_rank, 64) : 64;  // tiles hold <= 64 rows
     tdbem_tensor *T = new (std::nothrow) tdbem_tensor();
     if (!T) return TDBEM_ERR_OOM;
     T->ctx = ctx;
@@ -578,6 +578,27 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         const int64_t sa = (int64_t)(a[1] - a[0]) * (a[3] - a[2]), sb = (int64_t)(b[1] - b[0]) * (b[3] - b[2]);
         return sa != sb ? sa > sb : x < y;
     });
+    // learned presizing: predicted face ranks order the far blocks by cost,
+    // size the face pool and set the first unchecked ACA steps
+    std::vector<int32_t> kpred;
+    int64_t pred_far_cap = -1;
+    if (cfg->model) {
+        std::vector<double> cost;
+        if ((rc = td_predict_kpred(cfg->model, tree, mesh, f, op->c, far_ids, kpred, cost))) return fail(rc);
+        std::vector<size_t> order(far_ids.size());
+        for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::vector<int32_t> sorted(far_ids.size());
+        pred_far_cap = 0;
+        for (size_t q = 0; q < order.size(); ++q) {
+            sorted[q] = far_ids[order[q]];
+            const int32_t *bl = &tree->blocks[5 * sorted[q]];
+            int64_t ks = 0;
+            for (int u = 0; u < Nu; ++u) ks += std::min(kpred[(int64_t)sorted[q] * Nu + u], kcap);
+            pred_far_cap += ((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks;
+        }
+        far_ids.swap(sorted);
+    }
     T->kcap = kcap;
     T->max_near_rows = max_near_rows;
     // ---- persistent device data of the tensor
@@ -661,7 +682,13 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     const double t_plan = now_ms();
     // face pool: every near term fits (r <= Nu), far terms get a generous
     // estimate; on overflow the far phase is rerun with a larger pool.
-    int64_t cap = ntens + sum_far_len * 256 + 1024;
+    int64_t cap = ntens + (pred_far_cap >= 0 ? pred_far_cap + pred_far_cap / 4 : sum_far_len * 256) + 1024;
+    int32_t *dkpred = nullptr;
+    if (!kpred.empty()) {
+        if ((rc = dalloc(ctx, &dkpred, kpred.size(), &g.p)) || (rc = upload(ctx, dkpred, kpred.data(), kpred.size())))
+            return fail(rc);
+        fa.kpred = dkpred;
+    }
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) cudaEventCreate(&ev[k]);
     int hflags = 0;
@@ -888,6 +915,88 @@ extern "C" int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, i
     int rc = apply_impl(t, dW, nrhs, dy, -1);
     if (rc) return rc;
     TD_CUDA(ctx, cudaMemcpyAsync(y_host, dy, yb, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// face-rank harvest (training samples of the rank predictor)
+// ============================================================================
+extern "C" int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, tdbem_tree_t tree,
+                             const tdbem_aca_cfg *cfg, float *feats, int32_t *ranks, int64_t capacity, int64_t *count) {
+    if (!ctx || !mesh || !f || !tree || !cfg || !count) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_harvest: NULL argument");
+    cudaGetLastError();
+    int rc = check_op(ctx, op);
+    if (rc) return rc;
+    if (tree->mesh != mesh || tree->side[0].basis != TDBEM_P0 ||
+        tree->side[1].basis != (op->op == TDBEM_DLP ? TDBEM_P1 : TDBEM_P0))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tree does not match mesh and operator");
+    if (f->Nu > 256) return td_fail(ctx, TDBEM_ERR_ARG, "at most 256 unique frequencies are supported");
+    const int Nu = f->Nu;
+    std::vector<int32_t> far_ids;
+    int maxI = 1, maxJ = 1;
+    const int64_t nb = (int64_t)tree->blocks.size() / 5;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int32_t *bl = &tree->blocks[5 * b];
+        if (!bl[4]) continue;
+        far_ids.push_back((int32_t)b);
+        maxI = std::max(maxI, bl[1] - bl[0]);
+        maxJ = std::max(maxJ, bl[3] - bl[2]);
+    }
+    *count = (int64_t)far_ids.size() * Nu;
+    if (!feats || !ranks) return TDBEM_OK;
+    if (capacity < *count) return td_fail(ctx, TDBEM_ERR_ARG, "capacity %lld < %lld samples", (long long)capacity, (long long)*count);
+    if (*count == 0) return TDBEM_OK;
+    std::vector<float> x;
+    td_block_features(tree, mesh, f, op->c, far_ids, x);
+    if ((rc = upload(ctx, feats, x.data(), x.size()))) return rc;
+    const int kcap = cfg->max_face_rank > 0 ? std::min(cfg->max_face_rank, 64) : 64;
+    Guard g;
+    int32_t *dblocks, *dpr, *dpc, *dfar, *flags, *drank;
+    double *sig;
+    char *scr;
+    unsigned int *counter;
+    std::vector<double> hs(2 * Nu);
+    for (int u = 0; u < Nu; ++u) {
+        hs[2 * u] = f->s[2 * f->uidx[u]] / op->c;
+        hs[2 * u + 1] = f->s[2 * f->uidx[u] + 1] / op->c;
+    }
+    const size_t es = op->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
+    const int nctas = std::min<int64_t>(*count, (int64_t)ctx->num_sms * 2);
+    const int64_t sper = (int64_t)kcap * (maxI + maxJ);
+    if ((rc = dalloc(ctx, &dblocks, 5 * nb, &g.p)) || (rc = dalloc(ctx, &dpr, tree->side[0].n, &g.p)) ||
+        (rc = dalloc(ctx, &dpc, tree->side[1].n, &g.p)) || (rc = dalloc(ctx, &dfar, far_ids.size(), &g.p)) ||
+        (rc = dalloc(ctx, &flags, 4, &g.p)) || (rc = dalloc(ctx, &drank, nb, &g.p)) || (rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) ||
+        (rc = dalloc(ctx, &scr, es * sper * nctas, &g.p)) || (rc = dalloc(ctx, &counter, 4, &g.p)))
+        return rc;
+    if ((rc = upload(ctx, dblocks, tree->blocks.data(), 5 * nb)) || (rc = upload(ctx, dpr, tree->side[0].perm.data(), tree->side[0].n)) ||
+        (rc = upload(ctx, dpc, tree->side[1].perm.data(), tree->side[1].n)) ||
+        (rc = upload(ctx, dfar, far_ids.data(), far_ids.size())) || (rc = upload(ctx, sig, hs.data(), hs.size())))
+        return rc;
+    cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ctx->stream);
+    cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ctx->stream);
+    MeshDev md = mesh_dev(mesh, op->ng, nullptr, nullptr, nullptr);  // far blocks have no touching pairs
+    FarArgs fa{};
+    fa.nfar = (int)far_ids.size();
+    fa.far_ids = dfar;
+    fa.blocks = dblocks;
+    fa.perm_r = dpr;
+    fa.perm_c = dpc;
+    fa.sig = sig;
+    fa.nf = Nu;
+    fa.maxI = maxI;
+    fa.maxJ = maxJ;
+    fa.scratch = scr;
+    fa.scratch_per_cta = sper;
+    fa.counter = counter;
+    fa.harvest = ranks;
+    TensorOut o{};
+    o.Nu = Nu;
+    o.rank = drank;
+    o.dev_flags = flags;
+    AcaParams ap{cfg->eps, cfg->eps_aca, kcap};
+    if (td_launch_far_aca(ctx->stream, md, op->op, op->prec, fa, o, ap, nctas))
+        return td_fail(ctx, TDBEM_ERR_CUDA, "harvest kernel launch failed");
     TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return TDBEM_OK;
 }

@@ -116,5 +116,46 @@ TD_D void block_sum(double *v, double *red) {
     __syncthreads();
 }
 
+// Compensated ("twice the working precision") accumulation of products of
+// FP32 numbers on the FP32 pipe: TwoProd by FMA and TwoSum (Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005).  The
+// pair (s, c) represents s + c; the result is read out in FP64.  For FP64
+// inputs the plain FP64 accumulation is used.
+struct F2 {
+    float s, c;
+};
+// (the _rn intrinsics keep the compiler from contracting these steps into FMAs)
+TD_D void f2_fma(F2 &a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = fmaf(x, y, -p);
+    const float s = __fadd_rn(a.s, p);
+    const float z = __fsub_rn(s, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, z)), __fsub_rn(p, z));
+    a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+    a.s = s;
+}
+template <class T> struct DotAcc;
+template <> struct DotAcc<float> {
+    F2 re{0.f, 0.f}, im{0.f, 0.f};
+    // += x * conj(y)
+    TD_D void add(cx<float> x, cx<float> y) {
+        f2_fma(re, x.x, y.x);
+        f2_fma(re, x.y, y.y);
+        f2_fma(im, x.y, y.x);
+        f2_fma(im, -x.x, y.y);
+    }
+    TD_D double real() const { return (double)re.s + (double)re.c; }
+    TD_D double imag() const { return (double)im.s + (double)im.c; }
+};
+template <> struct DotAcc<double> {
+    double re = 0.0, im = 0.0;
+    TD_D void add(cx<double> x, cx<double> y) {
+        re = fma(x.x, y.x, fma(x.y, y.y, re));
+        im = fma(x.y, y.x, fma(-x.x, y.y, im));
+    }
+    TD_D double real() const { return re; }
+    TD_D double imag() const { return im; }
+};
+
 // Device-side error word: kernels record a code and keep going safely.
 enum { TD_DEV_OK = 0, TD_DEV_POOL_OVERFLOW = 1, TD_DEV_BAD_INDEX = 2, TD_DEV_RANK_CAP = 4 };

@@ -119,3 +119,11 @@ void td_plan_blocks(const HostTree &rows, const HostTree &cols, double eta,
 void td_mesh_adjacency(tdbem_mesh *m);
 int td_gauss01(int n, double *x, double *w);
 void td_rule7(double bary[7][3], double w[7]);
+
+// model.cu
+struct tdbem_model;
+void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
+                       const std::vector<int32_t> &far, std::vector<float> &x);
+int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
+                     const std::vector<int32_t> &far, std::vector<int32_t> &kpred_by_block,
+                     std::vector<double> &cost);

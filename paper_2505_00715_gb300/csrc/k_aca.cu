@@ -24,6 +24,42 @@ namespace {
 
 constexpr int kMaxNu = 256;
 
+// v -= sum_{c < cn} coef[c] * base[c][idx]: eight independent loads in flight
+// per thread (the loop is memory-latency bound otherwise).
+template <class T>
+TD_D cx<T> apply_coef(cx<T> v, const cx<T> *coef, const cx<T> *const *base, int cn, int idx) {
+    cx<T> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int c = 0;
+    for (; c + 8 <= cn; c += 8) {
+        cx<T> b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = base[c + q][idx];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(acc[q & 3], coef[c + q], b[q]);
+    }
+    for (; c < cn; ++c) cfma(acc[0], coef[c], base[c][idx]);
+    return v - ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
+// h = sum_{t < kf} U[t * su + i] V[t * sv + j] with independent accumulators.
+template <class T>
+TD_D cx<T> lowrank_at(const cx<T> *U, int64_t su, const cx<T> *V, int64_t sv, int kf, int i, int j) {
+    cx<T> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int t = 0;
+    for (; t + 4 <= kf; t += 4) {
+        cx<T> u[4], w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            u[q] = U[(t + q) * su + i];
+            w[q] = V[(t + q) * sv + j];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(acc[q], u[q], w[q]);
+    }
+    for (; t < kf; ++t) cfma(acc[0], U[t * su + i], V[t * sv + j]);
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
 // ============================================================================
 // Near field
 // ============================================================================
@@ -32,6 +68,8 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
                                                   cx<T> *scratch, int64_t sper) {
     __shared__ cx<T> s_fl[kMaxNu];
     __shared__ cx<T> s_hd[kMaxNu];
+    __shared__ cx<T> s_fk[kMaxNu];
+    __shared__ const cx<T> *s_base[kMaxNu];
     __shared__ int s_sel[kMaxNu];
     __shared__ ArgMaxD red[32];
     __shared__ double redd[32 * 2];
@@ -53,9 +91,13 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
         int l = 0, k = 0, r = -1;
         while (l < Nu) {
             ArgMaxD am = {-1.0, 0x7fffffff};
+            for (int d = threadIdx.x; d < l; d += blockDim.x) {
+                s_fk[d] = fib[(tb + d) * Nu + k];
+                s_base[d] = pool + o.foff[tb + d];
+            }
+            __syncthreads();
             for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
-                cx<T> h = N[k * nIJ + e];
-                for (int d = 0; d < l; ++d) cfms(h, fib[(tb + d) * Nu + k], pool[o.foff[tb + d] + e]);
+                cx<T> h = apply_coef(N[k * nIJ + e], s_fk, s_base, l, (int)e);
                 H[e] = h;
                 double v = (double)h.x * h.x + (double)h.y * h.y;
                 if (am_better(v, (int)e, am.v, am.i)) am = {v, (int)e};
@@ -77,9 +119,10 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
             __syncthreads();
             // eq. norm in FP64: <H_l, H_d>, ||H_l||^2, <f_l, f_d>
             double v2[2] = {0.0, 0.0};
-            for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
-                c64 h = ccast<double>(H[e]);
-                v2[0] += h.x * h.x + h.y * h.y;
+            {
+                DotAcc<T> acc;
+                for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) acc.add(H[e], H[e]);
+                v2[0] = acc.real();
             }
             block_sum<1>(v2, redd);
             const double hl2 = v2[0];
@@ -87,13 +130,10 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
             for (int kk = 0; kk < Nu; ++kk) fl2 += cabs2(ccast<double>(s_fl[kk]));
             double cross = 0.0;
             for (int d = 0; d < l; ++d) {
-                double g[2] = {0.0, 0.0};
                 const cx<T> *Hd = pool + o.foff[tb + d];
-                for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
-                    c64 x = ccast<double>(H[e]), y = ccast<double>(Hd[e]);
-                    g[0] += x.x * y.x + x.y * y.y;
-                    g[1] += x.y * y.x - x.x * y.y;
-                }
+                DotAcc<T> acc;
+                for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) acc.add(H[e], Hd[e]);
+                double g[2] = {acc.real(), acc.imag()};
                 block_sum<2>(g, redd);
                 c64 gf = {0.0, 0.0};
                 for (int kk = 0; kk < Nu; ++kk)
@@ -156,35 +196,8 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
 // ============================================================================
 // Far field
 // ============================================================================
-// Regular entry A[row, col] (no touching pairs in far blocks), 1/(4 pi) applied.
-template <class T, int OP>
-TD_D cx<T> far_entry(const MeshDev &m, const typename Reg<T>::Test &X, int col, T sr, T si) {
-    cx<T> acc = {0, 0};
-    if (OP == TD_SLP) {
-        cx<T> o[3] = {};
-        Reg<T>::template pair<TD_SLP>(X, m, col, sr, si, o);
-        acc = o[0];
-    } else {
-        for (int p = m.v2t_ptr[col]; p < m.v2t_ptr[col + 1]; ++p) {
-            cx<T> o[3] = {};
-            Reg<T>::template pair<TD_DLP>(X, m, m.v2t[p], sr, si, o);
-            acc = acc + o[m.v2t_loc[p]];
-        }
-    }
-    const T s = (T)(1.0 / TD_FOUR_PI);
-    return cx<T>{acc.x * s, acc.y * s};
-}
-
-// Column-fibre entry: test triangle per thread, trial DOF fixed.
-template <class T, int OP>
-TD_D cx<T> far_entry_col(const MeshDev &m, int row, int col, T sr, T si) {
-    typename Reg<T>::Test X;
-    load_test(m, row, X);
-    return far_entry<T, OP>(m, X, col, sr, si);
-}
-
-// One point pair (a of the test triangle, b of the trial triangle), for the
-// warp-split tube evaluation.
+// One point pair (a of the test triangle, b of the trial triangle); fibres and
+// tubes are evaluated one entry per warp, the lanes splitting the point pairs.
 TD_D c32 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int loc, float sr, float si) {
     const int oa = a * m.nt + ti, ob = b * m.nt + tj;
     float dx = (m.qxh[ob] - m.qxh[oa]) + (m.qxl[ob] - m.qxl[oa]);
@@ -231,6 +244,7 @@ TD_D cx<T> warp_entry(const MeshDev &m, int row, int col, T sr, T si) {
     return cx<T>{acc.x * s, acc.y * s};
 }
 
+
 constexpr int kNT = 256;
 constexpr int kNCoef = 1024;
 
@@ -246,6 +260,9 @@ struct FarShared {
     double redd[32 * 4];
     cx<T> coef[kNCoef];
     const cx<T> *base[kNCoef];
+    double nrow[64], nu[64], nv[64];  // ACA norm terms per step (face rank <= 64)
+    double normS2;
+    int kstop;
     int idx, jstar, istar, ncoef;
     long long off;
     cx<T> piv;
@@ -297,11 +314,99 @@ TD_D int build_coef(FarShared<T> &S, int mode, int fixed, int l, int kf, int k, 
     return total;
 }
 
+constexpr int kTI = 16;     // Gram tile width (rows of U / V per stage)
+constexpr int kGCh = 64;    // Gram tile height (factor columns per stage)
+constexpr int kGOut = 4;    // Gram outputs per thread
+
+// Shared tiles for the Gram sums (dynamic shared memory).
+template <class T>
+struct GramTiles {
+    cx<T> A[64][kTI + 1];      // current face: rows t < kf
+    cx<T> B[kGCh][kTI + 1];    // factor columns of the previous terms (and of the face itself)
+};
+
+// eq. norm for the new term l: for every previous term d < l and for d = l,
+// gH[d] += sum_{t < kf, tau < k_d} <u_t, U_d[tau]> <v_t, V_d[tau]>, where
+// u_t, v_t are the face's ACA factors (Uw, Vw).  The inner products are
+// small GEMMs over the rows of U and V, staged through shared-memory tiles;
+// each thread owns up to kGOut (t, tau) outputs and accumulates them with
+// compensated FP32 products (FP64 in the FP64 form); the products of the
+// two inner products are summed in FP64.
+template <class T>
+TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int nJ, const cx<T> *pool,
+                    const cx<T> *Uw, const cx<T> *Vw, int maxI, int maxJ) {
+    const int tid = threadIdx.x;
+    int Kprev = 0;
+    for (int d = 0; d < l; ++d) Kprev += S.frank[d];
+    const int Kall = Kprev + kf;
+    const int chmax = max(1, min(kGCh, (kGOut * (int)blockDim.x) / max(kf, 1)));
+    for (int g0 = 0; g0 < Kall; g0 += chmax) {
+        const int ch = min(chmax, Kall - g0);
+        DotAcc<T> au[kGOut], av[kGOut];
+        for (int pass = 0; pass < 2; ++pass) {
+            const int n = pass ? nJ : nI;
+            const cx<T> *W = pass ? Vw : Uw;
+            const int64_t sw = pass ? maxJ : maxI;
+            for (int x0 = 0; x0 < n; x0 += kTI) {
+                __syncthreads();
+                for (int e = tid; e < kf * kTI; e += blockDim.x) {
+                    const int t = e / kTI, xx = e % kTI;
+                    G.A[t][xx] = x0 + xx < n ? W[t * sw + x0 + xx] : cx<T>{0, 0};
+                }
+                for (int e = tid; e < ch * kTI; e += blockDim.x) {
+                    const int c = e / kTI, xx = e % kTI, g = g0 + c;
+                    int d = 0, rem = g;
+                    while (d < l && rem >= S.frank[d]) {
+                        rem -= S.frank[d];
+                        ++d;
+                    }
+                    const cx<T> *col;
+                    if (d < l) {
+                        const cx<T> *Ud = pool + S.foff[d];
+                        col = pass ? Ud + (int64_t)S.frank[d] * nI + (int64_t)rem * nJ : Ud + (int64_t)rem * nI;
+                    } else {
+                        col = W + (int64_t)rem * sw;
+                    }
+                    G.B[c][xx] = x0 + xx < n ? col[x0 + xx] : cx<T>{0, 0};
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < kGOut; ++q) {
+                    const int o = tid + q * blockDim.x;
+                    if (o < kf * ch) {
+                        const int t = o / ch, c = o % ch;
+                        DotAcc<T> &acc = pass ? av[q] : au[q];
+#pragma unroll 4
+                        for (int xx = 0; xx < kTI; ++xx) acc.add(G.A[t][xx], G.B[c][xx]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kGOut; ++q) {
+            const int o = tid + q * blockDim.x;
+            if (o < kf * ch) {
+                const int g = g0 + o % ch;
+                int d = 0, rem = g;
+                while (d < l && rem >= S.frank[d]) {
+                    rem -= S.frank[d];
+                    ++d;
+                }
+                const double ur = au[q].real(), ui = au[q].imag(), vr = av[q].real(), vi = av[q].imag();
+                atomicAdd(&S.gH[d].x, ur * vr - ui * vi);
+                atomicAdd(&S.gH[d].y, ur * vi + ui * vr);
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <class T, int OP>
 __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FarShared<T> &S = *reinterpret_cast<FarShared<T> *>(smem_raw);
-    unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + sizeof(FarShared<T>));
+    GramTiles<T> *gt = reinterpret_cast<GramTiles<T> *>(smem_raw + sizeof(FarShared<T>));
+    unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + sizeof(FarShared<T>) + sizeof(GramTiles<T>));
     const int Nu = a.nf;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     cx<T> *Uw = (cx<T> *)a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
@@ -314,8 +419,9 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
         __syncthreads();
         const int idx = S.idx;
         __syncthreads();
-        if (idx >= a.nfar) break;
-        const int b = a.far_ids[idx];
+        const int nitems = a.harvest ? a.nfar * Nu : a.nfar;
+        if (idx >= nitems) break;
+        const int b = a.far_ids[a.harvest ? idx / Nu : idx];
         const int *bl = a.blocks + 5 * b;
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         const int *rows = a.perm_r + bl[0], *cols = a.perm_c + bl[2];
@@ -323,36 +429,36 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
         for (int kk = tid; kk < Nu; kk += blockDim.x) S.sel[kk] = 0;
         __syncthreads();
         double normC2 = 0.0;
-        int l = 0, k = 0, r = -1;
+        int l = 0, k = a.harvest ? idx % Nu : 0, r = -1;
         while (l < Nu) {
             const T sr = (T)a.sig[2 * k], si = (T)a.sig[2 * k + 1];
             // ------------------------------------------------ ACA of the residual face
             for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
             __syncthreads();
             int kf = 0, istar = 0;
-            double normS2 = 0.0;
+            if (tid == 0) S.normS2 = 0.0;
+            int pend0 = 0;  // first ACA step whose norm terms are not yet summed
+            const int kp = (a.kpred && !a.harvest) ? min(a.kpred[tb + k], p.kcap) : 0;
             bool converged = false;
             int guard = 0;
             while (kf < p.kcap && guard < nI + p.kcap) {
                 ++guard;
                 // row fibre at istar
-                typename Reg<T>::Test X;
-                load_test(m, rows[istar], X);
                 ArgMaxD am = {-1.0, 0x7fffffff};
                 int total = 0;
                 // entries first (kept in Vw[kf]), then residual corrections in chunks
-                for (int j = tid; j < nJ; j += blockDim.x) Vw[(int64_t)kf * a.maxJ + j] = far_entry<T, OP>(m, X, cols[j], sr, si);
+                for (int j = wid; j < nJ; j += nwarps) {
+                    const cx<T> v = warp_entry<T, OP>(m, rows[istar], cols[j], sr, si);
+                    if (lane == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
+                }
                 ev_reg += nJ;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
                     total = build_coef(S, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     const int cn = min(kNCoef, total - c0);
-                    for (int j = tid; j < nJ; j += blockDim.x) {
-                        cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
-                        for (int c = 0; c < cn; ++c) cfms(v, S.coef[c], S.base[c][j]);
-                        Vw[(int64_t)kf * a.maxJ + j] = v;
-                    }
+                    for (int j = tid; j < nJ; j += blockDim.x)
+                        Vw[(int64_t)kf * a.maxJ + j] = apply_coef(Vw[(int64_t)kf * a.maxJ + j], S.coef, S.base, cn, j);
                     if (c0 + kNCoef >= total) break;
                 }
                 for (int j = tid; j < nJ; j += blockDim.x) {
@@ -386,19 +492,18 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
                     Vw[(int64_t)kf * a.maxJ + j] = cdiv(v, piv);
                 }
                 // column fibre at jstar
-                for (int i = tid; i < nI; i += blockDim.x)
-                    Uw[(int64_t)kf * a.maxI + i] = far_entry_col<T, OP>(m, rows[i], cols[jstar], sr, si);
+                for (int i = wid; i < nI; i += nwarps) {
+                    const cx<T> v = warp_entry<T, OP>(m, rows[i], cols[jstar], sr, si);
+                    if (lane == 0) Uw[(int64_t)kf * a.maxI + i] = v;
+                }
                 ev_reg += nI;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
                     total = build_coef(S, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     const int cn = min(kNCoef, total - c0);
-                    for (int i = tid; i < nI; i += blockDim.x) {
-                        cx<T> v = Uw[(int64_t)kf * a.maxI + i];
-                        for (int c = 0; c < cn; ++c) cfms(v, S.coef[c], S.base[c][i]);
-                        Uw[(int64_t)kf * a.maxI + i] = v;
-                    }
+                    for (int i = tid; i < nI; i += blockDim.x)
+                        Uw[(int64_t)kf * a.maxI + i] = apply_coef(Uw[(int64_t)kf * a.maxI + i], S.coef, S.base, cn, i);
                     if (c0 + kNCoef >= total) break;
                 }
                 __syncthreads();
@@ -410,54 +515,89 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
                     if (am_better(av, i, am2.v, am2.i)) am2 = {av, i};
                 }
                 am2 = block_argmax(am2, S.red);
-                // FP64 norm recursion: ||S_k||^2 += 2 Re sum_t <u_k,u_t><v_k,v_t> + |u_k|^2 |v_k|^2
-                double acc4[4] = {0.0, 0.0, 0.0, 0.0};  // cross, |u|^2, |v|^2
-                for (int t = wid; t <= kf; t += nwarps) {
-                    double gu[2] = {0, 0}, gv[2] = {0, 0};
-                    for (int i = lane; i < nI; i += 32) {
-                        c64 x = ccast<double>(Uw[(int64_t)kf * a.maxI + i]), y = ccast<double>(Uw[(int64_t)t * a.maxI + i]);
-                        gu[0] += x.x * y.x + x.y * y.y;
-                        gu[1] += x.y * y.x - x.x * y.y;
-                    }
-                    for (int j = lane; j < nJ; j += 32) {
-                        c64 x = ccast<double>(Vw[(int64_t)kf * a.maxJ + j]), y = ccast<double>(Vw[(int64_t)t * a.maxJ + j]);
-                        gv[0] += x.x * y.x + x.y * y.y;
-                        gv[1] += x.y * y.x - x.x * y.y;
-                    }
-                    for (int q = 0; q < 2; ++q) {
-                        gu[q] = warp_sum(gu[q]);
-                        gv[q] = warp_sum(gv[q]);
-                    }
-                    if (lane == 0) {
-                        if (t < kf)
-                            acc4[0] += gu[0] * gv[0] - gu[1] * gv[1];
-                        else {
-                            acc4[1] += gu[0];
-                            acc4[2] += gv[0];
+                // Norm recursion of the ACA (matrix analogue of eq. norm, FP64):
+                // ||S_k||^2 = ||S_{k-1}||^2 + 2 Re sum_{t<k} <u_k,u_t><v_k,v_t> + |u_k|^2 |v_k|^2.
+                // Steps below the predicted rank kp run without the check; their
+                // norms are formed in one batched pass when step kp - 1 is reached
+                // and the first step that meets the criterion is taken, exactly as
+                // if every step had been checked (the ACA steps themselves do not
+                // depend on the check).
+                const bool have_next = !(am2.i == 0x7fffffff || am2.v < 0.0);
+                if (kf + 1 < kp && have_next) {
+                    ++kf;
+                    istar = am2.i;
+                    continue;
+                }
+                for (int t = tid; t <= kf; t += blockDim.x) S.nrow[t] = 0.0;
+                __syncthreads();
+                {
+                    int npairs = 0;
+                    for (int t = pend0; t <= kf; ++t) npairs += t + 1;
+                    for (int pr = wid; pr < npairs; pr += nwarps) {
+                        int t = pend0, rem = pr;
+                        while (rem >= t + 1) {
+                            rem -= t + 1;
+                            ++t;
+                        }
+                        const int t2 = rem;
+                        DotAcc<T> au, av;
+                        for (int i = lane; i < nI; i += 32) au.add(Uw[(int64_t)t * a.maxI + i], Uw[(int64_t)t2 * a.maxI + i]);
+                        for (int j = lane; j < nJ; j += 32) av.add(Vw[(int64_t)t * a.maxJ + j], Vw[(int64_t)t2 * a.maxJ + j]);
+                        double gu[2] = {au.real(), au.imag()}, gv[2] = {av.real(), av.imag()};
+                        for (int q = 0; q < 2; ++q) {
+                            gu[q] = warp_sum(gu[q]);
+                            gv[q] = warp_sum(gv[q]);
+                        }
+                        if (lane == 0) {
+                            if (t2 < t) {
+                                atomicAdd(&S.nrow[t], gu[0] * gv[0] - gu[1] * gv[1]);
+                            } else {
+                                S.nu[t] = gu[0];
+                                S.nv[t] = gv[0];
+                            }
                         }
                     }
                 }
-                block_sum<3>(acc4, S.redd);
-                normS2 += 2.0 * acc4[0] + acc4[1] * acc4[2];
-                ++kf;
-                if (sqrt(acc4[1] * acc4[2]) <= p.eps_aca * sqrt(normS2)) {
+                __syncthreads();
+                if (tid == 0) {
+                    double n2 = S.normS2;
+                    int kstop = -1;
+                    for (int t = pend0; t <= kf; ++t) {
+                        n2 += 2.0 * S.nrow[t] + S.nu[t] * S.nv[t];
+                        if (sqrt(S.nu[t] * S.nv[t]) <= p.eps_aca * sqrt(n2)) {
+                            kstop = t;
+                            break;
+                        }
+                    }
+                    S.normS2 = n2;
+                    S.kstop = kstop;
+                }
+                __syncthreads();
+                if (S.kstop >= 0) {
+                    kf = S.kstop + 1;
                     converged = true;
                     break;
                 }
-                if (am2.i == 0x7fffffff || am2.v < 0.0) {
+                ++kf;
+                pend0 = kf;
+                if (!have_next) {
                     converged = true;
                     break;
                 }
                 istar = am2.i;
             }
             if (!converged && tid == 0) atomicOr(o.dev_flags, TD_DEV_RANK_CAP);
+            if (a.harvest) {  // face-rank harvest: record the ACA rank of the plain face and stop
+                if (tid == 0) a.harvest[idx] = converged ? kf : kf + 1;
+                r = 0;
+                break;
+            }
             // ------------------------------------------------ pivot on the rebuilt face
             ArgMaxD am = {-1.0, 0x7fffffff};
             const int64_t nIJ = (int64_t)nI * nJ;
             for (int64_t e = tid; e < nIJ; e += blockDim.x) {
                 const int i = (int)(e / nJ), j = (int)(e % nJ);
-                cx<T> h = {0, 0};
-                for (int t = 0; t < kf; ++t) cfma(h, Uw[(int64_t)t * a.maxI + i], Vw[(int64_t)t * a.maxJ + j]);
+                const cx<T> h = lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j);
                 double av = (double)h.x * h.x + (double)h.y * h.y;
                 if (am_better(av, (int)e, am.v, am.i)) am = {av, (int)e};
             }
@@ -476,9 +616,7 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
             for (int d = tid; d < l; d += blockDim.x) {
                 const cx<T> *Ud = pool + S.foff[d];
                 const cx<T> *Vd = Ud + (int64_t)S.frank[d] * nI;
-                cx<T> h = {0, 0};
-                for (int t = 0; t < S.frank[d]; ++t) cfma(h, Ud[(int64_t)t * nI + ip], Vd[(int64_t)t * nJ + jp]);
-                S.hd[d] = h;
+                S.hd[d] = lowrank_at(Ud, (int64_t)nI, Vd, (int64_t)nJ, S.frank[d], ip, jp);
             }
             __syncthreads();
             const cx<T> piv = S.piv;
@@ -493,55 +631,8 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
             ev_tube += Nu;
             for (int d = tid; d <= l; d += blockDim.x) S.gH[d] = {0.0, 0.0};
             __syncthreads();
-            // eq. norm (FP64): <H_l, H_d> = sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>
-            {
-                int npairs = 0;
-                for (int d = 0; d <= l; ++d) npairs += kf * (d < l ? S.frank[d] : kf);
-                for (int pr = wid; pr < npairs; pr += nwarps) {
-                    int rem = pr, d = 0;
-                    while (true) {
-                        const int kd = d < l ? S.frank[d] : kf;
-                        if (rem < kf * kd) break;
-                        rem -= kf * kd;
-                        ++d;
-                    }
-                    const int kd = d < l ? S.frank[d] : kf;
-                    const int t = rem / kd, tau = rem % kd;
-                    const cx<T> *Ud, *Vd;
-                    int64_t su, sv;
-                    if (d < l) {
-                        Ud = pool + S.foff[d];
-                        Vd = Ud + (int64_t)S.frank[d] * nI;
-                        su = nI;
-                        sv = nJ;
-                    } else {
-                        Ud = Uw;
-                        Vd = Vw;
-                        su = a.maxI;
-                        sv = a.maxJ;
-                    }
-                    double gu[2] = {0, 0}, gv[2] = {0, 0};
-                    for (int i = lane; i < nI; i += 32) {
-                        c64 x = ccast<double>(Uw[(int64_t)t * a.maxI + i]), y = ccast<double>(Ud[tau * su + i]);
-                        gu[0] += x.x * y.x + x.y * y.y;
-                        gu[1] += x.y * y.x - x.x * y.y;
-                    }
-                    for (int j = lane; j < nJ; j += 32) {
-                        c64 x = ccast<double>(Vw[(int64_t)t * a.maxJ + j]), y = ccast<double>(Vd[tau * sv + j]);
-                        gv[0] += x.x * y.x + x.y * y.y;
-                        gv[1] += x.y * y.x - x.x * y.y;
-                    }
-                    for (int q = 0; q < 2; ++q) {
-                        gu[q] = warp_sum(gu[q]);
-                        gv[q] = warp_sum(gv[q]);
-                    }
-                    if (lane == 0) {
-                        atomicAdd(&S.gH[d].x, gu[0] * gv[0] - gu[1] * gv[1]);
-                        atomicAdd(&S.gH[d].y, gu[0] * gv[1] + gu[1] * gv[0]);
-                    }
-                }
-            }
-            __syncthreads();
+            // eq. norm: <H_l, H_d> = sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>, d <= l
+            gram_sums(S, *gt, l, kf, nI, nJ, pool, Uw, Vw, a.maxI, a.maxJ);
             double fl2 = 0.0, cross = 0.0;
             for (int kk = 0; kk < Nu; ++kk) fl2 += cabs2(ccast<double>(S.fl[kk]));
             for (int d = 0; d < l; ++d) {
@@ -606,7 +697,7 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
             __syncthreads();
         }
         if (r < 0) r = l;
-        if (tid == 0) o.rank[b] = r;
+        if (tid == 0 && !a.harvest) o.rank[b] = r;
         __syncthreads();
     }
     if (tid == 0 && a.evals) {
@@ -630,7 +721,7 @@ int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const Tenso
 template <class T, int OP>
 static int launch_far(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
                       const AcaParams &p, int nctas) {
-    size_t sm = sizeof(FarShared<T>) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
+    size_t sm = sizeof(FarShared<T>) + sizeof(GramTiles<T>) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
     cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     k_far_aca<T, OP><<<nctas, kNT, sm, st>>>(m, a, o, p);

@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
     cx<T> *Wt = sm;
     cx<T> *z = Wt + (int64_t)NQ * TJ * nrhs;
     cx<T> *acc = z + (int64_t)RC * 2 * TJ * nrhs;
+    cx<T> *fq_s = acc + a.acc_max;                                   // [RC][NQ]
+    int *sg_s = reinterpret_cast<int *>(fq_s + (int64_t)RC * NQ);    // [NQ]
     const int tid = threadIdx.x;
     for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
         const int *bl = a.blocks + 5 * b;
@@ -49,6 +51,15 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
                 for (int d = d0; d < d0 + rc; ++d) sumk += o.frank[tb + d];
             const int nacc = far ? sumk * 2 * nrhs : nI * nrhs;
             for (int e = tid; e < nacc; e += blockDim.x) acc[e] = {0, 0};
+            // fibre value per point of the frequency list (conjugated for the
+            // conjugate half) and the half it belongs to
+            for (int e = tid; e < rc * NQ; e += blockDim.x) {
+                const int q = e % NQ, dd = e / NQ;
+                const int mp = a.qmap[a.single_f >= 0 ? a.single_f : q];
+                const cx<T> fv = fib[(tb + d0 + dd) * Nu + (mp > 0 ? mp - 1 : -mp - 1)];
+                fq_s[e] = mp > 0 ? fv : cconj(fv);
+                if (dd == 0) sg_s[q] = mp > 0 ? 1 : -1;
+            }
             for (int j0 = 0; j0 < nJ; j0 += TJ) {
                 const int tj = min(TJ, nJ - j0);
                 __syncthreads();
@@ -58,16 +69,17 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
                     Wt[((int64_t)q * TJ + jj) * nrhs + c] = W[((int64_t)q * a.ncols + col) * nrhs + c];
                 }
                 __syncthreads();
-                // frequency contraction of the tile for the chunk's terms
+                // frequency contraction of the tile for the chunk's terms; the
+                // per-point fibre coefficients were staged in shared memory
                 for (int e = tid; e < rc * tj * nrhs; e += blockDim.x) {
                     const int c = e % nrhs, jj = (e / nrhs) % tj, dd = e / (nrhs * tj);
-                    const cx<T> *f = fib + (tb + d0 + dd) * Nu;
+                    const cx<T> *fq = fq_s + (int64_t)dd * NQ;
                     cx<T> z1 = {0, 0}, z2 = {0, 0};
+#pragma unroll 4
                     for (int q = 0; q < NQ; ++q) {
-                        const int mp = a.qmap[a.single_f >= 0 ? a.single_f : q];
                         const cx<T> w = Wt[((int64_t)q * TJ + jj) * nrhs + c];
-                        if (mp > 0) cfma(z1, f[mp - 1], w);
-                        else cfma(z2, cconj(f[-mp - 1]), w);
+                        if (sg_s[q] > 0) cfma(z1, fq[q], w);
+                        else cfma(z2, fq[q], w);
                     }
                     z[(((int64_t)dd * 2 + 0) * TJ + jj) * nrhs + c] = z1;
                     z[(((int64_t)dd * 2 + 1) * TJ + jj) * nrhs + c] = z2;
@@ -188,22 +200,28 @@ int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorO
     int TJ = (int)std::max<int64_t>(1, std::min<int64_t>(32, (budget / 2) / ((int64_t)NQ * a.nrhs * es)));
     const int RC = 4;
     const int64_t acc_max = (int64_t)std::max(2 * RC * a.kcap, a.max_near_rows) * a.nrhs;
-    size_t sm = ((int64_t)NQ * TJ * a.nrhs + (int64_t)RC * 2 * TJ * a.nrhs + acc_max) * es;
+    auto smem = [&](int tj) {
+        return ((int64_t)NQ * tj * a.nrhs + (int64_t)RC * 2 * tj * a.nrhs + acc_max + (int64_t)RC * NQ) * es +
+               sizeof(int) * NQ;
+    };
+    size_t sm = smem(TJ);
     while (sm > (size_t)(200 * 1024) && TJ > 1) {
         TJ /= 2;
-        sm = ((int64_t)NQ * TJ * a.nrhs + (int64_t)RC * 2 * TJ * a.nrhs + acc_max) * es;
+        sm = smem(TJ);
     }
+    ApplyArgs aa = a;
+    aa.acc_max = acc_max;
     if (sm > (size_t)(220 * 1024)) return (int)cudaErrorInvalidConfiguration;
     const int grid = std::min(a.nb, num_sms * 4);
     cudaError_t e;
     if (prec == TDBEM_FP64) {
         e = cudaFuncSetAttribute(k_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        k_apply<double><<<grid, 256, sm, st>>>(a, o, TJ, RC);
+        k_apply<double><<<grid, 256, sm, st>>>(aa, o, TJ, RC);
     } else {
         e = cudaFuncSetAttribute(k_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        k_apply<float><<<grid, 256, sm, st>>>(a, o, TJ, RC);
+        k_apply<float><<<grid, 256, sm, st>>>(aa, o, TJ, RC);
     }
     return (int)cudaGetLastError();
 }

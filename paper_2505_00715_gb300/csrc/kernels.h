@@ -51,6 +51,8 @@ struct FarArgs {
     int64_t scratch_per_cta;  // complex units
     unsigned int *counter;  // work queue head
     int64_t *evals;         // [2] regular, tube entries evaluated
+    int *harvest;           // non-null: record face-ACA ranks per (far block, frequency), [nfar][Nu]
+    const int *kpred;       // nullable: predicted face rank per (block id, frequency) [nb][Nu]
 };
 
 int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
@@ -80,6 +82,7 @@ struct ApplyArgs {
     int single_f;          // >= 0: apply one frequency only (W is x [ncols][nrhs])
     int kcap;              // largest far face rank
     int max_near_rows;     // largest row count of a near block
+    int64_t acc_max;       // accumulator size (complex units), set by the launcher
 };
 int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorOut &o, int num_sms);
 int td_launch_tensor_entries(cudaStream_t st, int prec, const TensorOut &o, const int *blocks,
