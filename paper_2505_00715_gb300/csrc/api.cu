@@ -728,7 +728,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                 cudaMemsetAsync(evals, 0, sizeof(int64_t) * 4, ls);
                 cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ls);
                 cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ls);
-                lrc |= td_launch_sing_table(ls, md, op->op, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
+                lrc |= td_launch_sing_table(ls, md, op->op, op->prec, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
             } else if (ph == 1) {
                 lrc |= td_launch_near_entries(ls, md, op->op, op->prec, na, table, ctx->num_sms);
             } else if (ph == 2) {

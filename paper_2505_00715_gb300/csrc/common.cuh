@@ -134,6 +134,19 @@ TD_D void f2_fma(F2 &a, float x, float y) {
     a.c = __fadd_rn(a.c, __fadd_rn(err, e));
     a.s = s;
 }
+// Warp sum of a compensated pair, combined with TwoSum in FP32; read out in FP64.
+TD_D double warp_sum_f2(F2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, v.s, o), c2 = __shfl_xor_sync(0xffffffffu, v.c, o);
+        const float s = __fadd_rn(v.s, s2);
+        const float z = __fsub_rn(s, v.s);
+        const float err = __fadd_rn(__fsub_rn(v.s, __fsub_rn(s, z)), __fsub_rn(s2, z));
+        v.c = __fadd_rn(__fadd_rn(v.c, c2), err);
+        v.s = s;
+    }
+    return (double)v.s + (double)v.c;
+}
+
 template <class T> struct DotAcc;
 template <> struct DotAcc<float> {
     F2 re{0.f, 0.f}, im{0.f, 0.f};
@@ -146,6 +159,9 @@ template <> struct DotAcc<float> {
     }
     TD_D double real() const { return (double)re.s + (double)re.c; }
     TD_D double imag() const { return (double)im.s + (double)im.c; }
+    // sums over the 32 lanes of the warp (every lane gets the result)
+    TD_D double warp_real() const { return warp_sum_f2(re); }
+    TD_D double warp_imag() const { return warp_sum_f2(im); }
 };
 template <> struct DotAcc<double> {
     double re = 0.0, im = 0.0;
@@ -155,6 +171,8 @@ template <> struct DotAcc<double> {
     }
     TD_D double real() const { return re; }
     TD_D double imag() const { return im; }
+    TD_D double warp_real() const { return warp_sum(re); }
+    TD_D double warp_imag() const { return warp_sum(im); }
 };
 
 // Device-side error word: kernels record a code and keep going safely.

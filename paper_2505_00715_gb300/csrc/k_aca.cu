@@ -323,6 +323,9 @@ template <class T>
 struct GramTiles {
     cx<T> A[64][kTI + 1];      // current face: rows t < kf
     cx<T> B[kGCh][kTI + 1];    // factor columns of the previous terms (and of the face itself)
+    const cx<T> *colU[kGCh];   // column descriptors of the current chunk
+    const cx<T> *colV[kGCh];
+    int colD[kGCh];
 };
 
 // eq. norm for the new term l: for every previous term d < l and for d = l,
@@ -342,6 +345,23 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
     const int chmax = max(1, min(kGCh, (kGOut * (int)blockDim.x) / max(kf, 1)));
     for (int g0 = 0; g0 < Kall; g0 += chmax) {
         const int ch = min(chmax, Kall - g0);
+        __syncthreads();
+        for (int c = tid; c < ch; c += blockDim.x) {
+            int d = 0, rem = g0 + c;
+            while (d < l && rem >= S.frank[d]) {
+                rem -= S.frank[d];
+                ++d;
+            }
+            if (d < l) {
+                const cx<T> *Ud = pool + S.foff[d];
+                G.colU[c] = Ud + (int64_t)rem * nI;
+                G.colV[c] = Ud + (int64_t)S.frank[d] * nI + (int64_t)rem * nJ;
+            } else {
+                G.colU[c] = Uw + (int64_t)rem * maxI;
+                G.colV[c] = Vw + (int64_t)rem * maxJ;
+            }
+            G.colD[c] = d;
+        }
         DotAcc<T> au[kGOut], av[kGOut];
         for (int pass = 0; pass < 2; ++pass) {
             const int n = pass ? nJ : nI;
@@ -354,19 +374,8 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
                     G.A[t][xx] = x0 + xx < n ? W[t * sw + x0 + xx] : cx<T>{0, 0};
                 }
                 for (int e = tid; e < ch * kTI; e += blockDim.x) {
-                    const int c = e / kTI, xx = e % kTI, g = g0 + c;
-                    int d = 0, rem = g;
-                    while (d < l && rem >= S.frank[d]) {
-                        rem -= S.frank[d];
-                        ++d;
-                    }
-                    const cx<T> *col;
-                    if (d < l) {
-                        const cx<T> *Ud = pool + S.foff[d];
-                        col = pass ? Ud + (int64_t)S.frank[d] * nI + (int64_t)rem * nJ : Ud + (int64_t)rem * nI;
-                    } else {
-                        col = W + (int64_t)rem * sw;
-                    }
+                    const int c = e / kTI, xx = e % kTI;
+                    const cx<T> *col = pass ? G.colV[c] : G.colU[c];
                     G.B[c][xx] = x0 + xx < n ? col[x0 + xx] : cx<T>{0, 0};
                 }
                 __syncthreads();
@@ -386,12 +395,7 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
         for (int q = 0; q < kGOut; ++q) {
             const int o = tid + q * blockDim.x;
             if (o < kf * ch) {
-                const int g = g0 + o % ch;
-                int d = 0, rem = g;
-                while (d < l && rem >= S.frank[d]) {
-                    rem -= S.frank[d];
-                    ++d;
-                }
+                const int d = G.colD[o % ch];
                 const double ur = au[q].real(), ui = au[q].imag(), vr = av[q].real(), vi = av[q].imag();
                 atomicAdd(&S.gH[d].x, ur * vr - ui * vi);
                 atomicAdd(&S.gH[d].y, ur * vi + ui * vr);
@@ -543,11 +547,7 @@ __global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut
                         DotAcc<T> au, av;
                         for (int i = lane; i < nI; i += 32) au.add(Uw[(int64_t)t * a.maxI + i], Uw[(int64_t)t2 * a.maxI + i]);
                         for (int j = lane; j < nJ; j += 32) av.add(Vw[(int64_t)t * a.maxJ + j], Vw[(int64_t)t2 * a.maxJ + j]);
-                        double gu[2] = {au.real(), au.imag()}, gv[2] = {av.real(), av.imag()};
-                        for (int q = 0; q < 2; ++q) {
-                            gu[q] = warp_sum(gu[q]);
-                            gv[q] = warp_sum(gv[q]);
-                        }
+                        const double gu[2] = {au.warp_real(), au.warp_imag()}, gv[2] = {av.warp_real(), av.warp_imag()};
                         if (lane == 0) {
                             if (t2 < t) {
                                 atomicAdd(&S.nrow[t], gu[0] * gv[0] - gu[1] * gv[1]);

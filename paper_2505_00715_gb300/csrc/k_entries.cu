@@ -149,6 +149,97 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
     }
 }
 
+// Mixed form of the touching-pair table: the transformed coordinates, the
+// Jacobian weights and the cross-lane sums are FP64; the smooth factor
+// e^{-sigma r} (SLP) or e^{-sigma r}(1 + sigma r) (DLP) of every point and
+// frequency runs on the FP32 special-function path (relative error about
+// 3e-7), and each lane's partial sums over its points are FP32.  All FC
+// frequencies of a pass share one evaluation of the point geometry.
+template <int OP, int FC>
+__global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, int npairs, const double *sig,
+                                   int nf, c64 *table) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    constexpr int NV = OP == TD_SLP ? 1 : 3;
+    for (int p = warp; p < npairs; p += nwarps) {
+        int ti = pti[p], tj = ptj[p];
+        if (OP == TD_SLP && ti > tj) {
+            int t = ti;
+            ti = tj;
+            tj = t;
+        }
+        SingGeom G;
+        classify_pair(m, ti, tj, G);
+        const int nq = ss_npoints(G.cls, m.ng);
+        const bool zero = (OP == TD_DLP && G.cls == 3) || G.cls == 0;
+        for (int f0 = 0; f0 < nf; f0 += FC) {
+            float sg[FC][2];
+#pragma unroll
+            for (int j = 0; j < FC; ++j) {
+                const int k = min(f0 + j, nf - 1);
+                sg[j][0] = (float)sig[2 * k];
+                sg[j][1] = (float)sig[2 * k + 1];
+            }
+            c32 acc[FC][NV];
+#pragma unroll
+            for (int j = 0; j < FC; ++j)
+#pragma unroll
+                for (int k = 0; k < NV; ++k) acc[j][k] = {0.f, 0.f};
+            if (!zero) {
+                for (int q = lane; q < nq; q += 32) {
+                    double d[3], w, lam[3];
+                    ss_point(G, q, m.ng, m.gx, m.gw, d, w, lam);
+                    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    double base;
+                    if (OP == TD_SLP) {
+                        base = w / r;
+                    } else {
+                        const double dn = -(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]);
+                        base = w * dn / (r * r * r);
+                    }
+                    const float rf = (float)r, bf = (float)base;
+                    float lf[3] = {(float)lam[0], (float)lam[1], (float)lam[2]};
+#pragma unroll
+                    for (int j = 0; j < FC; ++j) {
+                        const c32 e = expm_sr(sg[j][0], sg[j][1], rf);
+                        c32 v;
+                        if (OP == TD_SLP) {
+                            v = {bf * e.x, bf * e.y};
+                        } else {
+                            const float pr = fmaf(sg[j][0], rf, 1.0f), pi = sg[j][1] * rf;
+                            v = {bf * (pr * e.x - pi * e.y), bf * (pr * e.y + pi * e.x)};
+                        }
+#pragma unroll
+                        for (int k = 0; k < NV; ++k) {
+                            const float lk = OP == TD_SLP ? 1.0f : lf[k];
+                            acc[j][k].x = fmaf(lk, v.x, acc[j][k].x);
+                            acc[j][k].y = fmaf(lk, v.y, acc[j][k].y);
+                        }
+                    }
+                }
+            }
+            const double inv4pi = 1.0 / TD_FOUR_PI;
+#pragma unroll
+            for (int j = 0; j < FC; ++j) {
+                c64 outv[NV];
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    outv[k] = {warp_sum((double)acc[j][k].x) * inv4pi, warp_sum((double)acc[j][k].y) * inv4pi};
+                if (lane == 0 && f0 + j < nf) {
+                    c64 *o = table + ((int64_t)p * nf + f0 + j) * 3;
+                    const c64 z = {0.0, 0.0};
+                    o[0] = o[1] = o[2] = z;
+                    if (OP == TD_SLP)
+                        o[0] = outv[0];
+                    else
+                        for (int k = 0; k < NV; ++k) o[G.loc[k]] = zero ? z : outv[k];
+                }
+            }
+        }
+    }
+}
+
 // ---- near-field dense entries -------------------------------------------------
 // Regular pair at FC frequencies with the geometry computed once per point
 // pair (test triangle in registers, trial points streamed from the tables).
@@ -321,10 +412,17 @@ int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const
     return (int)cudaGetLastError();
 }
 
-int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, const int *pti, const int *ptj,
+int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, const int *pti, const int *ptj,
                          int npairs, const double *sig, int nf, c64 *table, int num_sms) {
     if (npairs == 0) return 0;
     int grid = std::min((npairs + 3) / 4, num_sms * 8);
+    if (prec == TDBEM_MIXED) {
+        if (op == TD_SLP)
+            k_sing_table_mixed<TD_SLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+        else
+            k_sing_table_mixed<TD_DLP, 6><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+        return (int)cudaGetLastError();
+    }
     if (op == TD_SLP)
         k_sing_table<TD_SLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
     else

@@ -58,7 +58,7 @@ struct FarArgs {
 int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
                       const int *rows, int64_t nr, const int *cols, int64_t nc, const int *fidx,
                       int64_t nf, void *out);
-int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, const int *pti, const int *ptj,
+int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, const int *pti, const int *ptj,
                          int npairs, const double *sig, int nf, c64 *table, int num_sms);
 int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const NearArgs &a,
                            const c64 *table, int num_sms);
