@@ -165,6 +165,30 @@ int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const 
                   int64_t nr, const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf,
                   void *out);
 
+/* Allocation-free variant of tdbem_entries (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory at call time: code
+ * running while a stream is captured into a CUDA graph, where cudaMalloc and
+ * cudaFree are not allowed, and applications whose device memory is reserved
+ * up front by their own allocator).  Same arguments, kernel and results as
+ * tdbem_entries; the few scratch values of a call (quadrature nodes, scaled
+ * frequencies) live in one fixed device array of the library instead of
+ * buffers allocated per call.
+ *   - No cudaMalloc, cudaFree or other allocating call is made.
+ *   - The frequency set may have at most TDBEM_NOALLOC_MAX_NQ points;
+ *     larger sets return TDBEM_ERR_ARG with a message.
+ *   - The first call on a device looks up the device address of the fixed
+ *     array (once per device); make that first call before any stream
+ *     capture.  The array (about 132 KB) stays allocated on every device
+ *     that loaded the library until the process exits.
+ *   - All calls share the array and it keeps the last call's contents; calls
+ *     ordered on one stream are safe, calls that overlap on the GPU (other
+ *     streams, other threads) race on it.
+ *   - Asynchronous: returns after queuing the work on the context's stream. */
+#define TDBEM_NOALLOC_MAX_NQ 8192
+int tdbem_entries_noalloc(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const int32_t *rows,
+                          int64_t nr, const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf,
+                          void *out);
+
 /* ---- compression (Sec. 4, Algorithm 1 per block, eq. norm) ------------------- */
 /* 3D-ACA of the operator tensor over the Nu unique frequencies of f on every
  * block of `tree` (which must have been built with test P0 and trial P0 for

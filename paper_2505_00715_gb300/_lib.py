@@ -66,6 +66,8 @@ EXPORTS = {
     "tdbem_tree_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_entries": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                 C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
+    "tdbem_entries_noalloc": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
     "tdbem_compress": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p,
                                  C.POINTER(AcaCfg), C.POINTER(C.c_void_p)]),
     "tdbem_tensor_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
