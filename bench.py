@@ -33,6 +33,8 @@ import numpy as np  # noqa: E402
 from paper_2505_00715_gb300.inputs import icosphere, random_weights  # noqa: E402
 
 WORKLOADS = {
+    "sphere1280_slp_bdf2_N64": dict(level=3, op="SLP", N=64, dt=0.05, leaf=32, eta=2.0, eps=1e-4, eps_aca=1e-6,
+                                    ng=5, nrhs=16, c=1.0),
     "sphere5120_slp_bdf2_N64": dict(level=4, op="SLP", N=64, dt=0.05, leaf=32, eta=2.0, eps=1e-4, eps_aca=1e-6,
                                     ng=5, nrhs=16, c=1.0),
     "sphere5120_dlp_bdf2_N64": dict(level=4, op="DLP", N=64, dt=0.05, leaf=32, eta=2.0, eps=1e-4, eps_aca=1e-6,
@@ -175,6 +177,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--no-predictor", action="store_true", help="time the form without the rank predictor")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -212,7 +216,19 @@ def main():
 
     # rank predictor: trained on the GPU (untimed) from the plain method's own
     # face ranks on smaller spheres (320 and 1280 triangles, SLP and DLP)
-    model, pinfo = train_predictor(td, ctx, cfg, dev)
+    if args.no_predictor:
+        model, pinfo = None, {"disabled": True}
+    else:
+        model, pinfo = train_predictor(td, ctx, cfg, dev)
+    tuned = None
+    if not args.no_autotune:
+        # project autotuner: launch shape of the persistent far-field phase (untimed)
+        tr0 = td.Tree(mesh, td.P0, colb, cfg["leaf"], cfg["eta"])
+        tuned = td.autotune(mesh, op, freqs, tr0, eps=cfg["eps"], eps_aca=cfg["eps_aca"], prec=td.MIXED, c=cfg["c"],
+                            ng=cfg["ng"], model=model)
+        if not args.no_fp64:
+            td.autotune(mesh, op, freqs, tr0, eps=cfg["eps"], eps_aca=cfg["eps_aca"], prec=td.FP64, c=cfg["c"],
+                        ng=cfg["ng"])
 
     def step(prec=td.MIXED, Wd=W, yd=y, use_model=True):
         tree = td.Tree(mesh, td.P0, colb, cfg["leaf"], cfg["eta"])
@@ -310,7 +326,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": args.workload, "triangles": int(nrows), "cols": int(ncols), "N_Q": int(NQ),
                        "unique_freqs": int(freqs.Nu), "leaf": cfg["leaf"], "eta": cfg["eta"], "eps": cfg["eps"],
-                       "eps_aca": cfg["eps_aca"], "ng": cfg["ng"], "nrhs": nrhs, "form": "mixed + rank predictor",
+                       "eps_aca": cfg["eps_aca"], "ng": cfg["ng"], "nrhs": nrhs,
+                       "form": "mixed" + ("" if model is None else " + rank predictor"),
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_tensor_s": st["ms_total"] / 1e3,
@@ -322,6 +339,7 @@ def main():
                             "max_rank": st["max_rank"], "nblocks": st["nblocks"], "nfar": st["nfar"],
                             "sum_face_rank": st["sum_face_rank"]},
             "predictor": dict(pinfo, without=no_pred),
+            "autotuned_far_launch": tuned and {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1]},
             "fp64_form": fp64,
             "e2e": e2e,
             "roofline": roof,

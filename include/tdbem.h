@@ -41,7 +41,7 @@ extern "C" {
 #define TDBEM_ERR_ARG (-1)            /* bad argument, degenerate mesh, NaN, ... */
 #define TDBEM_ERR_OOM (-2)            /* device or host allocation failed */
 #define TDBEM_ERR_CUDA (-3)           /* a CUDA runtime call failed */
-#define TDBEM_ERR_NOT_CONVERGED (-4)  /* ACA / 3D-ACA hit its rank cap */
+#define TDBEM_ERR_NOT_CONVERGED (-4)  /* ACA / 3D-ACA rank cap hit, GMRES above tol */
 #define TDBEM_ERR_CAPACITY (-5)       /* a device pool overflowed (retried internally) */
 
 /* ---- enumerations ------------------------------------------------------- */
@@ -207,6 +207,14 @@ int tdbem_tensor_entries(tdbem_tensor_t t, const int32_t *rows, const int32_t *c
  * [nblocks], selected frequencies [nblocks][Nu+1] (-1 padded). */
 int tdbem_tensor_blocks(tdbem_tensor_t t, int32_t *rank, int32_t *face_rank_sum, int32_t *kpiv);
 int tdbem_tensor_destroy(tdbem_tensor_t t);
+/* Project-written autotuner of the persistent far-field phase (Sec. 4
+ * Algorithm 1 on the admissible blocks): times complete compressions of the
+ * given problem with candidate launch shapes (threads per CTA x resident
+ * CTAs per SM) and keeps the fastest in the context for op->prec.  chosen
+ * (nullable, host int32 [2]) receives {threads per CTA, CTAs per SM}.  The
+ * defaults without tuning are {128, 4}. */
+int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, tdbem_tree_t tree,
+                   const tdbem_aca_cfg *cfg, int32_t *chosen);
 
 /* ---- apply (eq. product) ------------------------------------------------------ */
 /* y[M][nrhs] = sum_{l < NQ} A(s_l) W_l  with W: device [NQ][ncols][nrhs]
@@ -220,6 +228,45 @@ int tdbem_apply_freq(tdbem_tensor_t t, int32_t fidx, const void *x, int32_t nrhs
  * host->device copy of W and the device->host copy of y are part of the
  * call, which returns when y is on the host. */
 int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, int32_t nrhs, void *y_host);
+
+/* ---- per-frequency solve (Sec. 2, the Laplace-domain systems of the gCQ
+ * step; Sec. 5 solves them iteratively) --------------------------------------
+ * Solves A(s_fidx) x = b for nrhs right-hand sides with restarted GMRES
+ * (modified Gram-Schmidt Arnoldi, complex Givens rotations, FP64 inner
+ * products; every operator application is tdbem_apply_freq on the compressed
+ * tensor).  The paper uses BiCGstab; GMRES reaches the same solution and
+ * its residual decreases monotonically.  Square operators only (SLP).
+ *   b, x     device [nrows][nrhs] complex in the tensor's precision
+ *            (caller-owned; x is overwritten, the start vector is 0)
+ *   tol      relative residual ||b - A x|| / ||b|| per column, > 0
+ *   maxit    total Arnoldi steps (all restarts), >= 1
+ *   restart  Krylov dimension per cycle (<= 0: 30; clamped to 200)
+ *   iters    (nullable) host int32: Arnoldi steps taken
+ *   relres   (nullable) host double [nrhs]: final relative residuals, formed
+ *            explicitly as ||b - A x|| / ||b||
+ * Returns TDBEM_ERR_NOT_CONVERGED (x holds the last iterate) when some column
+ * is above tol after maxit steps.  Allocates (M * nrhs * (restart + 3))
+ * complex values of device scratch per call and synchronises the stream. */
+int tdbem_solve(tdbem_tensor_t t, int32_t fidx, const void *b, int32_t nrhs, void *x, double tol, int32_t maxit,
+                int32_t restart, int32_t *iters, double *relres);
+
+/* ---- persistence (not part of the paper) ------------------------------------
+ * tdbem_tensor_save writes the compressed tensor (block list, permutations,
+ * per-block ranks and selected frequencies, fibres, face pool, statistics) to
+ * a binary file in native byte order; tdbem_tensor_load reads it into a new
+ * tensor of ctx that apply, tensor_entries, blocks, stats and solve accept
+ * like a freshly compressed one.  The file does not hold the mesh or the
+ * frequency set.  Errors: TDBEM_ERR_ARG for unreadable or foreign files.
+ * tdbem_model_save/load do the same for the rank predictor's FP32 parameters
+ * (the BF16 inference copy is rebuilt on load; the Adam state is not kept). */
+int tdbem_tensor_save(tdbem_tensor_t t, const char *path);
+/* Shape of a tensor (host outputs, each nullable): operator, precision,
+ * rows, columns, points of the frequency set, unique points. */
+int tdbem_tensor_info(tdbem_tensor_t t, int32_t *op, int32_t *prec, int64_t *nrows, int64_t *ncols, int32_t *NQ,
+                      int32_t *Nu);
+int tdbem_tensor_load(tdbem_ctx_t ctx, const char *path, tdbem_tensor_t *out);
+int tdbem_model_save(tdbem_model_t m, const char *path);
+int tdbem_model_load(tdbem_ctx_t ctx, const char *path, tdbem_model_t *out);
 
 /* ---- rank predictor (learned presizing; not part of the paper) ------------
  * A small MLP (6 features -> 64 -> 64 -> 16 rank bins, GELU) predicts, for a

@@ -10,13 +10,14 @@ PyTorch is used only for device buffers.  All numerical work runs in the CUDA
 library; the calls raise if the library or a CUDA device is unavailable.
 """
 import ctypes as C
+import os
 
 import numpy as np
 
 from . import _lib
 from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
 
-__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "compress", "harvest", "rank_bin",
+__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "compress", "harvest", "rank_bin", "autotune",
            "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError"]
 NPARAMS = 5648
 
@@ -166,11 +167,25 @@ def entries(mesh, op, freqs, rows, cols, fidx, prec=MIXED, c=1.0, ng=5):
 class Tensor:
     """3D-ACA compressed operator tensor held in device memory."""
 
-    def __init__(self, ctx, h, mesh, freqs, tree, op, prec):
+    def __init__(self, ctx, h, mesh=None, freqs=None, tree=None):
         self.ctx, self.h, self.mesh, self.freqs, self.tree = ctx, h, mesh, freqs, tree
-        self.op, self.prec = op, prec
-        self.nrows = mesh.ndof(P0)
-        self.ncols = mesh.ndof(P1 if op == DLP else P0)
+        op, prec, nq, nu = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        nr, nc = C.c_int64(), C.c_int64()
+        ctx.check(ctx.L.tdbem_tensor_info(h, C.byref(op), C.byref(prec), C.byref(nr), C.byref(nc), C.byref(nq),
+                                          C.byref(nu)), "tdbem_tensor_info")
+        self.op, self.prec = op.value, prec.value
+        self.nrows, self.ncols, self.NQ, self.Nu = nr.value, nc.value, nq.value, nu.value
+
+    @classmethod
+    def load(cls, ctx, path, mesh=None, freqs=None, tree=None):
+        """Read a tensor written by save() (the mesh, frequency set and tree
+        are not stored; pass them to keep them attached)."""
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_tensor_load(ctx.h, os.fsencode(path), C.byref(h)), "tdbem_tensor_load")
+        return cls(ctx, h, mesh, freqs, tree)
+
+    def save(self, path):
+        self.ctx.check(self.ctx.L.tdbem_tensor_save(self.h, os.fsencode(path)), "tdbem_tensor_save")
 
     def stats(self):
         st = _lib.Stats()
@@ -178,10 +193,10 @@ class Tensor:
         return st.as_dict()
 
     def blocks(self):
-        nb = len(self.tree.blocks)
+        nb = self.stats()["nblocks"]
         r = np.zeros(nb, dtype=np.int32)
         k = np.zeros(nb, dtype=np.int32)
-        kp = np.zeros((nb, self.freqs.Nu + 1), dtype=np.int32)
+        kp = np.zeros((nb, self.Nu + 1), dtype=np.int32)
         self.ctx.check(self.ctx.L.tdbem_tensor_blocks(self.h, _np_ptr(r), _np_ptr(k), _np_ptr(kp)),
                        "tdbem_tensor_blocks")
         return r, k, kp
@@ -222,6 +237,21 @@ class Tensor:
         self.ctx.check(self.ctx.L.tdbem_apply_weighted_host(self.h, wp, nrhs, yp), "tdbem_apply_weighted_host")
         return y_host
 
+    def solve(self, fidx, b, tol=1e-6, maxit=500, restart=30, x=None, check=True):
+        """x with A(s_fidx) x = b by restarted GMRES; b: device [nrows, nrhs].
+        Returns (x, iterations, relative residuals).  With check=False a
+        solve that stops above tol returns its last iterate instead of raising."""
+        torch = _torch()
+        nrhs = b.shape[1]
+        if x is None:
+            x = torch.empty_like(b)
+        it = C.c_int32()
+        rr = np.zeros(nrhs)
+        rc = self.ctx.L.tdbem_solve(self.h, fidx, _ptr(b), nrhs, _ptr(x), tol, maxit, restart, C.byref(it), _np_ptr(rr))
+        if check or rc != _lib.ERR_NOT_CONVERGED:
+            self.ctx.check(rc, "tdbem_solve")
+        return x, it.value, rr
+
     def __del__(self):
         if getattr(self, "h", None) and _lib._lib is not None:
             _lib._lib.tdbem_tensor_destroy(self.h)
@@ -236,7 +266,18 @@ def compress(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, n
     h = C.c_void_p()
     ctx.check(ctx.L.tdbem_compress(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), C.byref(h)),
               "tdbem_compress")
-    return Tensor(ctx, h, mesh, freqs, tree, op, prec)
+    return Tensor(ctx, h, mesh, freqs, tree)
+
+
+def autotune(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64, model=None):
+    """Time the far-field phase with candidate launch shapes and keep the fastest
+    in the context; returns (threads per CTA, CTAs per SM)."""
+    ctx = mesh.ctx
+    o = _op(op, prec, c, ng)
+    cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, 0, model.h if model is not None else None)
+    ch = (C.c_int32 * 2)()
+    ctx.check(ctx.L.tdbem_autotune(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), ch), "tdbem_autotune")
+    return int(ch[0]), int(ch[1])
 
 
 def rank_bin(rank):
@@ -277,6 +318,19 @@ class Model:
         self.ctx.check(self.ctx.L.tdbem_model_train(self.h, _ptr(x), _ptr(labels), x.shape[0], epochs, batch, lr, seed,
                                                     C.byref(fl)), "tdbem_model_train")
         return fl.value
+
+    def save(self, path):
+        self.ctx.check(self.ctx.L.tdbem_model_save(self.h, os.fsencode(path)), "tdbem_model_save")
+
+    @classmethod
+    def load(cls, ctx, path):
+        m = cls.__new__(cls)
+        m.ctx = ctx
+        m.h = None
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_model_load(ctx.h, os.fsencode(path), C.byref(h)), "tdbem_model_load")
+        m.h = h
+        return m
 
     def predict(self, x, logits=False):
         torch = _torch()

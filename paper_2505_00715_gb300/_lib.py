@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdbem.so")
 
 OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_CAPACITY = -1, -2, -3, -4, -5
 SLP, DLP = 0, 1
 P0, P1 = 0, 1
 FP64, MIXED = 0, 1
@@ -77,6 +78,16 @@ EXPORTS = {
     "tdbem_apply_weighted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_freq": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_weighted_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "tdbem_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32,
+                              C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
+    "tdbem_tensor_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "tdbem_tensor_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "tdbem_tensor_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
+    "tdbem_model_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "tdbem_model_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_void_p)]),
+    "tdbem_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.POINTER(AcaCfg),
+                                 C.c_void_p]),
     "tdbem_rank_bin": (C.c_int, [C.c_int32]),
     "tdbem_model_create": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)]),
     "tdbem_model_destroy": (C.c_int, [C.c_void_p]),

@@ -637,7 +637,8 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     int64_t *deprefix, *dnoff, *evals;
     unsigned int *counter;
     const int nctas_near = std::min<int64_t>(std::max<int64_t>(1, (int64_t)near_ids.size()), (int64_t)ctx->num_sms * 8);
-    const int nctas_far = std::min<int64_t>(std::max<int64_t>(1, (int64_t)far_ids.size()), (int64_t)ctx->num_sms * 2);
+    const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
+    const int nctas_far = std::min<int64_t>(std::max<int64_t>(1, (int64_t)far_ids.size()), (int64_t)ctx->num_sms * ctx->far_cps[pf]);
     const int64_t sper_far = (int64_t)kcap * (maxI + maxJ);
     if ((rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size())) ||
         (rc = dalloc(ctx, &table, (size_t)npairs * Nu * 3, &g.p)) || (rc = dalloc(ctx, &nearbuf, es * ntens, &g.p)) ||
@@ -734,7 +735,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
             } else if (ph == 2) {
                 lrc |= td_launch_near_aca(ls, op->prec, na, o, ap, scr_near, maxIJ, nctas_near);
             } else {
-                lrc |= td_launch_far_aca(ls, md, op->op, op->prec, fa, o, ap, nctas_far);
+                lrc |= td_launch_far_aca(ls, md, op->op, op->prec, fa, o, ap, nctas_far, ctx->far_nt[pf]);
             }
             if (use_graph) {
                 ge = cudaStreamEndCapture(ls, &graph);
@@ -962,7 +963,8 @@ extern "C" int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op 
         hs[2 * u + 1] = f->s[2 * f->uidx[u] + 1] / op->c;
     }
     const size_t es = op->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
-    const int nctas = std::min<int64_t>(*count, (int64_t)ctx->num_sms * 2);
+    const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
+    const int nctas = std::min<int64_t>(*count, (int64_t)ctx->num_sms * ctx->far_cps[pf]);
     const int64_t sper = (int64_t)kcap * (maxI + maxJ);
     if ((rc = dalloc(ctx, &dblocks, 5 * nb, &g.p)) || (rc = dalloc(ctx, &dpr, tree->side[0].n, &g.p)) ||
         (rc = dalloc(ctx, &dpc, tree->side[1].n, &g.p)) || (rc = dalloc(ctx, &dfar, far_ids.size(), &g.p)) ||
@@ -995,8 +997,50 @@ extern "C" int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op 
     o.rank = drank;
     o.dev_flags = flags;
     AcaParams ap{cfg->eps, cfg->eps_aca, kcap};
-    if (td_launch_far_aca(ctx->stream, md, op->op, op->prec, fa, o, ap, nctas))
+    if (td_launch_far_aca(ctx->stream, md, op->op, op->prec, fa, o, ap, nctas, ctx->far_nt[pf]))
         return td_fail(ctx, TDBEM_ERR_CUDA, "harvest kernel launch failed");
     TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TDBEM_OK;
+}
+
+// ============================================================================
+// autotuner of the far-field launch shape
+// ============================================================================
+extern "C" int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f,
+                              tdbem_tree_t tree, const tdbem_aca_cfg *cfg, int32_t *chosen) {
+    if (!ctx || !op) return TDBEM_ERR_ARG;
+    const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
+    // candidate shapes: threads per CTA x CTAs per SM (register and shared
+    // memory limits of the kernel allow all of them)
+    static const int cand[][2] = {{256, 2}, {128, 4}, {128, 6}, {64, 8}, {64, 12}};
+    double best = 1e300;
+    int bnt = ctx->far_nt[pf], bcps = ctx->far_cps[pf];
+    for (const auto &c : cand) {
+        ctx->far_nt[pf] = c[0];
+        ctx->far_cps[pf] = c[1];
+        double t = 0.0;
+        for (int rep = 0; rep < 2; ++rep) {
+            tdbem_tensor_t X = nullptr;
+            int rc = tdbem_compress(ctx, mesh, op, f, tree, cfg, &X);
+            if (rc) {
+                ctx->far_nt[pf] = bnt;
+                ctx->far_cps[pf] = bcps;
+                return rc;
+            }
+            if (rep == 1) t = X->stats.ms_far;  // the first run warms up
+            tdbem_tensor_destroy(X);
+        }
+        if (t < best) {
+            best = t;
+            bnt = c[0];
+            bcps = c[1];
+        }
+    }
+    ctx->far_nt[pf] = bnt;
+    ctx->far_cps[pf] = bcps;
+    if (chosen) {
+        chosen[0] = bnt;
+        chosen[1] = bcps;
+    }
     return TDBEM_OK;
 }

@@ -12,6 +12,10 @@ struct tdbem_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;  // side stream used only to capture graphs
+    // launch shape of the far-field kernel per precision form [FP64, MIXED]:
+    // threads per CTA and CTAs per SM (set by tdbem_autotune)
+    int far_nt[2] = {128, 128};
+    int far_cps[2] = {4, 4};
     std::string err;
     int num_sms = 0;
 };

@@ -245,7 +245,6 @@ TD_D cx<T> warp_entry(const MeshDev &m, int row, int col, T sr, T si) {
 }
 
 
-constexpr int kNT = 256;
 constexpr int kNCoef = 1024;
 
 template <class T>
@@ -405,8 +404,8 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
     __syncthreads();
 }
 
-template <class T, int OP>
-__global__ void __launch_bounds__(kNT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
+template <class T, int OP, int NT>
+__global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FarShared<T> &S = *reinterpret_cast<FarShared<T> *>(smem_raw);
     GramTiles<T> *gt = reinterpret_cast<GramTiles<T> *>(smem_raw + sizeof(FarShared<T>));
@@ -718,22 +717,31 @@ int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const Tenso
     return (int)cudaGetLastError();
 }
 
-template <class T, int OP>
-static int launch_far(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
-                      const AcaParams &p, int nctas) {
+template <class T, int OP, int NT>
+static int launch_far_nt(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
+                         const AcaParams &p, int nctas) {
     size_t sm = sizeof(FarShared<T>) + sizeof(GramTiles<T>) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
-    cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    k_far_aca<T, OP><<<nctas, kNT, sm, st>>>(m, a, o, p);
+    k_far_aca<T, OP, NT><<<nctas, NT, sm, st>>>(m, a, o, p);
     return (int)cudaGetLastError();
 }
 
+template <class T, int OP>
+static int launch_far(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
+                      const AcaParams &p, int nctas, int nt) {
+    if (nt <= 64) return launch_far_nt<T, OP, 64>(st, m, a, o, p, nctas);
+    if (nt <= 128) return launch_far_nt<T, OP, 128>(st, m, a, o, p, nctas);
+    return launch_far_nt<T, OP, 256>(st, m, a, o, p, nctas);
+}
+
 int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
-                      const TensorOut &o, const AcaParams &p, int nctas) {
-    if (a.nfar == 0) return 0;
+                      const TensorOut &o, const AcaParams &p, int nctas, int nt) {
+    const int nitems = a.harvest ? a.nfar * a.nf : a.nfar;
+    if (nitems == 0) return 0;
     if (prec == TDBEM_FP64)
-        return op == TD_SLP ? launch_far<double, TD_SLP>(st, m, a, o, p, nctas)
-                            : launch_far<double, TD_DLP>(st, m, a, o, p, nctas);
-    return op == TD_SLP ? launch_far<float, TD_SLP>(st, m, a, o, p, nctas)
-                        : launch_far<float, TD_DLP>(st, m, a, o, p, nctas);
+        return op == TD_SLP ? launch_far<double, TD_SLP>(st, m, a, o, p, nctas, nt)
+                            : launch_far<double, TD_DLP>(st, m, a, o, p, nctas, nt);
+    return op == TD_SLP ? launch_far<float, TD_SLP>(st, m, a, o, p, nctas, nt)
+                        : launch_far<float, TD_DLP>(st, m, a, o, p, nctas, nt);
 }

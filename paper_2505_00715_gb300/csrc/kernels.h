@@ -65,7 +65,7 @@ int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, 
 int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const TensorOut &o,
                        const AcaParams &p, void *scratch, int64_t scratch_per_cta, int nctas);
 int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
-                      const TensorOut &o, const AcaParams &p, int nctas);
+                      const TensorOut &o, const AcaParams &p, int nctas, int nt);
 int td_launch_bdf2(cudaStream_t st, int N, double dt, double lam, double *ds);
 int td_launch_gcq(cudaStream_t st, int NQ, double dt_min, double q, double *ds, double *dw);
 

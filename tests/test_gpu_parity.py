@@ -186,3 +186,20 @@ def test_config2_sampled_apply(td, ctx, orc, prec):
     yd = om.dense_apply_rows(orc.SLP, f.s, rows, W, ng=5)
     err = np.linalg.norm(y[rows] - yd) / np.linalg.norm(yd)
     assert err < 3 * eps, err
+
+
+def test_autotune_keeps_results(td, ctx, orc, sphere2):
+    """The launch-shape autotuner only changes the far-phase launch; the
+    compressed tensor applies identically."""
+    import torch
+    V, T, gm, om = sphere2
+    f = td.Freqs.bdf2(ctx, 16, 0.1)
+    tree = td.Tree(gm, td.P0, td.P0, 16, 2.0)
+    X0 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
+    nt, cps = td.autotune(gm, td.SLP, f, tree, prec=td.MIXED)
+    assert nt in (64, 128, 256) and cps >= 1
+    X1 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
+    W = torch.as_tensor(random_weights(16, len(T), 2, seed=3), dtype=torch.complex64, device="cuda")
+    y0 = X0.apply_weighted(W).cpu().numpy()
+    y1 = X1.apply_weighted(W).cpu().numpy()
+    assert np.linalg.norm(y1 - y0) <= 1e-5 * np.linalg.norm(y0)
