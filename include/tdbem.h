@@ -276,7 +276,7 @@ int tdbem_model_load(tdbem_ctx_t ctx, const char *path, tdbem_model_t *out);
  * face pool and to run the first (lower bin edge) ACA steps of each face
  * without per-step norm checks; their norms are then formed in one batch and
  * the adaptive stopping rule picks the same rank it would have picked step by
- * step (it stays the judge; under-predicted faces simply continue).
+ * step (the criterion still decides; under-predicted faces simply continue).
  * Bins: rank <= 1, 2, 3, 4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64, > 64.
  * Features (dimensionless): log(diam_I/dist), log(diam_J/dist), log(dist/h),
  * min(diam)/dist, log(1 + Re(s) dist/c), log(1 + |Im(s)| dist/c), h the mean

@@ -1010,9 +1010,10 @@ extern "C" int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                               tdbem_tree_t tree, const tdbem_aca_cfg *cfg, int32_t *chosen) {
     if (!ctx || !op) return TDBEM_ERR_ARG;
     const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
-    // candidate shapes: threads per CTA x CTAs per SM (register and shared
-    // memory limits of the kernel allow all of them)
-    static const int cand[][2] = {{256, 2}, {128, 4}, {128, 6}, {64, 8}, {64, 12}};
+    // candidate shapes: threads per CTA x CTAs per SM (CTAs beyond what the
+    // registers and shared memory of an SM hold start only when resident ones
+    // exit, i.e. once the work queue is empty)
+    static const int cand[][2] = {{256, 2}, {128, 4}, {128, 5}, {64, 8}, {64, 10}, {64, 16}};
     double best = 1e300;
     int bnt = ctx->far_nt[pf], bcps = ctx->far_cps[pf];
     for (const auto &c : cand) {

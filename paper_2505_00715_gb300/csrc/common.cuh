@@ -58,18 +58,34 @@ struct ArgMaxD {
     int i;
 };
 TD_D bool am_better(double v, int i, double bv, int bi) { return v > bv || (v == bv && i < bi); }
+TD_D bool am_better(float v, int i, float bv, int bi) { return v > bv || (v == bv && i < bi); }
 template <class AM>
 TD_D AM warp_argmax(AM a) {
     for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, (double)a.v, o);
-        int oi = __shfl_xor_sync(0xffffffffu, a.i, o);
+        const auto ov = __shfl_xor_sync(0xffffffffu, a.v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, a.i, o);
         if (am_better(ov, oi, a.v, a.i)) {
-            a.v = (decltype(a.v))ov;
+            a.v = ov;
             a.i = oi;
         }
     }
     return a;
 }
+
+// Pivot key of a complex value: a strictly increasing function of |v|.  In
+// FP32 it is |v| itself, formed without squaring (|v|^2 underflows for
+// entries below ~1e-19 that are still representable); in FP64 |v|^2.
+TD_D float pivot_key(cx<float> v) {
+    const float a = fabsf(v.x), b = fabsf(v.y);
+    const float hi = fmaxf(a, b), lo = fminf(a, b);
+    if (!(hi > 0.f)) return 0.f;
+    const float q = __fdividef(lo, hi);
+    return hi * sqrtf(fmaf(q, q, 1.f));
+}
+TD_D double pivot_key(cx<double> v) { return v.x * v.x + v.y * v.y; }
+template <class T> struct AmOf;
+template <> struct AmOf<float> { using type = ArgMax; };
+template <> struct AmOf<double> { using type = ArgMaxD; };
 
 // Block-wide arg-max; `red` is shared scratch of >= 32 entries.  All threads
 // receive the result.  Must be called by every thread of the block.
@@ -116,63 +132,25 @@ TD_D void block_sum(double *v, double *red) {
     __syncthreads();
 }
 
-// Compensated ("twice the working precision") accumulation of products of
-// FP32 numbers on the FP32 pipe: TwoProd by FMA and TwoSum (Ogita, Rump and
-// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005).  The
-// pair (s, c) represents s + c; the result is read out in FP64.  For FP64
-// inputs the plain FP64 accumulation is used.
-struct F2 {
-    float s, c;
-};
-// (the _rn intrinsics keep the compiler from contracting these steps into FMAs)
-TD_D void f2_fma(F2 &a, float x, float y) {
-    const float p = __fmul_rn(x, y);
-    const float e = fmaf(x, y, -p);
-    const float s = __fadd_rn(a.s, p);
-    const float z = __fsub_rn(s, a.s);
-    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, z)), __fsub_rn(p, z));
-    a.c = __fadd_rn(a.c, __fadd_rn(err, e));
-    a.s = s;
-}
-// Warp sum of a compensated pair, combined with TwoSum in FP32; read out in FP64.
-TD_D double warp_sum_f2(F2 v) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, v.s, o), c2 = __shfl_xor_sync(0xffffffffu, v.c, o);
-        const float s = __fadd_rn(v.s, s2);
-        const float z = __fsub_rn(s, v.s);
-        const float err = __fadd_rn(__fsub_rn(v.s, __fsub_rn(s, z)), __fsub_rn(s2, z));
-        v.c = __fadd_rn(__fadd_rn(v.c, c2), err);
-        v.s = s;
-    }
-    return (double)v.s + (double)v.c;
-}
-
-template <class T> struct DotAcc;
-template <> struct DotAcc<float> {
-    F2 re{0.f, 0.f}, im{0.f, 0.f};
+// Inner-product accumulator x * conj(y) in the working precision (FP32 in the
+// mixed form, FP64 in the FP64 form).  The stopping decisions built on these
+// sums are taken in FP64; an FP32 sum of n products carries a relative error
+// of about n * 6e-8 of the sum of magnitudes, far below the tolerances
+// (1e-4 / 1e-6) the norms are compared against.
+template <class T> struct DotAcc {
+    T re = 0, im = 0;
     // += x * conj(y)
-    TD_D void add(cx<float> x, cx<float> y) {
-        f2_fma(re, x.x, y.x);
-        f2_fma(re, x.y, y.y);
-        f2_fma(im, x.y, y.x);
-        f2_fma(im, -x.x, y.y);
-    }
-    TD_D double real() const { return (double)re.s + (double)re.c; }
-    TD_D double imag() const { return (double)im.s + (double)im.c; }
-    // sums over the 32 lanes of the warp (every lane gets the result)
-    TD_D double warp_real() const { return warp_sum_f2(re); }
-    TD_D double warp_imag() const { return warp_sum_f2(im); }
-};
-template <> struct DotAcc<double> {
-    double re = 0.0, im = 0.0;
-    TD_D void add(cx<double> x, cx<double> y) {
+    TD_D void add(cx<T> x, cx<T> y) {
         re = fma(x.x, y.x, fma(x.y, y.y, re));
         im = fma(x.y, y.x, fma(-x.x, y.y, im));
     }
-    TD_D double real() const { return re; }
-    TD_D double imag() const { return im; }
-    TD_D double warp_real() const { return warp_sum(re); }
-    TD_D double warp_imag() const { return warp_sum(im); }
+    TD_D double real() const { return (double)re; }
+    TD_D double imag() const { return (double)im; }
+    // sums over the 32 lanes of the warp (every lane gets the result)
+    TD_D T warp_re() const { return warp_sum(re); }
+    TD_D T warp_im() const { return warp_sum(im); }
+    TD_D double warp_real() const { return (double)warp_sum(re); }
+    TD_D double warp_imag() const { return (double)warp_sum(im); }
 };
 
 // Device-side error word: kernels record a code and keep going safely.

@@ -15,7 +15,7 @@ struct tdbem_ctx {
     // launch shape of the far-field kernel per precision form [FP64, MIXED]:
     // threads per CTA and CTAs per SM (set by tdbem_autotune)
     int far_nt[2] = {128, 128};
-    int far_cps[2] = {4, 4};
+    int far_cps[2] = {4, 5};
     std::string err;
     int num_sms = 0;
 };

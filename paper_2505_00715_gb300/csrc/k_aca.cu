@@ -66,15 +66,19 @@ TD_D cx<T> lowrank_at(const cx<T> *U, int64_t su, const cx<T> *V, int64_t sv, in
 template <class T>
 __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaParams p,
                                                   cx<T> *scratch, int64_t sper) {
+    using AM = typename AmOf<T>::type;
     __shared__ cx<T> s_fl[kMaxNu];
     __shared__ cx<T> s_hd[kMaxNu];
     __shared__ cx<T> s_fk[kMaxNu];
     __shared__ const cx<T> *s_base[kMaxNu];
     __shared__ int s_sel[kMaxNu];
-    __shared__ ArgMaxD red[32];
-    __shared__ double redd[32 * 2];
+    __shared__ c64 s_g[kMaxNu + 1], s_gf[kMaxNu + 1];  // <H_l, H_d>, <f_l, f_d> for d <= l
+    __shared__ AM red[32];
     __shared__ long long s_off;
+    __shared__ double s_normC2;
+    __shared__ int s_stop, s_knext;
     const int Nu = a.nf;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     cx<T> *H = scratch + (int64_t)blockIdx.x * sper;
     cx<T> *fib = (cx<T> *)o.fib;
     cx<T> *pool = (cx<T> *)o.face;
@@ -85,67 +89,65 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
         const int64_t nIJ = (int64_t)nI * nJ;
         const cx<T> *N = (const cx<T> *)a.near + a.noff[nb];
         const int64_t tb = (int64_t)b * Nu;
-        for (int kk = threadIdx.x; kk < Nu; kk += blockDim.x) s_sel[kk] = 0;
+        for (int kk = tid; kk < Nu; kk += blockDim.x) s_sel[kk] = 0;
+        if (tid == 0) s_normC2 = 0.0;
         __syncthreads();
-        double normC2 = 0.0;
         int l = 0, k = 0, r = -1;
         while (l < Nu) {
-            ArgMaxD am = {-1.0, 0x7fffffff};
-            for (int d = threadIdx.x; d < l; d += blockDim.x) {
+            AM am = {-1, 0x7fffffff};
+            for (int d = tid; d < l; d += blockDim.x) {
                 s_fk[d] = fib[(tb + d) * Nu + k];
                 s_base[d] = pool + o.foff[tb + d];
             }
             __syncthreads();
-            for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) {
+            for (int64_t e = tid; e < nIJ; e += blockDim.x) {
                 cx<T> h = apply_coef(N[k * nIJ + e], s_fk, s_base, l, (int)e);
                 H[e] = h;
-                double v = (double)h.x * h.x + (double)h.y * h.y;
-                if (am_better(v, (int)e, am.v, am.i)) am = {v, (int)e};
+                const auto key = pivot_key(h);
+                if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
             }
             am = block_argmax(am, red);
-            if (!(am.v > 0.0)) {
+            if (!(am.v > 0)) {
                 r = l;
                 break;
             }
             const int ep = am.i;
             const cx<T> piv = H[ep];
-            for (int d = threadIdx.x; d < l; d += blockDim.x) s_hd[d] = pool[o.foff[tb + d] + ep];
+            for (int d = tid; d < l; d += blockDim.x) s_hd[d] = pool[o.foff[tb + d] + ep];
             __syncthreads();
-            for (int kk = threadIdx.x; kk < Nu; kk += blockDim.x) {
+            for (int kk = tid; kk < Nu; kk += blockDim.x) {
                 cx<T> v = N[kk * nIJ + ep];
                 for (int d = 0; d < l; ++d) cfms(v, s_hd[d], fib[(tb + d) * Nu + kk]);
                 s_fl[kk] = cdiv(v, piv);
             }
             __syncthreads();
-            // eq. norm in FP64: <H_l, H_d>, ||H_l||^2, <f_l, f_d>
-            double v2[2] = {0.0, 0.0};
-            {
-                DotAcc<T> acc;
-                for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) acc.add(H[e], H[e]);
-                v2[0] = acc.real();
+            // eq. norm: <H_l, H_d> and <f_l, f_d> for d < l, ||H_l||^2 and
+            // ||f_l||^2 at d = l; one warp per term, the recursion in FP64
+            for (int d = wid; d <= l; d += nwarps) {
+                const cx<T> *Hd = d < l ? pool + o.foff[tb + d] : H;
+                DotAcc<T> ah, af;
+                for (int64_t e = lane; e < nIJ; e += 32) ah.add(H[e], Hd[e]);
+                for (int kk = lane; kk < Nu; kk += 32) af.add(s_fl[kk], d < l ? fib[(tb + d) * Nu + kk] : s_fl[kk]);
+                const double hr = ah.warp_real(), hi = ah.warp_imag(), fr = af.warp_real(), fi = af.warp_imag();
+                if (lane == 0) {
+                    s_g[d] = {hr, hi};
+                    s_gf[d] = {fr, fi};
+                }
             }
-            block_sum<1>(v2, redd);
-            const double hl2 = v2[0];
-            double fl2 = 0.0;
-            for (int kk = 0; kk < Nu; ++kk) fl2 += cabs2(ccast<double>(s_fl[kk]));
-            double cross = 0.0;
-            for (int d = 0; d < l; ++d) {
-                const cx<T> *Hd = pool + o.foff[tb + d];
-                DotAcc<T> acc;
-                for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) acc.add(H[e], Hd[e]);
-                double g[2] = {acc.real(), acc.imag()};
-                block_sum<2>(g, redd);
-                c64 gf = {0.0, 0.0};
-                for (int kk = 0; kk < Nu; ++kk)
-                    gf = gf + ccast<double>(s_fl[kk]) * cconj(ccast<double>(fib[(tb + d) * Nu + kk]));
-                cross += g[0] * gf.x - g[1] * gf.y;
+            __syncthreads();
+            if (tid == 0) {
+                double cross = 0.0;
+                for (int d = 0; d < l; ++d) cross += s_g[d].x * s_gf[d].x - s_g[d].y * s_gf[d].y;
+                const double hl2 = s_g[l].x, fl2 = s_gf[l].x;
+                s_normC2 += 2.0 * cross + hl2 * fl2;
+                s_stop = sqrt(hl2 * fl2) <= p.eps * sqrt(s_normC2);
             }
-            normC2 += 2.0 * cross + hl2 * fl2;
-            if (sqrt(hl2 * fl2) <= p.eps * sqrt(normC2)) {
+            __syncthreads();
+            if (s_stop) {
                 r = l;
                 break;
             }
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 unsigned long long off = atomicAdd(o.face_used, (unsigned long long)nIJ);
                 if ((int64_t)(off + nIJ) > o.face_cap) {
                     atomicOr(o.dev_flags, TD_DEV_POOL_OVERFLOW);
@@ -160,35 +162,37 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
                 r = l;
                 break;
             }
-            for (int64_t e = threadIdx.x; e < nIJ; e += blockDim.x) pool[off + e] = H[e];
-            for (int kk = threadIdx.x; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = s_fl[kk];
-            if (threadIdx.x == 0) {
+            for (int64_t e = tid; e < nIJ; e += blockDim.x) pool[off + e] = H[e];
+            for (int kk = tid; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = s_fl[kk];
+            if (tid == 0) {
                 o.kpiv[tb + l] = k;
                 o.frank[tb + l] = -1;
                 o.foff[tb + l] = off;
+                s_sel[k] = 1;
             }
-            s_sel[k] = 1;  // same value written by every thread
             __syncthreads();
             ++l;
-            int kn = -1;
-            double best = -1.0;
-            for (int kk = 0; kk < Nu; ++kk) {
-                if (s_sel[kk]) continue;
-                double v = cabs2(ccast<double>(s_fl[kk]));
-                if (v > best) {
-                    best = v;
-                    kn = kk;
+            // next frequency: largest |f_l[k]| among those not selected yet
+            if (wid == 0) {
+                AM an = {-1, 0x7fffffff};
+                for (int kk = lane; kk < Nu; kk += 32) {
+                    if (s_sel[kk]) continue;
+                    const auto key = pivot_key(s_fl[kk]);
+                    if (am_better(key, kk, an.v, an.i)) an = {key, kk};
                 }
+                an = warp_argmax(an);
+                if (lane == 0) s_knext = an.i == 0x7fffffff ? -1 : an.i;
             }
+            __syncthreads();
+            const int kn = s_knext;
             if (kn < 0) {
                 r = l;
                 break;
             }
             k = kn;
-            __syncthreads();
         }
         if (r < 0) r = l;
-        if (threadIdx.x == 0) o.rank[b] = r;
+        if (tid == 0) o.rank[b] = r;
         __syncthreads();
     }
 }
@@ -245,51 +249,84 @@ TD_D cx<T> warp_entry(const MeshDev &m, int row, int col, T sr, T si) {
 }
 
 
-constexpr int kNCoef = 1024;
+constexpr int kNCoef = 512;
 
+// accumulation type of the inner products: FP32 in the mixed form
+template <class T>
+using AccT = T;
+
+// Fixed shared state of one far-field CTA.
 template <class T>
 struct FarShared {
-    cx<T> fl[kMaxNu];
-    cx<T> hd[kMaxNu];
-    c64 gH[kMaxNu];
-    int sel[kMaxNu];
-    int frank[kMaxNu];
-    long long foff[kMaxNu];
-    ArgMaxD red[32];
-    double redd[32 * 4];
-    cx<T> coef[kNCoef];
-    const cx<T> *base[kNCoef];
-    double nrow[64], nu[64], nv[64];  // ACA norm terms per step (face rank <= 64)
-    double normS2;
-    int kstop;
-    int idx, jstar, istar, ncoef;
+    typename AmOf<T>::type red[32];
+    AccT<T> nrow[64], nu[64], nv[64];  // ACA norm terms per step (face rank <= 64)
+    double normS2, normC2;
+    int kstop, stop, knext;
+    int idx;
     long long off;
     cx<T> piv;
+    cx<T> coef[kNCoef];
+    const cx<T> *base[kNCoef];
 };
+
+// Per-frequency arrays of one far-field CTA, carved from dynamic shared memory
+// with Nu entries each (Nu + 1 for gf, 2 (Nu + 1) for gH).
+template <class T>
+struct FarFreq {
+    cx<T> *fl, *hd;
+    c64 *gf;          // <f_l, f_d> for d < l, |f_l|^2 at d = l
+    AccT<T> *gH;      // <H_l, H_d> (re, im) for d <= l
+    long long *foff;
+    int *sel, *frank;
+};
+
+TD_HD size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+template <class T>
+TD_HD size_t far_freq_bytes(int Nu) {
+    return align16(sizeof(cx<T>) * Nu) * 2 + align16(sizeof(c64) * (Nu + 1)) +
+           align16(sizeof(AccT<T>) * 2 * (Nu + 1)) + align16(sizeof(long long) * Nu) + align16(sizeof(int) * Nu) * 2;
+}
+template <class T>
+TD_D FarFreq<T> far_freq(unsigned char *p, int Nu) {
+    FarFreq<T> F;
+    F.fl = (cx<T> *)p;
+    p += align16(sizeof(cx<T>) * Nu);
+    F.hd = (cx<T> *)p;
+    p += align16(sizeof(cx<T>) * Nu);
+    F.gf = (c64 *)p;
+    p += align16(sizeof(c64) * (Nu + 1));
+    F.gH = (AccT<T> *)p;
+    p += align16(sizeof(AccT<T>) * 2 * (Nu + 1));
+    F.foff = (long long *)p;
+    p += align16(sizeof(long long) * Nu);
+    F.sel = (int *)p;
+    p += align16(sizeof(int) * Nu);
+    F.frank = (int *)p;
+    return F;
+}
 
 // coefficient list for the residual of previous terms at a fixed row (mode 0:
 // coef f_d[k] U_d[tau][i*], base V_d[tau]) or fixed column (mode 1: coef
 // f_d[k] V_d[tau][j*], base U_d[tau]), followed by the current face's own
 // terms (u_t[i*], base v_t) / (v_t[j*], base u_t).  Entries [c0, c0+kNCoef).
 template <class T>
-TD_D int build_coef(FarShared<T> &S, int mode, int fixed, int l, int kf, int k, int Nu, int64_t tb,
-                    int nI, int nJ, const cx<T> *pool, const cx<T> *fib, const cx<T> *Uw,
+TD_D int build_coef(FarShared<T> &S, const FarFreq<T> &F, int mode, int fixed, int l, int kf, int k, int Nu,
+                    int64_t tb, int nI, int nJ, const cx<T> *pool, const cx<T> *fib, const cx<T> *Uw,
                     const cx<T> *Vw, int maxI, int maxJ, int c0) {
-    // total count
     int total = kf;
-    for (int d = 0; d < l; ++d) total += S.frank[d];
+    for (int d = 0; d < l; ++d) total += F.frank[d];
     const int cend = min(total, c0 + kNCoef);
     for (int c = c0 + threadIdx.x; c < cend; c += blockDim.x) {
         int rem = c, d = 0;
-        while (d < l && rem >= S.frank[d]) {
-            rem -= S.frank[d];
+        while (d < l && rem >= F.frank[d]) {
+            rem -= F.frank[d];
             ++d;
         }
         cx<T> cf;
         const cx<T> *bp;
         if (d < l) {
-            const cx<T> *Ud = pool + S.foff[d];
-            const cx<T> *Vd = Ud + (int64_t)S.frank[d] * nI;
+            const cx<T> *Ud = pool + F.foff[d];
+            const cx<T> *Vd = Ud + (int64_t)F.frank[d] * nI;
             const cx<T> fk = fib[(tb + d) * Nu + k];
             if (mode == 0) {
                 cf = fk * Ud[(int64_t)rem * nI + fixed];
@@ -314,7 +351,7 @@ TD_D int build_coef(FarShared<T> &S, int mode, int fixed, int l, int kf, int k, 
 }
 
 constexpr int kTI = 16;     // Gram tile width (rows of U / V per stage)
-constexpr int kGCh = 64;    // Gram tile height (factor columns per stage)
+constexpr int kGCh = 32;    // Gram tile height (factor columns per stage)
 constexpr int kGOut = 4;    // Gram outputs per thread
 
 // Shared tiles for the Gram sums (dynamic shared memory).
@@ -327,19 +364,38 @@ struct GramTiles {
     int colD[kGCh];
 };
 
+// Adds v to gH[2 d] (re) / gH[2 d + 1] (im); d < 0: nothing.  Lanes of a warp
+// that all carry the same d are summed with shuffles first (the common case:
+// the outputs of one warp mostly belong to one term).
+template <class A>
+TD_D void add_by_term(A *gH, int d, A re, A im) {
+    const int d0 = __shfl_sync(0xffffffffu, d, 0);
+    if (__all_sync(0xffffffffu, d == d0)) {
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if ((threadIdx.x & 31) == 0 && d0 >= 0) {
+            atomicAdd(&gH[2 * d0], re);
+            atomicAdd(&gH[2 * d0 + 1], im);
+        }
+    } else if (d >= 0) {
+        atomicAdd(&gH[2 * d], re);
+        atomicAdd(&gH[2 * d + 1], im);
+    }
+}
+
 // eq. norm for the new term l: for every previous term d < l and for d = l,
 // gH[d] += sum_{t < kf, tau < k_d} <u_t, U_d[tau]> <v_t, V_d[tau]>, where
 // u_t, v_t are the face's ACA factors (Uw, Vw).  The inner products are
 // small GEMMs over the rows of U and V, staged through shared-memory tiles;
-// each thread owns up to kGOut (t, tau) outputs and accumulates them with
-// compensated FP32 products (FP64 in the FP64 form); the products of the
-// two inner products are summed in FP64.
+// each thread owns up to kGOut (t, tau) outputs (t fastest, so that the
+// outputs of a warp share a term).  gH must be zero on entry.
 template <class T>
-TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int nJ, const cx<T> *pool,
+TD_D void gram_sums(const FarFreq<T> &F, GramTiles<T> &G, int l, int kf, int nI, int nJ, const cx<T> *pool,
                     const cx<T> *Uw, const cx<T> *Vw, int maxI, int maxJ) {
+    using A = AccT<T>;
     const int tid = threadIdx.x;
     int Kprev = 0;
-    for (int d = 0; d < l; ++d) Kprev += S.frank[d];
+    for (int d = 0; d < l; ++d) Kprev += F.frank[d];
     const int Kall = Kprev + kf;
     const int chmax = max(1, min(kGCh, (kGOut * (int)blockDim.x) / max(kf, 1)));
     for (int g0 = 0; g0 < Kall; g0 += chmax) {
@@ -347,14 +403,14 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
         __syncthreads();
         for (int c = tid; c < ch; c += blockDim.x) {
             int d = 0, rem = g0 + c;
-            while (d < l && rem >= S.frank[d]) {
-                rem -= S.frank[d];
+            while (d < l && rem >= F.frank[d]) {
+                rem -= F.frank[d];
                 ++d;
             }
             if (d < l) {
-                const cx<T> *Ud = pool + S.foff[d];
+                const cx<T> *Ud = pool + F.foff[d];
                 G.colU[c] = Ud + (int64_t)rem * nI;
-                G.colV[c] = Ud + (int64_t)S.frank[d] * nI + (int64_t)rem * nJ;
+                G.colV[c] = Ud + (int64_t)F.frank[d] * nI + (int64_t)rem * nJ;
             } else {
                 G.colU[c] = Uw + (int64_t)rem * maxI;
                 G.colV[c] = Vw + (int64_t)rem * maxJ;
@@ -382,7 +438,7 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
                 for (int q = 0; q < kGOut; ++q) {
                     const int o = tid + q * blockDim.x;
                     if (o < kf * ch) {
-                        const int t = o / ch, c = o % ch;
+                        const int t = o % kf, c = o / kf;
                         DotAcc<T> &acc = pass ? av[q] : au[q];
 #pragma unroll 4
                         for (int xx = 0; xx < kTI; ++xx) acc.add(G.A[t][xx], G.B[c][xx]);
@@ -393,12 +449,11 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
 #pragma unroll
         for (int q = 0; q < kGOut; ++q) {
             const int o = tid + q * blockDim.x;
-            if (o < kf * ch) {
-                const int d = G.colD[o % ch];
-                const double ur = au[q].real(), ui = au[q].imag(), vr = av[q].real(), vi = av[q].imag();
-                atomicAdd(&S.gH[d].x, ur * vr - ui * vi);
-                atomicAdd(&S.gH[d].y, ur * vi + ui * vr);
-            }
+            const bool has = o < kf * ch;
+            const int d = has ? G.colD[o / kf] : -1;
+            const A pr = has ? au[q].re * av[q].re - au[q].im * av[q].im : A(0);
+            const A pi = has ? au[q].re * av[q].im + au[q].im * av[q].re : A(0);
+            add_by_term(F.gH, d, pr, pi);
         }
     }
     __syncthreads();
@@ -406,11 +461,17 @@ TD_D void gram_sums(FarShared<T> &S, GramTiles<T> &G, int l, int kf, int nI, int
 
 template <class T, int OP, int NT>
 __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
+    using AM = typename AmOf<T>::type;
+    using A = AccT<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FarShared<T> &S = *reinterpret_cast<FarShared<T> *>(smem_raw);
-    GramTiles<T> *gt = reinterpret_cast<GramTiles<T> *>(smem_raw + sizeof(FarShared<T>));
-    unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + sizeof(FarShared<T>) + sizeof(GramTiles<T>));
+    size_t soff = align16(sizeof(FarShared<T>));
+    GramTiles<T> *gt = reinterpret_cast<GramTiles<T> *>(smem_raw + soff);
+    soff += align16(sizeof(GramTiles<T>));
     const int Nu = a.nf;
+    FarFreq<T> F = far_freq<T>(smem_raw + soff, Nu);
+    soff += far_freq_bytes<T>(Nu);
+    unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + soff);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     cx<T> *Uw = (cx<T> *)a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
     cx<T> *Vw = Uw + (int64_t)p.kcap * a.maxI;
@@ -429,9 +490,9 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         const int *rows = a.perm_r + bl[0], *cols = a.perm_c + bl[2];
         const int64_t tb = (int64_t)b * Nu;
-        for (int kk = tid; kk < Nu; kk += blockDim.x) S.sel[kk] = 0;
+        for (int kk = tid; kk < Nu; kk += blockDim.x) F.sel[kk] = 0;
+        if (tid == 0) S.normC2 = 0.0;
         __syncthreads();
-        double normC2 = 0.0;
         int l = 0, k = a.harvest ? idx % Nu : 0, r = -1;
         while (l < Nu) {
             const T sr = (T)a.sig[2 * k], si = (T)a.sig[2 * k + 1];
@@ -446,10 +507,10 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
             int guard = 0;
             while (kf < p.kcap && guard < nI + p.kcap) {
                 ++guard;
-                // row fibre at istar
-                ArgMaxD am = {-1.0, 0x7fffffff};
+                // row fibre at istar: entries first (kept in Vw[kf]), then the
+                // residual corrections in chunks
+                AM am = {-1, 0x7fffffff};
                 int total = 0;
-                // entries first (kept in Vw[kf]), then residual corrections in chunks
                 for (int j = wid; j < nJ; j += nwarps) {
                     const cx<T> v = warp_entry<T, OP>(m, rows[istar], cols[j], sr, si);
                     if (lane == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
@@ -457,7 +518,7 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                 ev_reg += nJ;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
-                    total = build_coef(S, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    total = build_coef(S, F, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     const int cn = min(kNCoef, total - c0);
                     for (int j = tid; j < nJ; j += blockDim.x)
@@ -465,14 +526,13 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                     if (c0 + kNCoef >= total) break;
                 }
                 for (int j = tid; j < nJ; j += blockDim.x) {
-                    cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
-                    double av = (double)v.x * v.x + (double)v.y * v.y;
-                    if (am_better(av, j, am.v, am.i)) am = {av, j};
+                    const auto key = pivot_key(Vw[(int64_t)kf * a.maxJ + j]);
+                    if (am_better(key, j, am.v, am.i)) am = {key, j};
                 }
                 am = block_argmax(am, S.red);
                 if (tid == 0) used[istar >> 5] |= 1u << (istar & 31);
                 __syncthreads();
-                if (!(am.v > 0.0)) {
+                if (!(am.v > 0)) {
                     // zero residual row: next unused row, if any
                     int nxt = -1;
                     for (int i = 0; i < nI; ++i)
@@ -502,7 +562,7 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                 ev_reg += nI;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
-                    total = build_coef(S, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    total = build_coef(S, F, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     const int cn = min(kNCoef, total - c0);
                     for (int i = tid; i < nI; i += blockDim.x)
@@ -510,12 +570,11 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                     if (c0 + kNCoef >= total) break;
                 }
                 __syncthreads();
-                ArgMaxD am2 = {-1.0, 0x7fffffff};
+                AM am2 = {-1, 0x7fffffff};
                 for (int i = tid; i < nI; i += blockDim.x) {
                     if (used[i >> 5] & (1u << (i & 31))) continue;
-                    cx<T> v = Uw[(int64_t)kf * a.maxI + i];
-                    double av = (double)v.x * v.x + (double)v.y * v.y;
-                    if (am_better(av, i, am2.v, am2.i)) am2 = {av, i};
+                    const auto key = pivot_key(Uw[(int64_t)kf * a.maxI + i]);
+                    if (am_better(key, i, am2.v, am2.i)) am2 = {key, i};
                 }
                 am2 = block_argmax(am2, S.red);
                 // Norm recursion of the ACA (matrix analogue of eq. norm, FP64):
@@ -525,13 +584,13 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                 // and the first step that meets the criterion is taken, exactly as
                 // if every step had been checked (the ACA steps themselves do not
                 // depend on the check).
-                const bool have_next = !(am2.i == 0x7fffffff || am2.v < 0.0);
+                const bool have_next = !(am2.i == 0x7fffffff || am2.v < 0);
                 if (kf + 1 < kp && have_next) {
                     ++kf;
                     istar = am2.i;
                     continue;
                 }
-                for (int t = tid; t <= kf; t += blockDim.x) S.nrow[t] = 0.0;
+                for (int t = tid; t <= kf; t += blockDim.x) S.nrow[t] = A(0);
                 __syncthreads();
                 {
                     int npairs = 0;
@@ -546,14 +605,13 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                         DotAcc<T> au, av;
                         for (int i = lane; i < nI; i += 32) au.add(Uw[(int64_t)t * a.maxI + i], Uw[(int64_t)t2 * a.maxI + i]);
                         for (int j = lane; j < nJ; j += 32) av.add(Vw[(int64_t)t * a.maxJ + j], Vw[(int64_t)t2 * a.maxJ + j]);
-                        const double gu[2] = {au.warp_real(), au.warp_imag()}, gv[2] = {av.warp_real(), av.warp_imag()};
-                        if (lane == 0) {
-                            if (t2 < t) {
-                                atomicAdd(&S.nrow[t], gu[0] * gv[0] - gu[1] * gv[1]);
-                            } else {
-                                S.nu[t] = gu[0];
-                                S.nv[t] = gv[0];
-                            }
+                        const A ur = au.warp_re(), vr = av.warp_re();
+                        if (t2 < t) {
+                            const A ui = au.warp_im(), vi = av.warp_im();
+                            if (lane == 0) atomicAdd(&S.nrow[t], ur * vr - ui * vi);
+                        } else if (lane == 0) {
+                            S.nu[t] = ur;
+                            S.nv[t] = vr;
                         }
                     }
                 }
@@ -562,8 +620,9 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                     double n2 = S.normS2;
                     int kstop = -1;
                     for (int t = pend0; t <= kf; ++t) {
-                        n2 += 2.0 * S.nrow[t] + S.nu[t] * S.nv[t];
-                        if (sqrt(S.nu[t] * S.nv[t]) <= p.eps_aca * sqrt(n2)) {
+                        const double uu = S.nu[t], vv = S.nv[t];
+                        n2 += 2.0 * (double)S.nrow[t] + uu * vv;
+                        if (sqrt(uu * vv) <= p.eps_aca * sqrt(n2)) {
                             kstop = t;
                             break;
                         }
@@ -592,16 +651,15 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                 break;
             }
             // ------------------------------------------------ pivot on the rebuilt face
-            ArgMaxD am = {-1.0, 0x7fffffff};
+            AM am = {-1, 0x7fffffff};
             const int64_t nIJ = (int64_t)nI * nJ;
             for (int64_t e = tid; e < nIJ; e += blockDim.x) {
                 const int i = (int)(e / nJ), j = (int)(e % nJ);
-                const cx<T> h = lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j);
-                double av = (double)h.x * h.x + (double)h.y * h.y;
-                if (am_better(av, (int)e, am.v, am.i)) am = {av, (int)e};
+                const auto key = pivot_key(lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j));
+                if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
             }
             am = block_argmax(am, S.red);
-            if (!(am.v > 0.0) || kf == 0) {
+            if (!(am.v > 0) || kf == 0) {
                 r = l;
                 break;
             }
@@ -613,36 +671,41 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
             }
             // previous faces at the pivot
             for (int d = tid; d < l; d += blockDim.x) {
-                const cx<T> *Ud = pool + S.foff[d];
-                const cx<T> *Vd = Ud + (int64_t)S.frank[d] * nI;
-                S.hd[d] = lowrank_at(Ud, (int64_t)nI, Vd, (int64_t)nJ, S.frank[d], ip, jp);
+                const cx<T> *Ud = pool + F.foff[d];
+                const cx<T> *Vd = Ud + (int64_t)F.frank[d] * nI;
+                F.hd[d] = lowrank_at(Ud, (int64_t)nI, Vd, (int64_t)nJ, F.frank[d], ip, jp);
             }
+            for (int d = tid; d <= l; d += blockDim.x) F.gH[2 * d] = F.gH[2 * d + 1] = A(0);
             __syncthreads();
             const cx<T> piv = S.piv;
             // tube over all unique frequencies, one warp per frequency
             for (int kk = wid; kk < Nu; kk += nwarps) {
                 cx<T> v = warp_entry<T, OP>(m, rows[ip], cols[jp], (T)a.sig[2 * kk], (T)a.sig[2 * kk + 1]);
                 if (lane == 0) {
-                    for (int d = 0; d < l; ++d) cfms(v, S.hd[d], fib[(tb + d) * Nu + kk]);
-                    S.fl[kk] = cdiv(v, piv);
+                    for (int d = 0; d < l; ++d) cfms(v, F.hd[d], fib[(tb + d) * Nu + kk]);
+                    F.fl[kk] = cdiv(v, piv);
                 }
             }
             ev_tube += Nu;
-            for (int d = tid; d <= l; d += blockDim.x) S.gH[d] = {0.0, 0.0};
-            __syncthreads();
             // eq. norm: <H_l, H_d> = sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>, d <= l
-            gram_sums(S, *gt, l, kf, nI, nJ, pool, Uw, Vw, a.maxI, a.maxJ);
-            double fl2 = 0.0, cross = 0.0;
-            for (int kk = 0; kk < Nu; ++kk) fl2 += cabs2(ccast<double>(S.fl[kk]));
-            for (int d = 0; d < l; ++d) {
-                c64 gf = {0.0, 0.0};
-                for (int kk = 0; kk < Nu; ++kk)
-                    gf = gf + ccast<double>(S.fl[kk]) * cconj(ccast<double>(fib[(tb + d) * Nu + kk]));
-                cross += S.gH[d].x * gf.x - S.gH[d].y * gf.y;
+            gram_sums(F, *gt, l, kf, nI, nJ, pool, Uw, Vw, a.maxI, a.maxJ);
+            // <f_l, f_d> (d < l) and |f_l|^2 (d = l), one warp per term
+            for (int d = wid; d <= l; d += nwarps) {
+                DotAcc<T> acc;
+                for (int kk = lane; kk < Nu; kk += 32) acc.add(F.fl[kk], d < l ? fib[(tb + d) * Nu + kk] : F.fl[kk]);
+                const double gr = acc.warp_real(), gi = acc.warp_imag();
+                if (lane == 0) F.gf[d] = {gr, gi};
             }
-            const double hl2 = S.gH[l].x;
-            normC2 += 2.0 * cross + hl2 * fl2;
-            if (sqrt(fabs(hl2) * fl2) <= p.eps * sqrt(normC2)) {
+            __syncthreads();
+            if (tid == 0) {
+                double cross = 0.0;
+                for (int d = 0; d < l; ++d) cross += (double)F.gH[2 * d] * F.gf[d].x - (double)F.gH[2 * d + 1] * F.gf[d].y;
+                const double hl2 = F.gH[2 * l], fl2 = F.gf[l].x;
+                S.normC2 += 2.0 * cross + hl2 * fl2;
+                S.stop = sqrt(fabs(hl2) * fl2) <= p.eps * sqrt(S.normC2);
+            }
+            __syncthreads();
+            if (S.stop) {
                 r = l;
                 break;
             }
@@ -667,33 +730,35 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                 pool[off + e] = Uw[(e / nI) * a.maxI + e % nI];
             for (int64_t e = tid; e < (int64_t)kf * nJ; e += blockDim.x)
                 pool[off + (int64_t)kf * nI + e] = Vw[(e / nJ) * a.maxJ + e % nJ];
-            for (int kk = tid; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = S.fl[kk];
+            for (int kk = tid; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = F.fl[kk];
             if (tid == 0) {
                 o.kpiv[tb + l] = k;
                 o.frank[tb + l] = kf;
                 o.foff[tb + l] = off;
-                S.frank[l] = kf;
-                S.foff[l] = off;
+                F.frank[l] = kf;
+                F.foff[l] = off;
+                F.sel[k] = 1;
             }
-            S.sel[k] = 1;
             __syncthreads();
             ++l;
-            int kn = -1;
-            double best = -1.0;
-            for (int kk = 0; kk < Nu; ++kk) {
-                if (S.sel[kk]) continue;
-                double v = cabs2(ccast<double>(S.fl[kk]));
-                if (v > best) {
-                    best = v;
-                    kn = kk;
+            // next frequency: largest |f_l[k]| among those not selected yet
+            if (wid == 0) {
+                AM an = {-1, 0x7fffffff};
+                for (int kk = lane; kk < Nu; kk += 32) {
+                    if (F.sel[kk]) continue;
+                    const auto key = pivot_key(F.fl[kk]);
+                    if (am_better(key, kk, an.v, an.i)) an = {key, kk};
                 }
+                an = warp_argmax(an);
+                if (lane == 0) S.knext = an.i == 0x7fffffff ? -1 : an.i;
             }
+            __syncthreads();
+            const int kn = S.knext;
             if (kn < 0) {
                 r = l;
                 break;
             }
             k = kn;
-            __syncthreads();
         }
         if (r < 0) r = l;
         if (tid == 0 && !a.harvest) o.rank[b] = r;
@@ -720,7 +785,8 @@ int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const Tenso
 template <class T, int OP, int NT>
 static int launch_far_nt(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
                          const AcaParams &p, int nctas) {
-    size_t sm = sizeof(FarShared<T>) + sizeof(GramTiles<T>) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
+    const size_t sm = align16(sizeof(FarShared<T>)) + align16(sizeof(GramTiles<T>)) + far_freq_bytes<T>(a.nf) +
+                      sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
     cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     k_far_aca<T, OP, NT><<<nctas, NT, sm, st>>>(m, a, o, p);

@@ -107,7 +107,11 @@ def test_tensor_save_load_roundtrip(td, ctx, sphere2, tmp_path, prec):
     assert torch.equal(X.entries(rows, cols, fid), Y.entries(rows, cols, fid))
     ct = torch.complex128 if prec == "FP64" else torch.complex64
     W = torch.as_tensor(rng.standard_normal((16, len(T), 2)), dtype=ct, device="cuda")
-    assert torch.equal(X.apply_weighted(W), Y.apply_weighted(W))
+    # the apply sums block contributions with atomics: same values up to the
+    # order of the additions
+    ya, yb = X.apply_weighted(W), Y.apply_weighted(W)
+    tol = 1e-12 if prec == "FP64" else 1e-5
+    assert (torch.linalg.norm(ya - yb) <= tol * torch.linalg.norm(ya)).item()
 
 
 def test_load_rejects_foreign_files(td, ctx, tmp_path):
