@@ -24,10 +24,10 @@ namespace {
 
 constexpr int kMaxNu = 256;
 
-// v -= sum_{c < cn} coef[c] * base[c][idx]: eight independent loads in flight
+// sum_{c < cn} coef[c] * base[c][idx]: eight independent loads in flight
 // per thread (the loop is memory-latency bound otherwise).
 template <class T>
-TD_D cx<T> apply_coef(cx<T> v, const cx<T> *coef, const cx<T> *const *base, int cn, int idx) {
+TD_D cx<T> coef_sum(const cx<T> *coef, const cx<T> *const *base, int cn, int idx) {
     cx<T> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     int c = 0;
     for (; c + 8 <= cn; c += 8) {
@@ -38,7 +38,11 @@ TD_D cx<T> apply_coef(cx<T> v, const cx<T> *coef, const cx<T> *const *base, int 
         for (int q = 0; q < 8; ++q) cfma(acc[q & 3], coef[c + q], b[q]);
     }
     for (; c < cn; ++c) cfma(acc[0], coef[c], base[c][idx]);
-    return v - ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+template <class T>
+TD_D cx<T> apply_coef(cx<T> v, const cx<T> *coef, const cx<T> *const *base, int cn, int idx) {
+    return v - coef_sum(coef, base, cn, idx);
 }
 
 // h = sum_{t < kf} U[t * su + i] V[t * sv + j] with independent accumulators.
@@ -249,6 +253,36 @@ TD_D cx<T> warp_entry(const MeshDev &m, int row, int col, T sr, T si) {
 }
 
 
+// Entry by a group of 8 lanes: lanes 0..6 of the group take test point a =
+// lane % 8 against the 7 trial points (lane 7 adds nothing); the group sum
+// reaches all 8 lanes.  Every lane of the warp must call it (the shuffles
+// stay inside each group); valid = false contributes 0.
+template <class T, int OP>
+TD_D cx<T> group_entry(const MeshDev &m, int row, int col, T sr, T si, bool valid) {
+    const int sub = threadIdx.x & 7;
+    cx<T> acc = {0, 0};
+    if (valid && sub < 7) {
+        if (OP == TD_SLP) {
+#pragma unroll 1
+            for (int b = 0; b < 7; ++b) acc = acc + point_pair(m, OP, row, sub, col, b, 0, sr, si);
+        } else {
+            const int p1 = m.v2t_ptr[col + 1];
+            for (int p = m.v2t_ptr[col]; p < p1; ++p) {
+                const int tj = m.v2t[p], loc = m.v2t_loc[p];
+#pragma unroll 1
+                for (int b = 0; b < 7; ++b) acc = acc + point_pair(m, OP, row, sub, tj, b, loc, sr, si);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    const T s = (T)(1.0 / TD_FOUR_PI);
+    return cx<T>{acc.x * s, acc.y * s};
+}
+
 constexpr int kNCoef = 512;
 
 // accumulation type of the inner products: FP32 in the mixed form
@@ -267,6 +301,7 @@ struct FarShared {
     cx<T> piv;
     cx<T> coef[kNCoef];
     const cx<T> *base[kNCoef];
+    cx<T> part[256];  // partial corrections of the thread groups (correct_fibre)
 };
 
 // Per-frequency arrays of one far-field CTA, carved from dynamic shared memory
@@ -348,6 +383,30 @@ TD_D int build_coef(FarShared<T> &S, const FarFreq<T> &F, int mode, int fixed, i
         S.base[c - c0] = bp;
     }
     return total;
+}
+
+// x[idx] -= sum_{c < cn} S.coef[c] * S.base[c][idx] for idx < n.  Short
+// fibres (n < blockDim) split the coefficient list over G thread groups so
+// that more loads are in flight, and combine the partial sums through
+// shared memory.  Called by every thread of the block.
+template <class T>
+TD_D void correct_fibre(FarShared<T> &S, cx<T> *x, int n, int cn) {
+    const int G = n >= (int)blockDim.x ? 1 : min(16, (int)blockDim.x / n);
+    if (G == 1) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = x[j] - coef_sum(S.coef, S.base, cn, j);
+        return;
+    }
+    const int per = (cn + G - 1) / G;
+    for (int e = threadIdx.x; e < n * G; e += blockDim.x) {
+        const int j = e % n, g = e / n, cb = min(cn, g * per), ce = min(cn, cb + per);
+        S.part[e] = coef_sum(S.coef + cb, S.base + cb, ce - cb, j);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        cx<T> v = x[j];
+        for (int g = 0; g < G; ++g) v = v - S.part[g * n + j];
+        x[j] = v;
+    }
 }
 
 constexpr int kTI = 16;     // Gram tile width (rows of U / V per stage)
@@ -460,7 +519,7 @@ TD_D void gram_sums(const FarFreq<T> &F, GramTiles<T> &G, int l, int kf, int nI,
 }
 
 template <class T, int OP, int NT>
-__global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
+__global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
     using AM = typename AmOf<T>::type;
     using A = AccT<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -511,18 +570,17 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                 // residual corrections in chunks
                 AM am = {-1, 0x7fffffff};
                 int total = 0;
-                for (int j = wid; j < nJ; j += nwarps) {
-                    const cx<T> v = warp_entry<T, OP>(m, rows[istar], cols[j], sr, si);
-                    if (lane == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
+                for (int j0 = wid * 4; j0 < nJ; j0 += nwarps * 4) {  // warp-uniform trip count
+                    const int j = j0 + (lane >> 3);
+                    const cx<T> v = group_entry<T, OP>(m, rows[istar], cols[min(j, nJ - 1)], sr, si, j < nJ);
+                    if (j < nJ && (lane & 7) == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
                 }
                 ev_reg += nJ;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
                     total = build_coef(S, F, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
-                    const int cn = min(kNCoef, total - c0);
-                    for (int j = tid; j < nJ; j += blockDim.x)
-                        Vw[(int64_t)kf * a.maxJ + j] = apply_coef(Vw[(int64_t)kf * a.maxJ + j], S.coef, S.base, cn, j);
+                    correct_fibre(S, Vw + (int64_t)kf * a.maxJ, nJ, min(kNCoef, total - c0));
                     if (c0 + kNCoef >= total) break;
                 }
                 for (int j = tid; j < nJ; j += blockDim.x) {
@@ -555,18 +613,17 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
                     Vw[(int64_t)kf * a.maxJ + j] = cdiv(v, piv);
                 }
                 // column fibre at jstar
-                for (int i = wid; i < nI; i += nwarps) {
-                    const cx<T> v = warp_entry<T, OP>(m, rows[i], cols[jstar], sr, si);
-                    if (lane == 0) Uw[(int64_t)kf * a.maxI + i] = v;
+                for (int i0 = wid * 4; i0 < nI; i0 += nwarps * 4) {
+                    const int i = i0 + (lane >> 3);
+                    const cx<T> v = group_entry<T, OP>(m, rows[min(i, nI - 1)], cols[jstar], sr, si, i < nI);
+                    if (i < nI && (lane & 7) == 0) Uw[(int64_t)kf * a.maxI + i] = v;
                 }
                 ev_reg += nI;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
                     total = build_coef(S, F, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
-                    const int cn = min(kNCoef, total - c0);
-                    for (int i = tid; i < nI; i += blockDim.x)
-                        Uw[(int64_t)kf * a.maxI + i] = apply_coef(Uw[(int64_t)kf * a.maxI + i], S.coef, S.base, cn, i);
+                    correct_fibre(S, Uw + (int64_t)kf * a.maxI, nI, min(kNCoef, total - c0));
                     if (c0 + kNCoef >= total) break;
                 }
                 __syncthreads();
@@ -679,9 +736,11 @@ __global__ void __launch_bounds__(NT) k_far_aca(MeshDev m, FarArgs a, TensorOut 
             __syncthreads();
             const cx<T> piv = S.piv;
             // tube over all unique frequencies, one warp per frequency
-            for (int kk = wid; kk < Nu; kk += nwarps) {
-                cx<T> v = warp_entry<T, OP>(m, rows[ip], cols[jp], (T)a.sig[2 * kk], (T)a.sig[2 * kk + 1]);
-                if (lane == 0) {
+            for (int k0 = wid * 4; k0 < Nu; k0 += nwarps * 4) {
+                const int kk = min(k0 + (lane >> 3), Nu - 1);
+                cx<T> v = group_entry<T, OP>(m, rows[ip], cols[jp], (T)a.sig[2 * kk], (T)a.sig[2 * kk + 1],
+                                             k0 + (lane >> 3) < Nu);
+                if (k0 + (lane >> 3) < Nu && (lane & 7) == 0) {
                     for (int d = 0; d < l; ++d) cfms(v, F.hd[d], fib[(tb + d) * Nu + kk]);
                     F.fl[kk] = cdiv(v, piv);
                 }
