@@ -105,7 +105,8 @@ typedef struct {
 int tdbem_ctx_create(int device, void *cuda_stream, tdbem_ctx_t *out);
 int tdbem_ctx_destroy(tdbem_ctx_t ctx);
 const char *tdbem_last_error(tdbem_ctx_t ctx);
-/* Block until all work of the context's stream has finished. */
+/* Block until all work of the context's stream has finished; TDBEM_ERR_CUDA
+ * if a tensor-core wait of an earlier asynchronous call gave up. */
 int tdbem_ctx_sync(tdbem_ctx_t ctx);
 
 /* ---- mesh (Sec. 3 eq. geomapprox, spaces X_D = P1, X_N = P0) -------------- */
@@ -222,12 +223,29 @@ int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem
  * folded in through A(conj s) = conj A(s)); y: device [nrows][nrhs], same
  * complex type as the tensor.  Evaluated as sum_d H_d (sum_l f_d[l] W_l). */
 int tdbem_apply_weighted(tdbem_tensor_t t, const void *W, int32_t nrhs, void *y);
+/* The mixed form evaluates the frequency contraction sum_l f_d(l) W_l of every
+ * term as complex GEMMs on the tensor cores (tcgen05, BF16 operands split in
+ * a high and a low part, FP32 accumulation; see tdbem_zgemm), keeps the
+ * result in a device buffer of 2 * nrhs * sum_b rank_b * |J_b| complex values
+ * owned by the tensor (reallocated when nrhs changes), and then applies the
+ * faces on the FP32 cores.  The FP64 form runs every step in FP64. */
 /* y = A(s_fidx) x for one point of the full list: x device [ncols][nrhs]. */
 int tdbem_apply_freq(tdbem_tensor_t t, int32_t fidx, const void *x, int32_t nrhs, void *y);
 /* Same as tdbem_apply_weighted with host W and y (pinned or pageable): the
  * host->device copy of W and the device->host copy of y are part of the
  * call, which returns when y is on the host. */
 int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, int32_t nrhs, void *y_host);
+
+/* ---- tensor-core complex GEMM (no counterpart in the paper) ----------------
+ * D = A B for complex64 device matrices A [M][K] (row stride lda), B [K][N]
+ * (ldb), D [M][N] (ldd): the engine of the weighted apply's frequency
+ * contraction, exposed so that it can be tested on its own.  tcgen05 MMAs
+ * on split-BF16 operands (x = hi + lo, products hi*hi + hi*lo + lo*hi),
+ * FP32 accumulation in tensor memory; relative error about 1e-5 of
+ * sum_k |A[m][k]| |B[k][n]|.  Synchronous.  TDBEM_ERR_CUDA if a wait for the
+ * tensor cores gave up (the result is then invalid). */
+int tdbem_zgemm(tdbem_ctx_t ctx, int32_t M, int32_t N, int32_t K, const void *A, int64_t lda, const void *B,
+                int64_t ldb, void *D, int64_t ldd);
 
 /* ---- per-frequency solve (Sec. 2, the Laplace-domain systems of the gCQ
  * step; Sec. 5 solves them iteratively) --------------------------------------

@@ -280,6 +280,20 @@ def autotune(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, n
     return int(ch[0]), int(ch[1])
 
 
+def zgemm(ctx, A, B, D=None):
+    """D = A @ B for complex64 device matrices on the tensor cores (split BF16)."""
+    torch = _torch()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K2 == K and A.dtype == torch.complex64 and B.dtype == torch.complex64
+    A = A.contiguous()
+    B = B.contiguous()
+    if D is None:
+        D = torch.empty((M, N), dtype=torch.complex64, device=A.device)
+    ctx.check(ctx.L.tdbem_zgemm(ctx.h, M, N, K, _ptr(A), K, _ptr(B), N, _ptr(D), N), "tdbem_zgemm")
+    return D
+
+
 def rank_bin(rank):
     return int(_lib.load().tdbem_rank_bin(int(rank)))
 

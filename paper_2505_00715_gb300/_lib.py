@@ -78,6 +78,8 @@ EXPORTS = {
     "tdbem_apply_weighted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_freq": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_weighted_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "tdbem_zgemm": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                              C.c_int64, C.c_void_p, C.c_int64]),
     "tdbem_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32,
                               C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
     "tdbem_tensor_save": (C.c_int, [C.c_void_p, C.c_char_p]),

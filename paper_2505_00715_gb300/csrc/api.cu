@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "internal.h"
@@ -170,12 +171,19 @@ extern "C" int tdbem_ctx_create(int device, void *stream, tdbem_ctx_t *out) {
         delete c;
         return TDBEM_ERR_CUDA;
     }
+    if (cudaMalloc(&c->dflags, sizeof(int)) != cudaSuccess || cudaMemset(c->dflags, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(c->capture);
+        delete c;
+        return TDBEM_ERR_CUDA;
+    }
     *out = c;
     return TDBEM_OK;
 }
 
 extern "C" int tdbem_ctx_destroy(tdbem_ctx_t ctx) {
     if (ctx && ctx->capture) cudaStreamDestroy(ctx->capture);
+    if (ctx && ctx->dflags) cudaFree(ctx->dflags);
     delete ctx;
     return TDBEM_OK;
 }
@@ -185,6 +193,12 @@ extern "C" const char *tdbem_last_error(tdbem_ctx_t ctx) { return ctx ? ctx->err
 extern "C" int tdbem_ctx_sync(tdbem_ctx_t ctx) {
     if (!ctx) return TDBEM_ERR_ARG;
     TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int fl = 0;
+    TD_CUDA(ctx, cudaMemcpy(&fl, ctx->dflags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fl & TD_DEV_TIMEOUT) {
+        cudaMemset(ctx->dflags, 0, sizeof(int));
+        return td_fail(ctx, TDBEM_ERR_CUDA, "a tensor-core wait of an earlier call gave up (its result is invalid)");
+    }
     return TDBEM_OK;
 }
 
@@ -494,6 +508,8 @@ namespace {
 void free_tensor(tdbem_tensor *t) {
     if (!t) return;
     for (void *p : t->owned) cudaFree(p);
+    if (t->plan_mem) cudaFree(t->plan_mem);
+    if (t->plan_Z) cudaFree(t->plan_Z);
     delete t;
 }
 
@@ -857,12 +873,136 @@ extern "C" int tdbem_tensor_destroy(tdbem_tensor_t t) {
 // apply
 // ============================================================================
 namespace {
+// Plan of the tensor-core apply for nrhs right-hand sides: the Z rows
+// (block, term, half) grouped by column cluster, the tile jobs of the GEMM
+// and each block's first Z row.  Host work O(nblocks * rank + jobs).
+int build_apply_plan(tdbem_tensor *t, int nrhs) {
+    tdbem_ctx *ctx = t->ctx;
+    if (t->plan_nrhs == nrhs) return TDBEM_OK;
+    std::vector<int32_t> qmap(t->NQ);
+    TD_CUDA(ctx, cudaMemcpy(qmap.data(), t->dpartner, sizeof(int32_t) * t->NQ, cudaMemcpyDeviceToHost));
+    int rpt = 1;
+    for (int q = 0; q < t->NQ; ++q)
+        if (qmap[q] < 0) rpt = 2;
+    const int64_t nb = t->nblocks;
+    std::vector<ZGroup> groups;
+    std::vector<std::vector<int2>> rows;
+    std::vector<int64_t> zbase(nb, -1), brow(nb, -1);
+    std::vector<int> bgroup(nb, -1);
+    std::map<std::pair<int, int>, int> gid;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int r = t->rank[b];
+        if (r <= 0) continue;
+        const int32_t *bl = &t->blocks[5 * b];
+        auto key = std::make_pair(bl[2], bl[3]);
+        auto it = gid.find(key);
+        int g;
+        if (it == gid.end()) {
+            g = (int)groups.size();
+            gid[key] = g;
+            ZGroup zg{};
+            zg.J0 = bl[2];
+            zg.nJ = bl[3] - bl[2];
+            groups.push_back(zg);
+            rows.emplace_back();
+        } else {
+            g = it->second;
+        }
+        bgroup[b] = g;
+        brow[b] = (int64_t)rows[g].size();
+        for (int d = 0; d < r; ++d)
+            for (int p = 0; p < rpt; ++p) rows[g].push_back(make_int2((int)b, 2 * d + p));
+    }
+    std::vector<int2> rowtab;
+    std::vector<ZJob> jobs;
+    int64_t zsize = 0;
+    const int TM = td_zgemm_tile_rows(), TN = td_zgemm_tile_cols();
+    for (size_t g = 0; g < groups.size(); ++g) {
+        ZGroup &zg = groups[g];
+        zg.row0 = (int)rowtab.size();
+        zg.M = (int)rows[g].size();
+        zg.L = zg.nJ * nrhs;
+        zg.zoff = zsize;
+        zsize += (int64_t)zg.M * zg.L;
+        rowtab.insert(rowtab.end(), rows[g].begin(), rows[g].end());
+        for (int m0 = 0; m0 < zg.M; m0 += TM)
+            for (int n0 = 0; n0 < zg.L; n0 += TN) jobs.push_back(ZJob{(int)g, m0, n0, 0});
+    }
+    for (int64_t b = 0; b < nb; ++b)
+        if (bgroup[b] >= 0) zbase[b] = groups[bgroup[b]].zoff + brow[b] * groups[bgroup[b]].L;
+    if (jobs.size() > (size_t)INT32_MAX || rowtab.size() > (size_t)INT32_MAX)
+        return td_fail(ctx, TDBEM_ERR_ARG, "apply plan too large");
+    if (t->plan_mem || t->plan_Z) TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // an earlier apply may still read them
+    if (t->plan_mem) cudaFree(t->plan_mem);
+    if (t->plan_Z) cudaFree(t->plan_Z);
+    t->plan_mem = t->plan_Z = nullptr;
+    t->plan_nrhs = 0;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off[5];
+    off[0] = 0;
+    off[1] = off[0] + al(sizeof(ZGroup) * groups.size());
+    off[2] = off[1] + al(sizeof(int2) * rowtab.size());
+    off[3] = off[2] + al(sizeof(ZJob) * jobs.size());
+    off[4] = off[3] + al(sizeof(int64_t) * nb);
+    char *mem = nullptr;
+    if (cudaMalloc(&mem, std::max<size_t>(off[4], 256)) != cudaSuccess ||
+        cudaMalloc(&t->plan_Z, sizeof(c32) * std::max<int64_t>(zsize, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        if (mem) cudaFree(mem);
+        t->plan_Z = nullptr;
+        return td_fail(ctx, TDBEM_ERR_OOM, "apply plan: device allocation of %lld complex values failed", (long long)zsize);
+    }
+    t->plan_mem = mem;
+    TD_CUDA(ctx, cudaMemcpy(mem + off[0], groups.data(), sizeof(ZGroup) * groups.size(), cudaMemcpyHostToDevice));
+    TD_CUDA(ctx, cudaMemcpy(mem + off[1], rowtab.data(), sizeof(int2) * rowtab.size(), cudaMemcpyHostToDevice));
+    TD_CUDA(ctx, cudaMemcpy(mem + off[2], jobs.data(), sizeof(ZJob) * jobs.size(), cudaMemcpyHostToDevice));
+    TD_CUDA(ctx, cudaMemcpy(mem + off[3], zbase.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice));
+    for (int k = 0; k < 4; ++k) t->plan_off[k] = off[k];
+    t->plan_rpt = rpt;
+    t->plan_njobs = (int)jobs.size();
+    t->plan_nrhs = nrhs;
+    return TDBEM_OK;
+}
+
+// Weighted apply of the mixed form on the tensor cores: Z = frequency
+// contraction (split-BF16 tcgen05 GEMM per column cluster), then the faces.
+int apply_tc(tdbem_tensor *t, const void *W, int nrhs, void *y) {
+    tdbem_ctx *ctx = t->ctx;
+    int rc = build_apply_plan(t, nrhs);
+    if (rc) return rc;
+    char *mem = (char *)t->plan_mem;
+    const ZGroup *groups = (const ZGroup *)(mem + t->plan_off[0]);
+    const int2 *rowtab = (const int2 *)(mem + t->plan_off[1]);
+    const ZJob *jobs = (const ZJob *)(mem + t->plan_off[2]);
+    const int64_t *zbase = (const int64_t *)(mem + t->plan_off[3]);
+    int e = td_launch_zgemm_apply(ctx->stream, groups, rowtab, t->dpartner, (const c32 *)t->dfib, (const c32 *)W,
+                                  t->dperm_c, (c32 *)t->plan_Z, t->Nu, nrhs, t->ncols, t->NQ, jobs, t->plan_njobs,
+                                  ctx->dflags, ctx->num_sms);
+    if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "tensor-core contraction failed: %s", cudaGetErrorString((cudaError_t)e));
+    ApplyZArgs a{};
+    a.nb = (int)t->nblocks;
+    a.blocks = t->dblocks;
+    a.perm_r = t->dperm_r;
+    a.Nu = t->Nu;
+    a.nrhs = nrhs;
+    a.rpt = t->plan_rpt;
+    a.zbase = zbase;
+    a.Z = (const c32 *)t->plan_Z;
+    a.y = (c32 *)y;
+    a.kcap = t->kcap;
+    a.max_near_rows = t->max_near_rows;
+    e = td_launch_apply_z(ctx->stream, a, tensor_out(t, nullptr), ctx->num_sms);
+    if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "face apply kernel failed: %s", cudaGetErrorString((cudaError_t)e));
+    return TDBEM_OK;
+}
+
 int apply_impl(tdbem_tensor *t, const void *W, int nrhs, void *y, int single_f) {
     cudaGetLastError();
     tdbem_ctx *ctx = t->ctx;
     if (nrhs < 1 || nrhs > 64 || !W || !y) return td_fail(ctx, TDBEM_ERR_ARG, "apply: need 1 <= nrhs <= 64 and non-NULL buffers");
     const size_t es = t->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
     TD_CUDA(ctx, cudaMemsetAsync(y, 0, es * t->nrows * nrhs, ctx->stream));
+    if (t->prec == TDBEM_MIXED && single_f < 0) return apply_tc(t, W, nrhs, y);
     ApplyArgs a{};
     a.nb = (int)t->nblocks;
     a.blocks = t->dblocks;
@@ -1044,4 +1184,42 @@ extern "C" int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         chosen[1] = bcps;
     }
     return TDBEM_OK;
+}
+
+// ============================================================================
+// tensor-core complex GEMM (the engine of the weighted apply)
+// ============================================================================
+extern "C" int tdbem_zgemm(tdbem_ctx_t ctx, int32_t M, int32_t N, int32_t K, const void *A, int64_t lda,
+                           const void *B, int64_t ldb, void *D, int64_t ldd) {
+    if (!ctx) return TDBEM_ERR_ARG;
+    cudaGetLastError();
+    if (M < 0 || N < 0 || K < 0 || (M * (int64_t)N > 0 && (!D || (K > 0 && (!A || !B)))) || lda < K || ldb < N ||
+        ldd < N)
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_zgemm: bad sizes or NULL pointers");
+    if ((int64_t)M * N == 0) return TDBEM_OK;
+    if (K == 0) {
+        for (int m = 0; m < M; ++m)
+            TD_CUDA(ctx, cudaMemsetAsync((c32 *)D + (int64_t)m * ldd, 0, sizeof(c32) * N, ctx->stream));
+        return tdbem_ctx_sync(ctx);
+    }
+    const int TM = td_zgemm_tile_rows(), TN = td_zgemm_tile_cols();
+    std::vector<ZJob> jobs;
+    for (int m0 = 0; m0 < M; m0 += TM)
+        for (int n0 = 0; n0 < N; n0 += TN) jobs.push_back(ZJob{0, m0, n0, 0});
+    ZJob *dj = nullptr;
+    if (cudaMalloc(&dj, sizeof(ZJob) * jobs.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return td_fail(ctx, TDBEM_ERR_OOM, "tdbem_zgemm: job list allocation failed");
+    }
+    int rc = TDBEM_OK;
+    if (cudaMemcpyAsync(dj, jobs.data(), sizeof(ZJob) * jobs.size(), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        rc = td_fail(ctx, TDBEM_ERR_CUDA, "tdbem_zgemm: upload failed");
+    if (!rc) {
+        int e = td_launch_zgemm_dense(ctx->stream, (const c32 *)A, lda, (const c32 *)B, ldb, (c32 *)D, ldd, M, N, K,
+                                      dj, (int)jobs.size(), ctx->dflags, ctx->num_sms);
+        if (e) rc = td_fail(ctx, TDBEM_ERR_CUDA, "tdbem_zgemm: launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    }
+    if (!rc) rc = tdbem_ctx_sync(ctx);
+    cudaFree(dj);
+    return rc;
 }

@@ -18,6 +18,7 @@ struct tdbem_ctx {
     int far_cps[2] = {4, 5};
     std::string err;
     int num_sms = 0;
+    int *dflags = nullptr;  // device status word of asynchronous kernels (TD_DEV_* bits)
 };
 
 // Host-side planner output for the cluster trees and the block list.
@@ -103,6 +104,11 @@ struct tdbem_tensor {
     int kcap = 64;                  // face-rank cap used by the compression
     int max_near_rows = 1;
     void *dy_host = nullptr;        // staging buffers of tdbem_apply_weighted_host
+    // plan of the tensor-core weighted apply (mixed form), rebuilt when nrhs
+    // changes: groups | row table | jobs | per-block Z offsets, and Z itself
+    int plan_nrhs = 0, plan_rpt = 1, plan_njobs = 0;
+    void *plan_mem = nullptr, *plan_Z = nullptr;
+    size_t plan_off[4] = {0, 0, 0, 0};
     size_t host_buf_bytes = 0;
 };
 

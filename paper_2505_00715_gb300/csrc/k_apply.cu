@@ -150,6 +150,106 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
     }
 }
 
+// Second phase of the tensor-core apply: the frequency contraction
+// z_(b,d,p) = sum_l f_d(l) W_l[J] is already in Z (k_zgemm.cu); the faces are
+// applied as in k_apply (near: y_I += H_d z1 + conj(H_d) z2; far:
+// y_I += U_d (V_d^T z1) + conj(U_d) (V_d^H z2)).  Z rows of a block are
+// (term d, half p) at zbase[b] + (rpt d + p) nJ nrhs.
+// dynamic shared memory (complex64): acc [acc_max]
+__global__ void __launch_bounds__(256) k_apply_z(ApplyZArgs a, TensorOut o) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c32 *acc = reinterpret_cast<c32 *>(smem_raw);
+    const int nrhs = a.nrhs, Nu = a.Nu, RC = 4;
+    const c32 *pool = (const c32 *)o.face;
+    const int tid = threadIdx.x;
+    for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+        const int *bl = a.blocks + 5 * b;
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        const bool far = bl[4] != 0;
+        const int r = o.rank[b];
+        if (r == 0 || a.zbase[b] < 0) continue;
+        const int64_t tb = (int64_t)b * Nu, L = (int64_t)nJ * nrhs;
+        const c32 *Zb = a.Z + a.zbase[b];
+        for (int d0 = 0; d0 < r; d0 += RC) {
+            const int rc = min(RC, r - d0);
+            int sumk = 0;
+            if (far)
+                for (int d = d0; d < d0 + rc; ++d) sumk += o.frank[tb + d];
+            const int nacc = far ? sumk * 2 * nrhs : nI * nrhs;
+            __syncthreads();
+            for (int e = tid; e < nacc; e += blockDim.x) acc[e] = {0.f, 0.f};
+            __syncthreads();
+            if (!far) {
+                for (int e = tid; e < nI * nrhs; e += blockDim.x) {
+                    const int c = e % nrhs, i = e / nrhs;
+                    c32 s = {0.f, 0.f};
+                    for (int dd = 0; dd < rc; ++dd) {
+                        const c32 *H = pool + o.foff[tb + d0 + dd] + (int64_t)i * nJ;
+                        const c32 *z1 = Zb + (int64_t)a.rpt * (d0 + dd) * L + c;
+                        const c32 *z2 = z1 + L;
+                        if (a.rpt == 2) {
+                            for (int j = 0; j < nJ; ++j) {
+                                const c32 h = H[j];
+                                cfma(s, h, z1[(int64_t)j * nrhs]);
+                                cfma(s, cconj(h), z2[(int64_t)j * nrhs]);
+                            }
+                        } else {
+                            for (int j = 0; j < nJ; ++j) cfma(s, H[j], z1[(int64_t)j * nrhs]);
+                        }
+                    }
+                    acc[e] = s;
+                }
+            } else {
+                // acc[(tau, p, c)] = sum_j V[tau][j] z_p[j][c]  (p = 1 uses conj V)
+                for (int e = tid; e < sumk * nrhs; e += blockDim.x) {
+                    const int c = e % nrhs;
+                    int t = e / nrhs, dd = 0;
+                    while (t >= o.frank[tb + d0 + dd]) {
+                        t -= o.frank[tb + d0 + dd];
+                        ++dd;
+                    }
+                    const int kd = o.frank[tb + d0 + dd];
+                    const c32 *V = pool + o.foff[tb + d0 + dd] + (int64_t)kd * nI + (int64_t)t * nJ;
+                    const c32 *z1 = Zb + (int64_t)a.rpt * (d0 + dd) * L + c;
+                    const c32 *z2 = z1 + L;
+                    c32 s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
+                    for (int j = 0; j < nJ; ++j) {
+                        const c32 v = V[j];
+                        cfma(s1, v, z1[(int64_t)j * nrhs]);
+                        if (a.rpt == 2) cfma(s2, cconj(v), z2[(int64_t)j * nrhs]);
+                    }
+                    acc[(e / nrhs) * 2 * nrhs + c] = s1;
+                    acc[(e / nrhs) * 2 * nrhs + nrhs + c] = s2;
+                }
+            }
+            __syncthreads();
+            if (!far) {
+                for (int e = tid; e < nI * nrhs; e += blockDim.x) {
+                    const int c = e % nrhs, i = e / nrhs;
+                    atomic_add_c(a.y + (int64_t)a.perm_r[bl[0] + i] * nrhs + c, acc[e]);
+                }
+            } else {
+                for (int e = tid; e < nI * nrhs; e += blockDim.x) {
+                    const int c = e % nrhs, i = e / nrhs;
+                    c32 s = {0.f, 0.f};
+                    int base = 0;
+                    for (int dd = 0; dd < rc; ++dd) {
+                        const int kd = o.frank[tb + d0 + dd];
+                        const c32 *U = pool + o.foff[tb + d0 + dd];
+                        for (int t = 0; t < kd; ++t) {
+                            const c32 u = U[(int64_t)t * nI + i];
+                            cfma(s, u, acc[(int64_t)(base + t) * 2 * nrhs + c]);
+                            cfma(s, cconj(u), acc[(int64_t)(base + t) * 2 * nrhs + nrhs + c]);
+                        }
+                        base += kd;
+                    }
+                    atomic_add_c(a.y + (int64_t)a.perm_r[bl[0] + i] * nrhs + c, s);
+                }
+            }
+        }
+    }
+}
+
 template <class T>
 __global__ void k_tensor_entries(TensorOut o, const int *blocks, int nb, int64_t nrows, int64_t ncols,
                                  int nq, const int *inv_r, const int *inv_c, const int *qmap,
@@ -223,6 +323,18 @@ int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorO
         if (e != cudaSuccess) return (int)e;
         k_apply<float><<<grid, 256, sm, st>>>(aa, o, TJ, RC);
     }
+    return (int)cudaGetLastError();
+}
+
+int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms) {
+    ApplyZArgs aa = a;
+    aa.acc_max = (int64_t)std::max(2 * 4 * a.kcap, a.max_near_rows) * a.nrhs;
+    const size_t sm = sizeof(c32) * aa.acc_max;
+    if (sm > (size_t)(220 * 1024)) return (int)cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    const int grid = std::min(a.nb, num_sms * 4);
+    k_apply_z<<<grid, 256, sm, st>>>(aa, o);
     return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,243 @@
+// Complex GEMM on the tensor cores (tcgen05, BF16 operands split in two,
+// FP32 accumulation in tensor memory):
+//
+//   D[m][n] = sum_k A[m][k] B[k][n]      (complex64 in and out)
+//
+// Real embedding: per chunk of kTK complex k, the real K axis holds the real
+// parts (first kTK) and then the imaginary parts of A; the real N axis holds
+// re / im of every complex column (interleaved, so that a row of D in tensor
+// memory is a complex64 row):
+//   A_r[m][k']      = Re A[m][k']           A_r[m][kTK + k'] = Im A[m][k']
+//   B_r[2n][k']     = Re B[k'][n]           B_r[2n][kTK + k'] = -Im B[k'][n]
+//   B_r[2n+1][k']   = Im B[k'][n]           B_r[2n+1][kTK + k'] = Re B[k'][n]
+// so that D_r = A_r B_r^T has D_r[m][2n] = Re D[m][n], D_r[m][2n+1] = Im D[m][n].
+// Split BF16: x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the product
+// is taken as hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-16 relative, is
+// dropped), which keeps about 16 mantissa bits of every product.
+//
+// A tile is 128 complex rows (the 128 TMEM lanes) x 128 complex columns
+// (256 FP32 TMEM columns); K is consumed in chunks of 64 complex values
+// (128 real = 8 MMAs of K = 16 per split term).  One CTA of 256 threads per
+// SM (the operand tiles take 192 KB of shared memory); tiles are taken from
+// a job list in a persistent loop.  Used by the weighted apply (the
+// frequency contraction of eq. product) and exposed for testing as
+// tdbem_zgemm.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int kTM = 128;                       // complex rows per tile
+constexpr int kTN = 128;                       // complex columns per tile
+constexpr int kTK = 64;                        // complex K per chunk
+constexpr int kThreads = 256;
+constexpr int kABytes = kTM * 2 * kTK * 2;     // one split part of A: 32 KB
+constexpr int kBBytes = 2 * kTN * 2 * kTK * 2; // one split part of B: 64 KB
+constexpr int kSmemBytes = 2 * kABytes + 2 * kBBytes + 1024 + 64;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kMaxPolls = 1u << 24;
+
+struct SplitPack {
+    uint4 hi, lo;
+};
+// 8 real values -> 8 BF16 hi parts and 8 BF16 lo parts (16 bytes each)
+TD_D SplitPack split8(const float *v) {
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        h[e] = __float2bfloat16_rn(v[e]);
+        l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
+    }
+    SplitPack p;
+    p.hi = *reinterpret_cast<const uint4 *>(h);
+    p.lo = *reinterpret_cast<const uint4 *>(l);
+    return p;
+}
+
+// Dense operands (tdbem_zgemm): A [M][K] lda, B [K][N] ldb, D [M][N] ldd.
+struct DenseOps {
+    const c32 *A, *B;
+    c32 *D;
+    int64_t lda, ldb, ldd;
+    int M, N;
+    TD_D c32 a(const ZJob &, int m, int k) const { return A[(int64_t)m * lda + k]; }
+    TD_D c32 b(const ZJob &, int k, int n) const { return B[(int64_t)k * ldb + n]; }
+    TD_D int rows(const ZJob &j) const { return min(kTM, M - j.m0); }
+    TD_D int cols(const ZJob &j) const { return min(kTN, N - j.n0); }
+    TD_D c32 *drow(const ZJob &, int m) const { return D + (int64_t)m * ldd; }
+};
+
+// Frequency contraction of the apply: rows (block b, term d, half p) of a
+// column-cluster group g, columns (j, c) of W[l][perm_c[J0 + j]][c].
+//   A[(b,d,p)][l] = f_d(l) if l belongs to half p (p = 1: conjugate half,
+//                   coefficient conj(f_d[u])), else 0
+//   Z[(b,d,p)][(j,c)] = sum_l A[(b,d,p)][l] W[l][J0 + j][c]
+struct ApplyOps {
+    const ZGroup *groups;
+    const int2 *rowtab;   // (block, 2 * term + half) per Z row
+    const int *qmap;      // [NQ]
+    const c32 *fib;       // [nb][Nu][Nu]
+    const c32 *W;         // [NQ][ncols][nrhs]
+    const int *perm_c;
+    c32 *Z;
+    int Nu, nrhs;
+    int64_t ncols;
+    TD_D c32 a(const ZJob &j, int m, int l) const {
+        const int2 rt = rowtab[groups[j.g].row0 + m];
+        const int qm = qmap[l];
+        const int half = qm > 0 ? 0 : 1;
+        if (half != (rt.y & 1)) return c32{0.f, 0.f};
+        const c32 f = fib[((int64_t)rt.x * Nu + (rt.y >> 1)) * Nu + (qm > 0 ? qm - 1 : -qm - 1)];
+        return half ? cconj(f) : f;
+    }
+    TD_D c32 b(const ZJob &j, int l, int n) const {
+        const ZGroup &g = groups[j.g];
+        const int jj = n / nrhs, c = n - jj * nrhs;
+        return W[((int64_t)l * ncols + perm_c[g.J0 + jj]) * nrhs + c];
+    }
+    TD_D int rows(const ZJob &j) const { return min(kTM, groups[j.g].M - j.m0); }
+    TD_D int cols(const ZJob &j) const { return min(kTN, groups[j.g].L - j.n0); }
+    TD_D c32 *drow(const ZJob &j, int m) const {
+        const ZGroup &g = groups[j.g];
+        return Z + g.zoff + (int64_t)m * g.L;
+    }
+};
+
+template <class Ops>
+__global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs, int njobs, int K, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 1024-byte aligned operand region
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Ah = base, *Al = base + kABytes, *Bh = base + 2 * kABytes, *Bl = Bh + kBBytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bl + kBBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(tslot, kTmemCols);
+    if (tid == 0) mbar_init(bar, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = idesc_bf16_f32(kTM, 2 * kTN);
+    uint32_t phase = 0;
+    bool failed = false;
+    for (int jb = blockIdx.x; jb < njobs && !failed; jb += gridDim.x) {
+        const ZJob job = jobs[jb];
+        const int mr = ops.rows(job), nc = ops.cols(job);
+        for (int k0 = 0; k0 < K && !failed; k0 += kTK) {
+            const int kc = min(kTK, K - k0);
+            // ---- A tile: item it -> (kstep s, row group g, core matrix kh, row rr);
+            // its 16 bytes sit at byte offset 16 * it of the canonical layout
+            for (int it = tid; it < kTM * 16; it += kThreads) {
+                const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 15, s = it >> 8;
+                const int r = g * 8 + rr, kr = s * 16 + kh * 8;  // real k of the first element
+                float v[8];
+                const bool imag = kr >= kTK;
+                const int kk = imag ? kr - kTK : kr;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    c32 x = {0.f, 0.f};
+                    if (r < mr && kk + e < kc) x = ops.a(job, job.m0 + r, k0 + kk + e);
+                    v[e] = imag ? x.y : x.x;
+                }
+                const SplitPack p = split8(v);
+                *reinterpret_cast<uint4 *>(Ah + 16 * it) = p.hi;
+                *reinterpret_cast<uint4 *>(Al + 16 * it) = p.lo;
+            }
+            // ---- B tile: 2 kTN real rows (re / im row of every complex column)
+            for (int it = tid; it < 2 * kTN * 16; it += kThreads) {
+                const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 31, s = it >> 9;
+                const int nr = g * 8 + rr, kr = s * 16 + kh * 8;
+                const int n = nr >> 1, im_row = nr & 1;
+                const bool second = kr >= kTK;
+                const int kk = second ? kr - kTK : kr;
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    c32 x = {0.f, 0.f};
+                    if (n < nc && kk + e < kc) x = ops.b(job, k0 + kk + e, job.n0 + n);
+                    v[e] = im_row ? (second ? x.x : x.y) : (second ? -x.y : x.x);
+                }
+                const SplitPack p = split8(v);
+                *reinterpret_cast<uint4 *>(Bh + 16 * it) = p.hi;
+                *reinterpret_cast<uint4 *>(Bl + 16 * it) = p.lo;
+            }
+            fence_async_shared();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+#pragma unroll 1
+                for (int s = 0; s < 8; ++s) {
+                    const uint64_t dah = smem_desc(ah + s * 4096, 128, 256), dal = smem_desc(al + s * 4096, 128, 256);
+                    const uint64_t dbh = smem_desc(bh + s * 8192, 128, 256), dbl = smem_desc(bl + s * 8192, 128, 256);
+                    tc_mma_bf16(tmem, dah, dbh, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+                    tc_mma_bf16(tmem, dah, dbl, idesc, 1u);
+                    tc_mma_bf16(tmem, dal, dbh, idesc, 1u);
+                }
+                tc_commit(bar);
+            }
+            const bool ok = mbar_wait(bar, phase, kMaxPolls);
+            phase ^= 1u;
+            failed = __syncthreads_or(!ok) != 0;
+            tc_fence_after();
+        }
+        if (failed) break;
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows),
+        // real columns 128 (w / 4) .. +127
+        const int q = warp & 3, h = warp >> 2;
+        const int r = 32 * q + lane;
+        c32 *drow = r < mr ? ops.drow(job, job.m0 + r) : nullptr;
+#pragma unroll 1
+        for (int c16 = 0; c16 < 8; ++c16) {
+            const int col = 128 * h + 16 * c16;  // real column of the first value
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+            const int n0 = col >> 1;  // complex column
+            if (drow) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (n0 + e < nc) drow[job.n0 + n0 + e] = c32{v[2 * e], v[2 * e + 1]};
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (failed && tid == 0) atomicOr(err, TD_DEV_TIMEOUT);
+    if (failed) mbar_wait(bar, phase ^ 1u, kMaxPolls);  // let a late MMA group finish before freeing TMEM
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+template <class Ops>
+int launch_zgemm(cudaStream_t st, const Ops &ops, const ZJob *jobs, int njobs, int K, int *err, int num_sms) {
+    if (njobs == 0) return 0;
+    cudaError_t e = cudaFuncSetAttribute(k_zgemm<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return (int)e;
+    const int grid = std::min(njobs, num_sms);
+    k_zgemm<Ops><<<grid, kThreads, kSmemBytes, st>>>(ops, jobs, njobs, K, err);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 *B, int64_t ldb, c32 *D, int64_t ldd,
+                          int M, int N, int K, const ZJob *jobs, int njobs, int *err, int num_sms) {
+    DenseOps ops{A, B, D, lda, ldb, ldd, M, N};
+    return launch_zgemm(st, ops, jobs, njobs, K, err, num_sms);
+}
+
+int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap, const c32 *fib,
+                          const c32 *W, const int *perm_c, c32 *Z, int Nu, int nrhs, int64_t ncols, int NQ,
+                          const ZJob *jobs, int njobs, int *err, int num_sms) {
+    ApplyOps ops{groups, rowtab, qmap, fib, W, perm_c, Z, Nu, nrhs, ncols};
+    return launch_zgemm(st, ops, jobs, njobs, NQ, err, num_sms);
+}
+
+int td_zgemm_tile_rows() { return kTM; }
+int td_zgemm_tile_cols() { return kTN; }

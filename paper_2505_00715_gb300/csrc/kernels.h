@@ -85,6 +85,38 @@ struct ApplyArgs {
     int64_t acc_max;       // accumulator size (complex units), set by the launcher
 };
 int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorOut &o, int num_sms);
+
+// ---- tensor-core complex GEMM (k_zgemm.cu) and the apply built on it ----
+struct ZJob {               // one output tile
+    int g, m0, n0, pad;     // group, first row, first complex column
+};
+struct ZGroup {             // rows (block, term, half) that share a column cluster
+    int J0, nJ;             // column cluster (permuted column range)
+    int row0, M;            // first entry in the row table, number of rows
+    int64_t zoff;           // offset of the group's first Z row (complex units)
+    int L, pad;             // Z row length = nJ * nrhs
+};
+int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 *B, int64_t ldb, c32 *D, int64_t ldd,
+                          int M, int N, int K, const ZJob *jobs, int njobs, int *err, int num_sms);
+int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap, const c32 *fib,
+                          const c32 *W, const int *perm_c, c32 *Z, int Nu, int nrhs, int64_t ncols, int NQ,
+                          const ZJob *jobs, int njobs, int *err, int num_sms);
+int td_zgemm_tile_rows();
+int td_zgemm_tile_cols();
+
+// second phase of the tensor-core apply: y += faces x Z (k_apply.cu)
+struct ApplyZArgs {
+    int nb;
+    const int *blocks;
+    const int *perm_r;
+    int Nu, nrhs, rpt;      // rpt: Z rows per term (2 with a conjugate half, else 1)
+    const int64_t *zbase;   // [nb] Z offset of the block's first row (-1: rank 0)
+    const c32 *Z;
+    c32 *y;
+    int kcap, max_near_rows;
+    int64_t acc_max;
+};
+int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms);
 int td_launch_tensor_entries(cudaStream_t st, int prec, const TensorOut &o, const int *blocks,
                              int nb, int64_t nrows, int64_t ncols, int nq, const int *inv_r,
                              const int *inv_c, const int *qmap,
