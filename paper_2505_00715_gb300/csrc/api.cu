@@ -76,6 +76,8 @@ MeshDev mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw
     d.qzl = m->qzl;
     d.qw32 = m->qw32;
     d.n32 = m->n32;
+    d.qp = (const float4 *)m->qp;
+    d.nrm4 = (const float4 *)m->nrm4;
     d.qx = m->qx;
     d.qy = m->qy;
     d.qz = m->qz;
@@ -256,9 +258,24 @@ extern "C" int tdbem_mesh_create(tdbem_ctx_t ctx, const double *verts, int64_t n
             qw32[p * nt + e] = (float)qw[p * nt + e];
         }
     for (int64_t k = 0; k < 3 * nt; ++k) n32[k] = (float)nrm[k];
+    // 16-byte packs: (hi xyz, weight) and (lo xyz, 0) per point, (normal, 0) per triangle
+    std::vector<float> qp(8 * 7 * (size_t)nt), nrm4(4 * (size_t)nt, 0.f);
+    for (int64_t e = 0; e < nt; ++e) {
+        for (int p = 0; p < 7; ++p) {
+            float *o = &qp[8 * ((size_t)p * nt + e)];
+            for (int c = 0; c < 3; ++c) {
+                o[c] = qh[((int64_t)c * 7 + p) * nt + e];
+                o[4 + c] = ql[((int64_t)c * 7 + p) * nt + e];
+            }
+            o[3] = qw32[p * nt + e];
+            o[7] = 0.f;
+        }
+        for (int c = 0; c < 3; ++c) nrm4[4 * e + c] = n32[c * nt + e];
+    }
     // one device allocation for every table
     const size_t n7 = 7 * (size_t)nt;
     size_t bytes = sizeof(double) * (3 * n7 + n7 + 3 * nt + 3 * nv + nt) + sizeof(float) * (6 * n7 + n7 + 3 * nt) +
+                   sizeof(float) * (8 * n7 + 4 * nt) + 64 +
                    sizeof(int32_t) * (3 * nt + (nv + 1) + 3 * nt + (nt + 1) + m->tp_tri.size()) + 3 * nt + 256;
     char *base = nullptr;
     if (cudaMalloc((void **)&base, bytes) != cudaSuccess) {
@@ -288,6 +305,8 @@ extern "C" int tdbem_mesh_create(tdbem_ctx_t ctx, const double *verts, int64_t n
     m->qzl = (float *)take(sizeof(float) * n7);
     m->qw32 = (float *)take(sizeof(float) * n7);
     m->n32 = (float *)take(sizeof(float) * 3 * nt);
+    m->qp = take(sizeof(float) * 8 * n7);
+    m->nrm4 = take(sizeof(float) * 4 * nt);
     m->dtris = (int32_t *)take(sizeof(int32_t) * 3 * nt);
     m->dv2t_ptr = (int32_t *)take(sizeof(int32_t) * (nv + 1));
     m->dv2t = (int32_t *)take(sizeof(int32_t) * 3 * nt);
@@ -303,6 +322,7 @@ extern "C" int tdbem_mesh_create(tdbem_ctx_t ctx, const double *verts, int64_t n
         (rc = upload(ctx, m->qxl, ql.data(), n7)) || (rc = upload(ctx, m->qyl, ql.data() + n7, n7)) ||
         (rc = upload(ctx, m->qzl, ql.data() + 2 * n7, n7)) || (rc = upload(ctx, m->qw32, qw32.data(), n7)) ||
         (rc = upload(ctx, m->n32, n32.data(), 3 * nt)) || (rc = upload(ctx, m->dtris, tris, 3 * nt)) ||
+        (rc = upload(ctx, (float *)m->qp, qp.data(), 8 * n7)) || (rc = upload(ctx, (float *)m->nrm4, nrm4.data(), 4 * nt)) ||
         (rc = upload(ctx, m->dv2t_ptr, m->v2t_ptr.data(), nv + 1)) || (rc = upload(ctx, m->dv2t, m->v2t.data(), 3 * nt)) ||
         (rc = upload(ctx, m->dtp_ptr, m->tp_ptr.data(), nt + 1)) ||
         (rc = upload(ctx, m->dtp_tri, m->tp_tri.data(), m->tp_tri.size())) ||
@@ -960,6 +980,11 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     for (int k = 0; k < 4; ++k) t->plan_off[k] = off[k];
     t->plan_rpt = rpt;
     t->plan_njobs = (int)jobs.size();
+    t->plan_maxI = t->plan_maxJ = 1;
+    for (int64_t b = 0; b < nb; ++b) {
+        t->plan_maxI = std::max(t->plan_maxI, t->blocks[5 * b + 1] - t->blocks[5 * b]);
+        t->plan_maxJ = std::max(t->plan_maxJ, t->blocks[5 * b + 3] - t->blocks[5 * b + 2]);
+    }
     t->plan_nrhs = nrhs;
     return TDBEM_OK;
 }

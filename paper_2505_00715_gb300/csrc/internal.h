@@ -55,6 +55,7 @@ struct tdbem_mesh {
     std::vector<int32_t> tp_ptr, tp_tri;
     // device tables
     float *qxh = nullptr, *qyh, *qzh, *qxl, *qyl, *qzl, *qw32, *n32;
+    void *qp = nullptr, *nrm4 = nullptr;  // float4 packs of the FP32 tables (see MeshDev)
     double *qx = nullptr, *qy, *qz, *qw, *n64, *dverts, *darea;
     int32_t *dtris = nullptr, *dv2t_ptr = nullptr, *dv2t = nullptr;
     int8_t *dv2t_loc = nullptr;
@@ -106,7 +107,7 @@ struct tdbem_tensor {
     void *dy_host = nullptr;        // staging buffers of tdbem_apply_weighted_host
     // plan of the tensor-core weighted apply (mixed form), rebuilt when nrhs
     // changes: groups | row table | jobs | per-block Z offsets, and Z itself
-    int plan_nrhs = 0, plan_rpt = 1, plan_njobs = 0;
+    int plan_nrhs = 0, plan_rpt = 1, plan_njobs = 0, plan_maxI = 1, plan_maxJ = 1;
     void *plan_mem = nullptr, *plan_Z = nullptr;
     size_t plan_off[4] = {0, 0, 0, 0};
     size_t host_buf_bytes = 0;

@@ -208,16 +208,19 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
 // tubes are evaluated one entry per warp, the lanes splitting the point pairs.
 TD_D c32 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int loc, float sr, float si) {
     const int oa = a * m.nt + ti, ob = b * m.nt + tj;
-    float dx = (m.qxh[ob] - m.qxh[oa]) + (m.qxl[ob] - m.qxl[oa]);
-    float dy = (m.qyh[ob] - m.qyh[oa]) + (m.qyl[ob] - m.qyl[oa]);
-    float dz = (m.qzh[ob] - m.qzh[oa]) + (m.qzl[ob] - m.qzl[oa]);
-    float r2 = dx * dx + dy * dy + dz * dz;
-    float rinv = rsqrtf(r2), r = r2 * rinv;
-    c32 e = expm_sr(sr, si, r);
-    float w = m.qw32[oa] * m.qw32[ob] * rinv;
+    const float4 xa = __ldg(&m.qp[2 * oa]), xla = __ldg(&m.qp[2 * oa + 1]);
+    const float4 yb = __ldg(&m.qp[2 * ob]), ylb = __ldg(&m.qp[2 * ob + 1]);
+    const float dx = (yb.x - xa.x) + (ylb.x - xla.x);
+    const float dy = (yb.y - xa.y) + (ylb.y - xla.y);
+    const float dz = (yb.z - xa.z) + (ylb.z - xla.z);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rinv = rsqrtf(r2), r = r2 * rinv;
+    const c32 e = expm_sr(sr, si, r);
+    float w = xa.w * yb.w * rinv;
     if (op == TD_SLP) return {w * e.x, w * e.y};
-    w *= bary7f(b, loc) * -(dx * m.n32[tj] + dy * m.n32[m.nt + tj] + dz * m.n32[2 * m.nt + tj]) * rinv * rinv;
-    float pr = fmaf(sr, r, 1.0f), pi = si * r;
+    const float4 n = __ldg(&m.nrm4[tj]);
+    w *= bary7f(b, loc) * -(dx * n.x + dy * n.y + dz * n.z) * rinv * rinv;
+    const float pr = fmaf(sr, r, 1.0f), pi = si * r;
     return {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
 }
 TD_D c64 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int loc, double sr, double si) {
@@ -231,27 +234,6 @@ TD_D c64 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int 
     double pr = 1.0 + sr * r, pi = si * r;
     return {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
 }
-
-// Entry by one warp (lanes split the point pairs); every lane gets the value.
-template <class T, int OP>
-TD_D cx<T> warp_entry(const MeshDev &m, int row, int col, T sr, T si) {
-    const int lane = threadIdx.x & 31;
-    cx<T> acc = {0, 0};
-    if (OP == TD_SLP) {
-        for (int c = lane; c < 49; c += 32) acc = acc + point_pair(m, OP, row, c / 7, col, c % 7, 0, sr, si);
-    } else {
-        const int p0 = m.v2t_ptr[col], ns = m.v2t_ptr[col + 1] - p0;
-        for (int c = lane; c < 49 * ns; c += 32) {
-            const int s = c / 49, q = c % 49, p = p0 + s;
-            acc = acc + point_pair(m, OP, row, q / 7, m.v2t[p], q % 7, m.v2t_loc[p], sr, si);
-        }
-    }
-    acc.x = warp_sum(acc.x);
-    acc.y = warp_sum(acc.y);
-    const T s = (T)(1.0 / TD_FOUR_PI);
-    return cx<T>{acc.x * s, acc.y * s};
-}
-
 
 // Entry by a group of 8 lanes: lanes 0..6 of the group take test point a =
 // lane % 8 against the 7 trial points (lane 7 adds nothing); the group sum
@@ -292,7 +274,7 @@ using AccT = T;
 // Fixed shared state of one far-field CTA.
 template <class T>
 struct FarShared {
-    typename AmOf<T>::type red[32];
+    typename AmOf<T>::type red[2][32];  // arg-max scratch, used alternately
     AccT<T> nrow[64], nu[64], nv[64];  // ACA norm terms per step (face rank <= 64)
     double normS2, normC2;
     int kstop, stop, knext;
@@ -407,6 +389,22 @@ TD_D void correct_fibre(FarShared<T> &S, cx<T> *x, int n, int cn) {
         for (int g = 0; g < G; ++g) v = v - S.part[g * n + j];
         x[j] = v;
     }
+}
+
+// Block-wide arg-max with one barrier: warp maxima to `red`, then every
+// thread reduces the warp maxima itself.  Successive calls must alternate
+// between two `red` arrays (a call may start writing while slower threads
+// still read the previous one).
+template <class AM>
+TD_D AM block_argmax_1sync(AM a, AM *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    a = warp_argmax(a);
+    if (lane == 0) red[wid] = a;
+    __syncthreads();
+    AM r = red[0];
+    for (int w = 1; w < nw; ++w)
+        if (am_better(red[w].v, red[w].i, r.v, r.i)) r = red[w];
+    return r;
 }
 
 constexpr int kTI = 16;     // Gram tile width (rows of U / V per stage)
@@ -558,7 +556,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             // ------------------------------------------------ ACA of the residual face
             for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
             __syncthreads();
-            int kf = 0, istar = 0;
+            int kf = 0, istar = 0, par = 0;
             if (tid == 0) S.normS2 = 0.0;
             int pend0 = 0;  // first ACA step whose norm terms are not yet summed
             const int kp = (a.kpred && !a.harvest) ? min(a.kpred[tb + k], p.kcap) : 0;
@@ -587,7 +585,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     const auto key = pivot_key(Vw[(int64_t)kf * a.maxJ + j]);
                     if (am_better(key, j, am.v, am.i)) am = {key, j};
                 }
-                am = block_argmax(am, S.red);
+                am = block_argmax_1sync(am, S.red[par]);
+                par ^= 1;
                 if (tid == 0) used[istar >> 5] |= 1u << (istar & 31);
                 __syncthreads();
                 if (!(am.v > 0)) {
@@ -633,7 +632,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     const auto key = pivot_key(Uw[(int64_t)kf * a.maxI + i]);
                     if (am_better(key, i, am2.v, am2.i)) am2 = {key, i};
                 }
-                am2 = block_argmax(am2, S.red);
+                am2 = block_argmax_1sync(am2, S.red[par]);
+                par ^= 1;
                 // Norm recursion of the ACA (matrix analogue of eq. norm, FP64):
                 // ||S_k||^2 = ||S_{k-1}||^2 + 2 Re sum_{t<k} <u_k,u_t><v_k,v_t> + |u_k|^2 |v_k|^2.
                 // Steps below the predicted rank kp run without the check; their
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 const auto key = pivot_key(lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j));
                 if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
             }
-            am = block_argmax(am, S.red);
+            am = block_argmax(am, S.red[0]);
             if (!(am.v > 0) || kf == 0) {
                 r = l;
                 break;

@@ -102,6 +102,8 @@ extern "C" int tdbem_entries_noalloc(tdbem_mesh_t mesh, const tdbem_op *op, tdbe
     m.qzl = mesh->qzl;
     m.qw32 = mesh->qw32;
     m.n32 = mesh->n32;
+    m.qp = (const float4 *)mesh->qp;
+    m.nrm4 = (const float4 *)mesh->nrm4;
     m.qx = mesh->qx;
     m.qy = mesh->qy;
     m.qz = mesh->qz;

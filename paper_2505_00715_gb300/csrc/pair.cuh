@@ -30,6 +30,10 @@ struct MeshDev {
     // FP32 7-point tables, layout [7][nt]: hi/lo coordinates, weight*area
     const float *qxh, *qyh, *qzh, *qxl, *qyl, *qzl, *qw32;
     const float *n32;  // [3][nt] unit normals
+    // the same FP32 tables packed for 16-byte loads: qp[2 (p nt + e)] =
+    // (x_hi, y_hi, z_hi, weight*area), qp[2 (p nt + e) + 1] = (x_lo, y_lo,
+    // z_lo, 0); nrm4[e] = (n_x, n_y, n_z, 0)
+    const float4 *qp, *nrm4;
     // FP64 7-point tables [7][nt] and normals [3][nt]
     const double *qx, *qy, *qz, *qw, *n64;
     const double *verts;  // [nv][3]
