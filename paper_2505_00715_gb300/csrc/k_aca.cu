@@ -266,6 +266,9 @@ TD_D cx<T> group_entry(const MeshDev &m, int row, int col, T sr, T si, bool vali
 }
 
 constexpr int kNCoef = 512;
+// blocks with |I||J| <= kDense form the correction of the previous terms at the
+// current frequency, C(k) = sum_d f_d[k] U_d V_d^T, densely in shared memory
+constexpr int kDense = 1600;
 
 // accumulation type of the inner products: FP32 in the mixed form
 template <class T>
@@ -528,6 +531,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
     const int Nu = a.nf;
     FarFreq<T> F = far_freq<T>(smem_raw + soff, Nu);
     soff += far_freq_bytes<T>(Nu);
+    cx<T> *Cd = reinterpret_cast<cx<T> *>(smem_raw + soff);
+    soff += align16(sizeof(cx<T>) * kDense);
     unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + soff);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     cx<T> *Uw = (cx<T> *)a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
@@ -555,6 +560,35 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const T sr = (T)a.sig[2 * k], si = (T)a.sig[2 * k + 1];
             // ------------------------------------------------ ACA of the residual face
             for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
+            // small blocks: C(k)[i][j] = sum_d f_d[k] sum_tau U_d[tau][i] V_d[tau][j] once per term
+            const bool dense = l > 0 && nI * nJ <= kDense;
+            if (dense) {
+                for (int e = tid; e < nI * nJ; e += blockDim.x) {
+                    const int i = e / nJ, j = e - (e / nJ) * nJ;
+                    cx<T> acc = {0, 0};
+                    for (int d = 0; d < l; ++d) {
+                        const int kd = F.frank[d];
+                        const cx<T> *Ud = pool + F.foff[d] + i;
+                        const cx<T> *Vd = pool + F.foff[d] + (int64_t)kd * nI + j;
+                        cx<T> s4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+                        int t = 0;
+                        for (; t + 4 <= kd; t += 4) {
+                            cx<T> uu[4], vv[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                uu[q] = Ud[(int64_t)(t + q) * nI];
+                                vv[q] = Vd[(int64_t)(t + q) * nJ];
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) cfma(s4[q], uu[q], vv[q]);
+                        }
+                        for (; t < kd; ++t) cfma(s4[0], Ud[(int64_t)t * nI], Vd[(int64_t)t * nJ]);
+                        cfma(acc, fib[(tb + d) * Nu + k], (s4[0] + s4[1]) + (s4[2] + s4[3]));
+                    }
+                    Cd[e] = acc;
+                }
+            }
+            const int lc = dense ? 0 : l;  // previous terms left to the fibre corrections
             __syncthreads();
             int kf = 0, istar = 0, par = 0;
             if (tid == 0) S.normS2 = 0.0;
@@ -576,13 +610,18 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 ev_reg += nJ;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
-                    total = build_coef(S, F, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    total = build_coef(S, F, 0, istar, lc, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     correct_fibre(S, Vw + (int64_t)kf * a.maxJ, nJ, min(kNCoef, total - c0));
                     if (c0 + kNCoef >= total) break;
                 }
                 for (int j = tid; j < nJ; j += blockDim.x) {
-                    const auto key = pivot_key(Vw[(int64_t)kf * a.maxJ + j]);
+                    cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
+                    if (dense) {
+                        v = v - Cd[istar * nJ + j];
+                        Vw[(int64_t)kf * a.maxJ + j] = v;
+                    }
+                    const auto key = pivot_key(v);
                     if (am_better(key, j, am.v, am.i)) am = {key, j};
                 }
                 am = block_argmax_1sync(am, S.red[par]);
@@ -620,7 +659,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 ev_reg += nI;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
-                    total = build_coef(S, F, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    total = build_coef(S, F, 1, jstar, lc, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     correct_fibre(S, Uw + (int64_t)kf * a.maxI, nI, min(kNCoef, total - c0));
                     if (c0 + kNCoef >= total) break;
@@ -628,8 +667,13 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 __syncthreads();
                 AM am2 = {-1, 0x7fffffff};
                 for (int i = tid; i < nI; i += blockDim.x) {
+                    cx<T> u = Uw[(int64_t)kf * a.maxI + i];
+                    if (dense) {
+                        u = u - Cd[i * nJ + jstar];
+                        Uw[(int64_t)kf * a.maxI + i] = u;
+                    }
                     if (used[i >> 5] & (1u << (i & 31))) continue;
-                    const auto key = pivot_key(Uw[(int64_t)kf * a.maxI + i]);
+                    const auto key = pivot_key(u);
                     if (am_better(key, i, am2.v, am2.i)) am2 = {key, i};
                 }
                 am2 = block_argmax_1sync(am2, S.red[par]);
@@ -845,7 +889,7 @@ template <class T, int OP, int NT>
 static int launch_far_nt(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
                          const AcaParams &p, int nctas) {
     const size_t sm = align16(sizeof(FarShared<T>)) + align16(sizeof(GramTiles<T>)) + far_freq_bytes<T>(a.nf) +
-                      sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
+                      align16(sizeof(cx<T>) * kDense) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
     cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     k_far_aca<T, OP, NT><<<nctas, NT, sm, st>>>(m, a, o, p);

@@ -98,16 +98,44 @@ def _outline(radius, nfins, fin_h, fin_t, n_arc):
     return np.array(pts, dtype=np.float64)
 
 
+def _zipper(outer, oang, inner, iang, emit):
+    """Triangulate the annulus between two closed rings of vertex ids whose
+    polar angles (`oang`, `iang`, increasing, unwrapped, first angles within
+    one step of each other) go once around: advance on the side whose next
+    angle comes first."""
+    no, ni = len(outer), len(inner)
+    i = j = 0
+    while i < no or j < ni:
+        to = oang[(i + 1) % no] + (2 * math.pi if i + 1 >= no else 0.0)
+        tn = iang[(j + 1) % ni] + (2 * math.pi if j + 1 >= ni else 0.0)
+        if j >= ni or (i < no and to <= tn):
+            emit(outer[i % no], outer[(i + 1) % no], inner[j % ni])
+            i += 1
+        else:
+            emit(outer[i % no], inner[(j + 1) % ni], inner[j % ni])
+            j += 1
+
+
+def _cap_counts(n_disk, nrings):
+    """Points of the end-cap rings: ring 0 is the outline's circle part
+    (n_disk points), ring r >= 1 a circle of relative size 1 - r/nrings with
+    proportionally fewer points."""
+    return [n_disk] + [max(6, int(round(n_disk * (1.0 - r / nrings)))) for r in range(1, nrings)]
+
+
 def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005, jitter=0.01, seed=0):
     """Synthetic electric-machine housing: a closed finned cylinder along z.
 
     The cross-section is a circle with `nfins` radial fins; it is extruded
-    over `length` and closed by flat end caps triangulated in rings.  The
-    resolution is chosen so that the triangle count is close to `n_target`.
-    Every vertex is moved by a seeded uniform random offset in a ball of
-    radius `jitter` times the mean edge length (flat end caps and fins stay
-    closed because only vertex positions move)."""
-    # choose arc resolution and axial layers for ~n_target triangles
+    over `length` and closed by flat end caps.  In a cap, every fin's cross
+    section is split into two triangles and the disk inside the fin roots is
+    triangulated in rings of points on concentric circles, each ring with a
+    number of points proportional to its radius, neighbouring rings joined
+    by angle (no sliver triangles).  The resolution is chosen so that the
+    triangle count is close to `n_target`.  Every vertex is moved by a
+    seeded uniform random offset in a ball of radius `jitter` times the mean
+    edge length (flat end caps and fins stay closed because only vertex
+    positions move)."""
     best = None
     for n_arc in range(2, 400):
         out = _outline(radius, nfins, fin_h, fin_t, n_arc)
@@ -116,7 +144,8 @@ def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005
         h = perim / P
         nz = max(2, int(round(length / h)))
         nrings = max(1, int(round(radius / h)))
-        ntri = 2 * P * nz + 2 * (2 * P * nrings)
+        cnt = _cap_counts(P - 2 * nfins, nrings)
+        ntri = 2 * P * nz + 2 * (2 * nfins + sum(cnt[r] + cnt[r + 1] for r in range(nrings - 1)) + cnt[-1])
         if best is None or abs(ntri - n_target) < abs(best[0] - n_target):
             best = (ntri, n_arc, nz, nrings)
         if ntri > 1.3 * n_target:
@@ -124,6 +153,7 @@ def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005
     _, n_arc, nz, nrings = best
     out = _outline(radius, nfins, fin_h, fin_t, n_arc)
     P = len(out)
+    per_fin = n_arc + 3  # two tip points, then the arc to the next fin
     verts = []
     tris = []
     # side wall: layers k = 0..nz
@@ -131,6 +161,7 @@ def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005
         z = -length / 2 + length * k / nz
         for p in range(P):
             verts.append((out[p, 0], out[p, 1], z))
+
     def vid(k, p):
         return k * P + (p % P)
     for k in range(nz):
@@ -138,39 +169,41 @@ def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005
             a, b, c, d = vid(k, p), vid(k, p + 1), vid(k + 1, p + 1), vid(k + 1, p)
             tris.append((a, b, c))
             tris.append((a, c, d))
-    # end caps: rings shrinking the outline to the axis; ring 0 = boundary layer
+    disk = [p for p in range(P) if p % per_fin >= 2]       # outline points on the circle
+    disk_ang = np.unwrap([math.atan2(out[p, 1], out[p, 0]) for p in disk])
+    cnt = _cap_counts(len(disk), nrings)
     for cap, k in ((0, 0), (1, nz)):
         z = -length / 2 + length * k / nz
-        ring_ids = [[vid(k, p) for p in range(P)]]
+
+        def emit(a, b, c):
+            # cap 1 (z = +L/2) keeps (a, b, c); cap 0 is seen from the other side
+            tris.append((a, b, c) if cap == 1 else (a, c, b))
+        # fin cross sections: (right root, tip 1, tip 2, left root)
+        for f in range(nfins):
+            t1, t2, rl = f * per_fin, f * per_fin + 1, f * per_fin + 2
+            rr = (f * per_fin - 1) % P
+            emit(vid(k, rr), vid(k, t1), vid(k, t2))
+            emit(vid(k, rr), vid(k, t2), vid(k, rl))
+        # disk rings
+        ids = [[vid(k, p) for p in disk]]
+        angs = [disk_ang]
         for r in range(1, nrings):
-            s = 1.0 - r / nrings
-            ids = []
-            for p in range(P):
-                verts.append((out[p, 0] * s, out[p, 1] * s, z))
-                ids.append(len(verts) - 1)
-            ring_ids.append(ids)
+            rad = radius * (1.0 - r / nrings)
+            n = cnt[r]
+            th = disk_ang[0] + 2 * math.pi * np.arange(n) / n
+            cur = []
+            for t in th:
+                verts.append((rad * math.cos(t), rad * math.sin(t), z))
+                cur.append(len(verts) - 1)
+            ids.append(cur)
+            angs.append(th)
         verts.append((0.0, 0.0, z))
         centre = len(verts) - 1
-        for r in range(nrings):
-            outer = ring_ids[r]
-            if r + 1 < nrings:
-                inner = ring_ids[r + 1]
-                for p in range(P):
-                    a, b = outer[p], outer[(p + 1) % P]
-                    c, d = inner[(p + 1) % P], inner[p]
-                    if cap == 1:
-                        tris.append((a, b, c))
-                        tris.append((a, c, d))
-                    else:
-                        tris.append((a, c, b))
-                        tris.append((a, d, c))
-            else:
-                for p in range(P):
-                    a, b = outer[p], outer[(p + 1) % P]
-                    if cap == 1:
-                        tris.append((a, b, centre))
-                    else:
-                        tris.append((a, centre, b))
+        for r in range(nrings - 1):
+            _zipper(ids[r], angs[r], ids[r + 1], angs[r + 1], emit)
+        last = ids[-1]
+        for i in range(len(last)):
+            emit(last[i], last[(i + 1) % len(last)], centre)
     V = np.array(verts, dtype=np.float64)
     T = np.array(tris, dtype=np.int32)
     if jitter > 0:
