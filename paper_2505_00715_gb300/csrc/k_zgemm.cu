@@ -63,8 +63,16 @@ struct DenseOps {
     c32 *D;
     int64_t lda, ldb, ldd;
     int M, N;
-    TD_D c32 a(const ZJob &, int m, int k) const { return A[(int64_t)m * lda + k]; }
-    TD_D c32 b(const ZJob &, int k, int n) const { return B[(int64_t)k * ldb + n]; }
+    // 8 consecutive k of row m of A / column n of B; entries k >= kend are 0
+    TD_D void a8(const ZJob &, int m, int k, int kend, c32 *x) const {
+        const c32 *p = A + (int64_t)m * lda;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = k + e < kend ? p[k + e] : c32{0.f, 0.f};
+    }
+    TD_D void b8(const ZJob &, int k, int kend, int n, c32 *x) const {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = k + e < kend ? B[(int64_t)(k + e) * ldb + n] : c32{0.f, 0.f};
+    }
     TD_D int rows(const ZJob &j) const { return min(kTM, M - j.m0); }
     TD_D int cols(const ZJob &j) const { return min(kTN, N - j.n0); }
     TD_D c32 *drow(const ZJob &, int m) const { return D + (int64_t)m * ldd; }
@@ -85,18 +93,27 @@ struct ApplyOps {
     c32 *Z;
     int Nu, nrhs;
     int64_t ncols;
-    TD_D c32 a(const ZJob &j, int m, int l) const {
+    TD_D void a8(const ZJob &j, int m, int l, int lend, c32 *x) const {
         const int2 rt = rowtab[groups[j.g].row0 + m];
-        const int qm = qmap[l];
-        const int half = qm > 0 ? 0 : 1;
-        if (half != (rt.y & 1)) return c32{0.f, 0.f};
-        const c32 f = fib[((int64_t)rt.x * Nu + (rt.y >> 1)) * Nu + (qm > 0 ? qm - 1 : -qm - 1)];
-        return half ? cconj(f) : f;
+        const int half = rt.y & 1;
+        const c32 *fr = fib + ((int64_t)rt.x * Nu + (rt.y >> 1)) * Nu;
+        int qm[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) qm[e] = l + e < lend ? qmap[l + e] : 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const bool on = qm[e] != 0 && (qm[e] > 0 ? 0 : 1) == half;
+            const c32 f = on ? fr[qm[e] > 0 ? qm[e] - 1 : -qm[e] - 1] : c32{0.f, 0.f};
+            x[e] = half ? cconj(f) : f;
+        }
     }
-    TD_D c32 b(const ZJob &j, int l, int n) const {
+    TD_D void b8(const ZJob &j, int l, int lend, int n, c32 *x) const {
         const ZGroup &g = groups[j.g];
         const int jj = n / nrhs, c = n - jj * nrhs;
-        return W[((int64_t)l * ncols + perm_c[g.J0 + jj]) * nrhs + c];
+        const c32 *w = W + (int64_t)perm_c[g.J0 + jj] * nrhs + c;
+        const int64_t ls = ncols * nrhs;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = l + e < lend ? w[(int64_t)(l + e) * ls] : c32{0.f, 0.f};
     }
     TD_D int rows(const ZJob &j) const { return min(kTM, groups[j.g].M - j.m0); }
     TD_D int cols(const ZJob &j) const { return min(kTN, groups[j.g].L - j.n0); }
@@ -137,12 +154,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                 float v[8];
                 const bool imag = kr >= kTK;
                 const int kk = imag ? kr - kTK : kr;
+                c32 x[8];
+                if (r < mr) {
+                    ops.a8(job, job.m0 + r, k0 + kk, k0 + kc, x);
+                } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    c32 x = {0.f, 0.f};
-                    if (r < mr && kk + e < kc) x = ops.a(job, job.m0 + r, k0 + kk + e);
-                    v[e] = imag ? x.y : x.x;
+                    for (int e = 0; e < 8; ++e) x[e] = c32{0.f, 0.f};
                 }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = imag ? x[e].y : x[e].x;
                 const SplitPack p = split8(v);
                 *reinterpret_cast<uint4 *>(Ah + 16 * it) = p.hi;
                 *reinterpret_cast<uint4 *>(Al + 16 * it) = p.lo;
@@ -155,12 +175,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                 const bool second = kr >= kTK;
                 const int kk = second ? kr - kTK : kr;
                 float v[8];
+                c32 x[8];
+                if (n < nc) {
+                    ops.b8(job, k0 + kk, k0 + kc, job.n0 + n, x);
+                } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    c32 x = {0.f, 0.f};
-                    if (n < nc && kk + e < kc) x = ops.b(job, k0 + kk + e, job.n0 + n);
-                    v[e] = im_row ? (second ? x.x : x.y) : (second ? -x.y : x.x);
+                    for (int e = 0; e < 8; ++e) x[e] = c32{0.f, 0.f};
                 }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = im_row ? (second ? x[e].x : x[e].y) : (second ? -x[e].y : x[e].x);
                 const SplitPack p = split8(v);
                 *reinterpret_cast<uint4 *>(Bh + 16 * it) = p.hi;
                 *reinterpret_cast<uint4 *>(Bl + 16 * it) = p.lo;
