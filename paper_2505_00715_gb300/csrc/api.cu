@@ -675,7 +675,18 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     const int nctas_near = std::min<int64_t>(std::max<int64_t>(1, (int64_t)near_ids.size()), (int64_t)ctx->num_sms * 8);
     const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
     const int nctas_far = std::min<int64_t>(std::max<int64_t>(1, (int64_t)far_ids.size()), (int64_t)ctx->num_sms * ctx->far_cps[pf]);
-    const int64_t sper_far = (int64_t)kcap * (maxI + maxJ);
+    // dense faces for far blocks up to dense_cap entries, within a scratch budget of 8 GB
+    int64_t dense_cap = 0;
+    for (int32_t b : far_ids) {
+        const int32_t *bl = &tree->blocks[5 * b];
+        dense_cap = std::max<int64_t>(dense_cap, (int64_t)(bl[1] - bl[0]) * (bl[3] - bl[2]));
+    }
+    {
+        const int64_t budget = (int64_t)8 << 30;
+        const int64_t per = (int64_t)es * (Nu + 1) * std::max(1, nctas_far);
+        dense_cap = std::min<int64_t>(dense_cap, budget / per);
+    }
+    const int64_t sper_far = (int64_t)kcap * (maxI + maxJ) + (int64_t)(Nu + 1) * dense_cap;
     if ((rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size())) ||
         (rc = dalloc(ctx, &table, (size_t)npairs * Nu * 3, &g.p)) || (rc = dalloc(ctx, &nearbuf, es * ntens, &g.p)) ||
         (rc = dalloc(ctx, &scr_near, es * maxIJ * nctas_near, &g.p)) ||
@@ -714,6 +725,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     fa.maxJ = maxJ;
     fa.scratch = scr_far;
     fa.scratch_per_cta = sper_far;
+    fa.dense_cap = dense_cap;
     fa.counter = counter;
     fa.evals = evals;
     const double t_plan = now_ms();

@@ -266,9 +266,6 @@ TD_D cx<T> group_entry(const MeshDev &m, int row, int col, T sr, T si, bool vali
 }
 
 constexpr int kNCoef = 512;
-// blocks with |I||J| <= kDense form the correction of the previous terms at the
-// current frequency, C(k) = sum_d f_d[k] U_d V_d^T, densely in shared memory
-constexpr int kDense = 1600;
 
 // accumulation type of the inner products: FP32 in the mixed form
 template <class T>
@@ -531,12 +528,13 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
     const int Nu = a.nf;
     FarFreq<T> F = far_freq<T>(smem_raw + soff, Nu);
     soff += far_freq_bytes<T>(Nu);
-    cx<T> *Cd = reinterpret_cast<cx<T> *>(smem_raw + soff);
-    soff += align16(sizeof(cx<T>) * kDense);
     unsigned int *used = reinterpret_cast<unsigned int *>(smem_raw + soff);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     cx<T> *Uw = (cx<T> *)a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
     cx<T> *Vw = Uw + (int64_t)p.kcap * a.maxI;
+    cx<T> *Hs = Vw + (int64_t)p.kcap * a.maxJ;  // rebuilt faces of dense-path blocks [Nu][dense_cap]
+    cx<T> *Cd = Hs + (int64_t)Nu * a.dense_cap;  // C(k) of the current term [dense_cap]
+    const int64_t dcap = a.dense_cap;
     cx<T> *fib = (cx<T> *)o.fib;
     cx<T> *pool = (cx<T> *)o.face;
     long long ev_reg = 0, ev_tube = 0;
@@ -552,6 +550,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         const int *rows = a.perm_r + bl[0], *cols = a.perm_c + bl[2];
         const int64_t tb = (int64_t)b * Nu;
+        const bool small = (int64_t)nI * nJ <= dcap;
         for (int kk = tid; kk < Nu; kk += blockDim.x) F.sel[kk] = 0;
         if (tid == 0) S.normC2 = 0.0;
         __syncthreads();
@@ -560,31 +559,12 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const T sr = (T)a.sig[2 * k], si = (T)a.sig[2 * k + 1];
             // ------------------------------------------------ ACA of the residual face
             for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
-            // small blocks: C(k)[i][j] = sum_d f_d[k] sum_tau U_d[tau][i] V_d[tau][j] once per term
-            const bool dense = l > 0 && nI * nJ <= kDense;
+            // dense-path blocks: C(k) = sum_d f_d[k] H_d from the rebuilt faces, once per term
+            const bool dense = l > 0 && small;
             if (dense) {
                 for (int e = tid; e < nI * nJ; e += blockDim.x) {
-                    const int i = e / nJ, j = e - (e / nJ) * nJ;
                     cx<T> acc = {0, 0};
-                    for (int d = 0; d < l; ++d) {
-                        const int kd = F.frank[d];
-                        const cx<T> *Ud = pool + F.foff[d] + i;
-                        const cx<T> *Vd = pool + F.foff[d] + (int64_t)kd * nI + j;
-                        cx<T> s4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-                        int t = 0;
-                        for (; t + 4 <= kd; t += 4) {
-                            cx<T> uu[4], vv[4];
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                uu[q] = Ud[(int64_t)(t + q) * nI];
-                                vv[q] = Vd[(int64_t)(t + q) * nJ];
-                            }
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) cfma(s4[q], uu[q], vv[q]);
-                        }
-                        for (; t < kd; ++t) cfma(s4[0], Ud[(int64_t)t * nI], Vd[(int64_t)t * nJ]);
-                        cfma(acc, fib[(tb + d) * Nu + k], (s4[0] + s4[1]) + (s4[2] + s4[3]));
-                    }
+                    for (int d = 0; d < l; ++d) cfma(acc, fib[(tb + d) * Nu + k], Hs[(int64_t)d * dcap + e]);
                     Cd[e] = acc;
                 }
             }
@@ -756,7 +736,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const int64_t nIJ = (int64_t)nI * nJ;
             for (int64_t e = tid; e < nIJ; e += blockDim.x) {
                 const int i = (int)(e / nJ), j = (int)(e % nJ);
-                const auto key = pivot_key(lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j));
+                const cx<T> h = lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j);
+                if (small) Hs[(int64_t)l * dcap + e] = h;
+                const auto key = pivot_key(h);
                 if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
             }
             am = block_argmax(am, S.red[0]);
@@ -772,9 +754,13 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             }
             // previous faces at the pivot
             for (int d = tid; d < l; d += blockDim.x) {
-                const cx<T> *Ud = pool + F.foff[d];
-                const cx<T> *Vd = Ud + (int64_t)F.frank[d] * nI;
-                F.hd[d] = lowrank_at(Ud, (int64_t)nI, Vd, (int64_t)nJ, F.frank[d], ip, jp);
+                if (small) {
+                    F.hd[d] = Hs[(int64_t)d * dcap + am.i];
+                } else {
+                    const cx<T> *Ud = pool + F.foff[d];
+                    const cx<T> *Vd = Ud + (int64_t)F.frank[d] * nI;
+                    F.hd[d] = lowrank_at(Ud, (int64_t)nI, Vd, (int64_t)nJ, F.frank[d], ip, jp);
+                }
             }
             for (int d = tid; d <= l; d += blockDim.x) F.gH[2 * d] = F.gH[2 * d + 1] = A(0);
             __syncthreads();
@@ -790,8 +776,24 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 }
             }
             ev_tube += Nu;
-            // eq. norm: <H_l, H_d> = sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>, d <= l
-            gram_sums(F, *gt, l, kf, nI, nJ, pool, Uw, Vw, a.maxI, a.maxJ);
+            // eq. norm: <H_l, H_d> for d <= l; small blocks from the dense faces (one
+            // warp per term), others from the factors:
+            // sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>
+            if (small) {
+                for (int d = wid; d <= l; d += nwarps) {
+                    const cx<T> *Hl = Hs + (int64_t)l * dcap, *Hd = Hs + (int64_t)d * dcap;
+                    DotAcc<T> acc;
+                    for (int64_t e = lane; e < nIJ; e += 32) acc.add(Hl[e], Hd[e]);
+                    const A gr = acc.warp_re(), gi = acc.warp_im();
+                    if (lane == 0) {
+                        F.gH[2 * d] = gr;
+                        F.gH[2 * d + 1] = gi;
+                    }
+                }
+                __syncthreads();
+            } else {
+                gram_sums(F, *gt, l, kf, nI, nJ, pool, Uw, Vw, a.maxI, a.maxJ);
+            }
             // <f_l, f_d> (d < l) and |f_l|^2 (d = l), one warp per term
             for (int d = wid; d <= l; d += nwarps) {
                 DotAcc<T> acc;
@@ -889,7 +891,7 @@ template <class T, int OP, int NT>
 static int launch_far_nt(cudaStream_t st, const MeshDev &m, const FarArgs &a, const TensorOut &o,
                          const AcaParams &p, int nctas) {
     const size_t sm = align16(sizeof(FarShared<T>)) + align16(sizeof(GramTiles<T>)) + far_freq_bytes<T>(a.nf) +
-                      align16(sizeof(cx<T>) * kDense) + sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
+                      sizeof(unsigned int) * ((a.maxI + 31) / 32 + 1);
     cudaError_t e = cudaFuncSetAttribute(k_far_aca<T, OP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     k_far_aca<T, OP, NT><<<nctas, NT, sm, st>>>(m, a, o, p);

@@ -47,12 +47,15 @@ struct FarArgs {
     const double *sig;      // [2*Nu]
     int nf;
     int maxI, maxJ;
-    void *scratch;          // per-CTA workspace
+    void *scratch;          // per-CTA workspace: U [kcap][maxI], V [kcap][maxJ], then for far
+                            // blocks with |I||J| <= dense_cap the rebuilt faces [Nu][dense_cap]
+                            // and the correction C(k) [dense_cap]
     int64_t scratch_per_cta;  // complex units
     unsigned int *counter;  // work queue head
     int64_t *evals;         // [2] regular, tube entries evaluated
     int *harvest;           // non-null: record face-ACA ranks per (far block, frequency), [nfar][Nu]
     const int *kpred;       // nullable: predicted face rank per (block id, frequency) [nb][Nu]
+    int64_t dense_cap;      // largest |I||J| handled with dense faces (0: none)
 };
 
 int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
