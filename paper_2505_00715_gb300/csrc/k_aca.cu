@@ -266,6 +266,10 @@ TD_D cx<T> group_entry(const MeshDev &m, int row, int col, T sr, T si, bool vali
 }
 
 constexpr int kNCoef = 512;
+// blocks up to kDenseS entries also keep the face under construction,
+// S = sum_t u_t v_t^T, densely (its rank-1 updates cost |I||J| per ACA step,
+// which pays off only for small blocks)
+constexpr int kDenseS = 1600;
 
 // accumulation type of the inner products: FP32 in the mixed form
 template <class T>
@@ -277,6 +281,7 @@ struct FarShared {
     typename AmOf<T>::type red[2][32];  // arg-max scratch, used alternately
     AccT<T> nrow[64], nu[64], nv[64];  // ACA norm terms per step (face rank <= 64)
     double normS2, normC2;
+    double redd[32 * 3];               // block sums of the dense path
     int kstop, stop, knext;
     int idx;
     long long off;
@@ -550,7 +555,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         const int *rows = a.perm_r + bl[0], *cols = a.perm_c + bl[2];
         const int64_t tb = (int64_t)b * Nu;
-        const bool small = (int64_t)nI * nJ <= dcap;
+        const bool small = (int64_t)nI * nJ <= dcap;       // dense faces in scratch
+        const bool dense_s = small && nI * nJ <= kDenseS;  // and the face's own S kept densely
         for (int kk = tid; kk < Nu; kk += blockDim.x) F.sel[kk] = 0;
         if (tid == 0) S.normC2 = 0.0;
         __syncthreads();
@@ -559,16 +565,17 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const T sr = (T)a.sig[2 * k], si = (T)a.sig[2 * k + 1];
             // ------------------------------------------------ ACA of the residual face
             for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
-            // dense-path blocks: C(k) = sum_d f_d[k] H_d from the rebuilt faces, once per term
-            const bool dense = l > 0 && small;
-            if (dense) {
+            // dense-path blocks: C(k) = sum_d f_d[k] H_d from the rebuilt faces, once per
+            // term, and the face's own approximation S = 0 (it becomes H_l)
+            cx<T> *Sd = Hs + (int64_t)l * dcap;
+            if (small) {
                 for (int e = tid; e < nI * nJ; e += blockDim.x) {
                     cx<T> acc = {0, 0};
                     for (int d = 0; d < l; ++d) cfma(acc, fib[(tb + d) * Nu + k], Hs[(int64_t)d * dcap + e]);
                     Cd[e] = acc;
+                    Sd[e] = cx<T>{0, 0};
                 }
             }
-            const int lc = dense ? 0 : l;  // previous terms left to the fibre corrections
             __syncthreads();
             int kf = 0, istar = 0, par = 0;
             if (tid == 0) S.normS2 = 0.0;
@@ -576,6 +583,94 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const int kp = (a.kpred && !a.harvest) ? min(a.kpred[tb + k], p.kcap) : 0;
             bool converged = false;
             int guard = 0;
+            if (dense_s) {
+                // ---- dense path: R = A(k) - C(k) - S, S = sum_t u_t v_t^T kept densely
+                while (kf < p.kcap && guard < nI + p.kcap) {
+                    ++guard;
+                    // residual row fibre at i*: entries, then minus C and S
+                    for (int j0 = wid * 4; j0 < nJ; j0 += nwarps * 4) {
+                        const int j = j0 + (lane >> 3);
+                        const cx<T> v = group_entry<T, OP>(m, rows[istar], cols[min(j, nJ - 1)], sr, si, j < nJ);
+                        if (j < nJ && (lane & 7) == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
+                    }
+                    ev_reg += nJ;
+                    __syncthreads();
+                    AM am = {-1, 0x7fffffff};
+                    for (int j = tid; j < nJ; j += blockDim.x) {
+                        const int64_t e = (int64_t)istar * nJ + j;
+                        const cx<T> v = Vw[(int64_t)kf * a.maxJ + j] - Cd[e] - Sd[e];
+                        Vw[(int64_t)kf * a.maxJ + j] = v;
+                        const auto key = pivot_key(v);
+                        if (am_better(key, j, am.v, am.i)) am = {key, j};
+                    }
+                    am = block_argmax_1sync(am, S.red[par]);
+                    par ^= 1;
+                    if (tid == 0) used[istar >> 5] |= 1u << (istar & 31);
+                    if (!(am.v > 0)) {
+                        // zero residual row: next unused row, if any
+                        __syncthreads();
+                        int nxt = -1;
+                        for (int i = 0; i < nI; ++i)
+                            if (!(used[i >> 5] & (1u << (i & 31)))) {
+                                nxt = i;
+                                break;
+                            }
+                        if (nxt < 0) {
+                            converged = true;
+                            break;
+                        }
+                        istar = nxt;
+                        continue;
+                    }
+                    const int jstar = am.i;
+                    const cx<T> piv = Vw[(int64_t)kf * a.maxJ + jstar];
+                    // residual column fibre at j*, divided by the pivot
+                    for (int i0 = wid * 4; i0 < nI; i0 += nwarps * 4) {
+                        const int i = i0 + (lane >> 3);
+                        const cx<T> v = group_entry<T, OP>(m, rows[min(i, nI - 1)], cols[jstar], sr, si, i < nI);
+                        if (i < nI && (lane & 7) == 0) Uw[(int64_t)kf * a.maxI + i] = v;
+                    }
+                    ev_reg += nI;
+                    __syncthreads();
+                    AM am2 = {-1, 0x7fffffff};
+                    for (int i = tid; i < nI; i += blockDim.x) {
+                        const int64_t e = (int64_t)i * nJ + jstar;
+                        const cx<T> u = cdiv(Uw[(int64_t)kf * a.maxI + i] - Cd[e] - Sd[e], piv);
+                        Uw[(int64_t)kf * a.maxI + i] = u;
+                        if (i == istar || (used[i >> 5] & (1u << (i & 31)))) continue;
+                        const auto key = pivot_key(u);
+                        if (am_better(key, i, am2.v, am2.i)) am2 = {key, i};
+                    }
+                    am2 = block_argmax_1sync(am2, S.red[par]);
+                    par ^= 1;
+                    // S += u v^T with ||S||_F^2, |u|^2 and |v|^2 (FP32 partial sums, FP64 block sums)
+                    double sums[3] = {0.0, 0.0, 0.0};
+                    {
+                        A s2 = 0, uu = 0, vv = 0;
+                        const cx<T> *uk = Uw + (int64_t)kf * a.maxI, *vk = Vw + (int64_t)kf * a.maxJ;
+                        for (int64_t e = tid; e < (int64_t)nI * nJ; e += blockDim.x) {
+                            const int i = (int)(e / nJ), j = (int)(e - (e / nJ) * nJ);
+                            cx<T> sv = Sd[e];
+                            cfma(sv, uk[i], vk[j]);
+                            Sd[e] = sv;
+                            s2 += cabs2(sv);
+                        }
+                        for (int i = tid; i < nI; i += blockDim.x) uu += cabs2(uk[i]);
+                        for (int j = tid; j < nJ; j += blockDim.x) vv += cabs2(vk[j]);
+                        sums[0] = s2;
+                        sums[1] = uu;
+                        sums[2] = vv;
+                    }
+                    block_sum<3>(sums, S.redd);
+                    const bool have_next = !(am2.i == 0x7fffffff || am2.v < 0);
+                    ++kf;
+                    if (sqrt(sums[1] * sums[2]) <= p.eps_aca * sqrt(sums[0]) || !have_next) {
+                        converged = true;
+                        break;
+                    }
+                    istar = am2.i;
+                }
+            } else
             while (kf < p.kcap && guard < nI + p.kcap) {
                 ++guard;
                 // row fibre at istar: entries first (kept in Vw[kf]), then the
@@ -590,15 +685,15 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 ev_reg += nJ;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
-                    total = build_coef(S, F, 0, istar, lc, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    total = build_coef(S, F, 0, istar, small ? 0 : l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     correct_fibre(S, Vw + (int64_t)kf * a.maxJ, nJ, min(kNCoef, total - c0));
                     if (c0 + kNCoef >= total) break;
                 }
                 for (int j = tid; j < nJ; j += blockDim.x) {
                     cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
-                    if (dense) {
-                        v = v - Cd[istar * nJ + j];
+                    if (small) {  // previous terms from C(k)
+                        v = v - Cd[(int64_t)istar * nJ + j];
                         Vw[(int64_t)kf * a.maxJ + j] = v;
                     }
                     const auto key = pivot_key(v);
@@ -639,7 +734,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 ev_reg += nI;
                 for (int c0 = 0;; c0 += kNCoef) {
                     __syncthreads();
-                    total = build_coef(S, F, 1, jstar, lc, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                    total = build_coef(S, F, 1, jstar, small ? 0 : l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
                     __syncthreads();
                     correct_fibre(S, Uw + (int64_t)kf * a.maxI, nI, min(kNCoef, total - c0));
                     if (c0 + kNCoef >= total) break;
@@ -648,8 +743,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 AM am2 = {-1, 0x7fffffff};
                 for (int i = tid; i < nI; i += blockDim.x) {
                     cx<T> u = Uw[(int64_t)kf * a.maxI + i];
-                    if (dense) {
-                        u = u - Cd[i * nJ + jstar];
+                    if (small) {
+                        u = u - Cd[(int64_t)i * nJ + jstar];
                         Uw[(int64_t)kf * a.maxI + i] = u;
                     }
                     if (used[i >> 5] & (1u << (i & 31))) continue;
@@ -736,8 +831,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const int64_t nIJ = (int64_t)nI * nJ;
             for (int64_t e = tid; e < nIJ; e += blockDim.x) {
                 const int i = (int)(e / nJ), j = (int)(e % nJ);
-                const cx<T> h = lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j);
-                if (small) Hs[(int64_t)l * dcap + e] = h;
+                // dense-S path: the rebuilt face is S itself; other dense-face blocks store it
+                const cx<T> h = dense_s ? Sd[e] : lowrank_at(Uw, (int64_t)a.maxI, Vw, (int64_t)a.maxJ, kf, i, j);
+                if (small && !dense_s) Sd[e] = h;
                 const auto key = pivot_key(h);
                 if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
             }
@@ -749,7 +845,10 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             const int ip = am.i / nJ, jp = am.i % nJ;
             if (tid == 0) {
                 cx<T> h = {0, 0};
-                for (int t = 0; t < kf; ++t) cfma(h, Uw[(int64_t)t * a.maxI + ip], Vw[(int64_t)t * a.maxJ + jp]);
+                if (small)
+                    h = Sd[am.i];
+                else
+                    for (int t = 0; t < kf; ++t) cfma(h, Uw[(int64_t)t * a.maxI + ip], Vw[(int64_t)t * a.maxJ + jp]);
                 S.piv = h;
             }
             // previous faces at the pivot
