@@ -616,11 +616,14 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     });
     // learned presizing: predicted face ranks order the far blocks by cost,
     // size the face pool and set the first unchecked ACA steps
-    std::vector<int32_t> kpred;
     int64_t pred_far_cap = -1;
+    int32_t *dkpred = nullptr;
+    Guard gk;
     if (cfg->model) {
         std::vector<double> cost;
-        if ((rc = td_predict_kpred(cfg->model, tree, mesh, f, op->c, far_ids, kpred, cost))) return fail(rc);
+        std::vector<int32_t> ks;
+        if ((rc = dalloc(ctx, &dkpred, nb * Nu, &gk.p))) return fail(rc);
+        if ((rc = td_predict_kpred(cfg->model, tree, mesh, f, op->c, far_ids, kcap, dkpred, cost, ks))) return fail(rc);
         std::vector<size_t> order(far_ids.size());
         for (size_t q = 0; q < order.size(); ++q) order[q] = q;
         std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
@@ -629,9 +632,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         for (size_t q = 0; q < order.size(); ++q) {
             sorted[q] = far_ids[order[q]];
             const int32_t *bl = &tree->blocks[5 * sorted[q]];
-            int64_t ks = 0;
-            for (int u = 0; u < Nu; ++u) ks += std::min(kpred[(int64_t)sorted[q] * Nu + u], kcap);
-            pred_far_cap += ((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks;
+            pred_far_cap += (int64_t)((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks[order[q]];
         }
         far_ids.swap(sorted);
     }
@@ -732,12 +733,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     // face pool: every near term fits (r <= Nu), far terms get a generous
     // estimate; on overflow the far phase is rerun with a larger pool.
     int64_t cap = ntens + (pred_far_cap >= 0 ? pred_far_cap + pred_far_cap / 4 : sum_far_len * 256) + 1024;
-    int32_t *dkpred = nullptr;
-    if (!kpred.empty()) {
-        if ((rc = dalloc(ctx, &dkpred, kpred.size(), &g.p)) || (rc = upload(ctx, dkpred, kpred.data(), kpred.size())))
-            return fail(rc);
-        fa.kpred = dkpred;
-    }
+    if (dkpred) fa.kpred = dkpred;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) cudaEventCreate(&ev[k]);
     int hflags = 0;

@@ -136,5 +136,5 @@ struct tdbem_model;
 void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
                        const std::vector<int32_t> &far, std::vector<float> &x);
 int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
-                     const std::vector<int32_t> &far, std::vector<int32_t> &kpred_by_block,
-                     std::vector<double> &cost);
+                     const std::vector<int32_t> &far, int kcap, int32_t *dkpred, std::vector<double> &cost,
+                     std::vector<int32_t> &ks);

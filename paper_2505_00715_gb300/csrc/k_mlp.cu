@@ -33,6 +33,60 @@ __global__ void k_to_bf16(const float *p, __nv_bfloat16 *q, int n) {
     if (i < n) q[i] = __float2bfloat16(p[i]);
 }
 
+// Forward pass of one sample from weights in shared memory; returns the arg-max bin.
+TD_D int mlp_forward_bin(const float *w, const float *in, float *logits) {
+    float h1[NH], h2[NH];
+    for (int o = 0; o < NH; ++o) {
+        float a = w[OB1 + o];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) a = fmaf(w[OW1 + o * NIN + i], in[i], a);
+        h1[o] = gelu(a);
+    }
+    for (int o = 0; o < NH; ++o) {
+        float a = w[OB2 + o];
+        for (int i = 0; i < NH; ++i) a = fmaf(w[OW2 + o * NH + i], h1[i], a);
+        h2[o] = gelu(a);
+    }
+    int best = 0;
+    float bv = -INFINITY;
+    for (int o = 0; o < NOUT; ++o) {
+        float a = w[OB3 + o];
+        for (int i = 0; i < NH; ++i) a = fmaf(w[OW3 + o * NH + i], h2[i], a);
+        if (logits) logits[o] = a;
+        if (a > bv) {
+            bv = a;
+            best = o;
+        }
+    }
+    return best;
+}
+
+// lower edges of the rank bins (the first ACA steps the compressor may run unchecked)
+__constant__ int c_bin_lower[NOUT] = {1, 2, 3, 4, 5, 7, 9, 11, 13, 17, 21, 25, 33, 41, 49, 65};
+
+// Presizing of the far blocks: sample s = (far block q, unique frequency u);
+// the two frequency features are formed here from the block distance and
+// s/c.  Writes the predicted first trip count kp to kpred[far[q] Nu + u] and
+// adds min(kp, kcap) to ks[q] and len[q] kp^2 to cost[q].
+__global__ void __launch_bounds__(128) k_mlp_presize(const __nv_bfloat16 *P, const float *bfeat, const float *ffeat,
+                                                     int nfar, int Nu, const int *far, const int *len, int kcap,
+                                                     int *kpred, int *ks, float *cost) {
+    __shared__ float w[NP];
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) w[i] = __bfloat162float(P[i]);
+    __syncthreads();
+    const int64_t n = (int64_t)nfar * Nu;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(s / Nu), u = (int)(s - (s / Nu) * Nu);
+        const float *b = bfeat + (int64_t)q * 5;
+        float in[NIN] = {b[0], b[1], b[2], b[3], log1pf(fmaxf(0.f, ffeat[2 * u]) * b[4]),
+                         log1pf(ffeat[2 * u + 1] * b[4])};
+        const int kp = c_bin_lower[mlp_forward_bin(w, in, nullptr)];
+        kpred[(int64_t)far[q] * Nu + u] = kp;
+        atomicAdd(&ks[q], min(kp, kcap));
+        atomicAdd(&cost[q], (float)len[q] * (float)kp * (float)kp);
+    }
+}
+
 // Inference: bins[n] = argmax logits (BF16 weights, FP32 accumulation).
 __global__ void __launch_bounds__(128) k_mlp_predict(const __nv_bfloat16 *P, const float *x, int64_t n,
                                                      int *bins, float *logits) {
@@ -221,6 +275,16 @@ int td_mlp_predict(cudaStream_t st, const void *Pb, const float *x, int64_t n, i
     if (n <= 0) return 0;
     const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms * 8);
     k_mlp_predict<<<grid, 128, 0, st>>>((const __nv_bfloat16 *)Pb, x, n, bins, logits);
+    return (int)cudaGetLastError();
+}
+
+int td_mlp_presize(cudaStream_t st, const void *Pb, const float *bfeat, const float *ffeat, int nfar, int Nu,
+                   const int *far, const int *len, int kcap, int *kpred, int *ks, float *cost, int num_sms) {
+    if (nfar <= 0) return 0;
+    const int64_t n = (int64_t)nfar * Nu;
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms * 8);
+    k_mlp_presize<<<grid, 128, 0, st>>>((const __nv_bfloat16 *)Pb, bfeat, ffeat, nfar, Nu, far, len, kcap, kpred, ks,
+                                        cost);
     return (int)cudaGetLastError();
 }
 

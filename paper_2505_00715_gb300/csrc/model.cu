@@ -37,6 +37,8 @@ struct tdbem_model {
     void *Pb = nullptr;                                                             // BF16 copy
     int step = 0;
     bool bf16_stale = true;
+    void *pbuf = nullptr;  // presizing buffers (grown on demand)
+    size_t pbytes = 0;
 };
 
 namespace {
@@ -106,48 +108,83 @@ void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_fre
     }
 }
 
-// Predicted face ranks per (block id, unique frequency) for the far blocks,
-// lower edge of the predicted bin; also the predicted cost per far block.
+// Predicted first trip counts per (block id, unique frequency) for the far
+// blocks, written to the device array dkpred [nb][Nu] (entries of other
+// blocks untouched); per far block the predicted cost len * sum kp^2 and
+// ks = sum_u min(kp, kcap) (face-pool presizing).  The block features are
+// formed on the host (7652 blocks: a fraction of a millisecond), the
+// frequency features and the MLP on the device.
 int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
-                     const std::vector<int32_t> &far, std::vector<int32_t> &kpred_by_block,
-                     std::vector<double> &cost) {
+                     const std::vector<int32_t> &far, int kcap, int32_t *dkpred, std::vector<double> &cost,
+                     std::vector<int32_t> &ks) {
     tdbem_ctx *ctx = M->ctx;
-    std::vector<float> x;
-    td_block_features(t, m, f, c, far, x);
     const int Nu = f->Nu;
-    const int64_t n = (int64_t)far.size() * Nu;
-    float *dx = nullptr;
-    int *dbins = nullptr;
-    if (cudaMalloc(&dx, sizeof(float) * std::max<int64_t>(1, x.size())) != cudaSuccess ||
-        cudaMalloc(&dbins, sizeof(int) * std::max<int64_t>(1, n)) != cudaSuccess) {
-        cudaFree(dx);
-        return td_fail(ctx, TDBEM_ERR_OOM, "predictor buffers");
+    const int nfar = (int)far.size();
+    cost.assign(nfar, 0.0);
+    ks.assign(nfar, 0);
+    if (nfar == 0) return TDBEM_OK;
+    double h = 0.0;
+    for (int64_t e = 0; e < m->nt; ++e)
+        for (int k = 0; k < 3; ++k) {
+            const double *a = &m->verts[3 * m->tris[3 * e + k]], *b = &m->verts[3 * m->tris[3 * e + (k + 1) % 3]];
+            h += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+        }
+    h /= (3.0 * m->nt);
+    // host staging: bfeat [nfar][5] | ffeat [Nu][2] | far [nfar] | len [nfar] (4-byte words)
+    const size_t nw = (size_t)nfar * 5 + (size_t)Nu * 2 + (size_t)nfar * 2;
+    std::vector<uint32_t> host(nw);
+    float *bf = reinterpret_cast<float *>(host.data());
+    float *ff = bf + (size_t)nfar * 5;
+    int32_t *hfar = reinterpret_cast<int32_t *>(ff + (size_t)Nu * 2);
+    int32_t *hlen = hfar + nfar;
+    for (int q = 0; q < nfar; ++q) {
+        const int32_t *bl = &t->blocks[5 * far[q]];
+        const ClusterNode *A = find_node(t->side[0], bl[0], bl[1]), *B = find_node(t->side[1], bl[2], bl[3]);
+        const double da = A ? diag(*A) : 0.0, db = B ? diag(*B) : 0.0;
+        const double ds = (A && B) ? std::max(gap(*A, *B), 1e-300) : 1.0;
+        float *o = bf + (size_t)q * 5;
+        o[0] = (float)std::log(std::max(da, 1e-300) / ds);
+        o[1] = (float)std::log(std::max(db, 1e-300) / ds);
+        o[2] = (float)std::log(ds / h);
+        o[3] = (float)(std::min(da, db) / ds);
+        o[4] = (float)ds;
+        hfar[q] = far[q];
+        hlen[q] = (bl[1] - bl[0]) + (bl[3] - bl[2]);
+    }
+    for (int u = 0; u < Nu; ++u) {
+        ff[2 * u] = (float)(f->s[2 * f->uidx[u]] / c);
+        ff[2 * u + 1] = (float)(std::fabs(f->s[2 * f->uidx[u] + 1]) / c);
+    }
+    // device buffers (kept by the model, grown when needed): staging + ks [nfar] + cost [nfar]
+    const size_t need = sizeof(uint32_t) * (nw + 2 * (size_t)nfar);
+    if (need > M->pbytes) {
+        if (M->pbuf) cudaFree(M->pbuf);
+        M->pbuf = nullptr;
+        M->pbytes = 0;
+        if (cudaMalloc(&M->pbuf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return td_fail(ctx, TDBEM_ERR_OOM, "predictor buffers");
+        }
+        M->pbytes = need;
     }
     int rc = model_bf16(M);
-    std::vector<int> bins(n);
-    if (!rc) {
-        cudaMemcpyAsync(dx, x.data(), sizeof(float) * x.size(), cudaMemcpyHostToDevice, ctx->stream);
-        if (td_mlp_predict(ctx->stream, M->Pb, dx, n, dbins, nullptr, ctx->num_sms))
-            rc = td_fail(ctx, TDBEM_ERR_CUDA, "predictor kernel failed");
-        else if (cudaMemcpyAsync(bins.data(), dbins, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-                 cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-            rc = td_fail(ctx, TDBEM_ERR_CUDA, "predictor copy failed");
-    }
-    cudaFree(dx);
-    cudaFree(dbins);
     if (rc) return rc;
-    const int64_t nb = (int64_t)t->blocks.size() / 5;
-    kpred_by_block.assign(nb * Nu, 0);
-    cost.assign(far.size(), 0.0);
-    for (size_t q = 0; q < far.size(); ++q) {
-        const int32_t *bl = &t->blocks[5 * far[q]];
-        const double len = (double)(bl[1] - bl[0]) + (bl[3] - bl[2]);
-        for (int u = 0; u < Nu; ++u) {
-            const int kp = bin_lower(bins[q * Nu + u]);
-            kpred_by_block[(int64_t)far[q] * Nu + u] = kp;
-            cost[q] += len * kp * kp;
-        }
-    }
+    uint32_t *dev = (uint32_t *)M->pbuf;
+    const float *dbf = (const float *)dev;
+    const float *dff = dbf + (size_t)nfar * 5;
+    const int32_t *dfar = (const int32_t *)(dff + (size_t)Nu * 2);
+    const int32_t *dlen = dfar + nfar;
+    int32_t *dks = (int32_t *)(dlen + nfar);
+    float *dcost = (float *)(dks + nfar);
+    std::vector<float> hcost(nfar);
+    if (cudaMemcpyAsync(dev, host.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(dks, 0, sizeof(int32_t) * 2 * nfar, ctx->stream) != cudaSuccess ||
+        td_mlp_presize(ctx->stream, M->Pb, dbf, dff, nfar, Nu, dfar, dlen, kcap, dkpred, dks, dcost, ctx->num_sms) ||
+        cudaMemcpyAsync(ks.data(), dks, sizeof(int32_t) * nfar, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(hcost.data(), dcost, sizeof(float) * nfar, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return td_fail(ctx, TDBEM_ERR_CUDA, "predictor presizing failed");
+    for (int q = 0; q < nfar; ++q) cost[q] = hcost[q];
     return TDBEM_OK;
 }
 
@@ -182,6 +219,7 @@ extern "C" int tdbem_model_create(tdbem_ctx_t ctx, uint64_t seed, tdbem_model_t 
 extern "C" int tdbem_model_destroy(tdbem_model_t M) {
     if (M) {
         cudaFree(M->P);
+        if (M->pbuf) cudaFree(M->pbuf);
         delete M;
     }
     return TDBEM_OK;
