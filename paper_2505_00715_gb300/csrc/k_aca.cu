@@ -281,7 +281,7 @@ struct FarShared {
     typename AmOf<T>::type red[2][32];  // arg-max scratch, used alternately
     AccT<T> nrow[64], nu[64], nv[64];  // ACA norm terms per step (face rank <= 64)
     double normS2, normC2;
-    double redd[32 * 3];               // block sums of the dense path
+    AccT<T> red3[2][32][3];            // block sums of the dense path, used alternately
     int kstop, stop, knext;
     int idx;
     long long off;
@@ -643,8 +643,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     }
                     am2 = block_argmax_1sync(am2, S.red[par]);
                     par ^= 1;
-                    // S += u v^T with ||S||_F^2, |u|^2 and |v|^2 (FP32 partial sums, FP64 block sums)
-                    double sums[3] = {0.0, 0.0, 0.0};
+                    // S += u v^T with ||S||_F^2, |u|^2 and |v|^2: FP32 partial and block sums,
+                    // the stopping test in FP64 by each warp's first lane (no FP64 per element)
+                    bool stop;
                     {
                         A s2 = 0, uu = 0, vv = 0;
                         const cx<T> *uk = Uw + (int64_t)kf * a.maxI, *vk = Vw + (int64_t)kf * a.maxJ;
@@ -657,14 +658,30 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                         }
                         for (int i = tid; i < nI; i += blockDim.x) uu += cabs2(uk[i]);
                         for (int j = tid; j < nJ; j += blockDim.x) vv += cabs2(vk[j]);
-                        sums[0] = s2;
-                        sums[1] = uu;
-                        sums[2] = vv;
+                        s2 = warp_sum(s2);
+                        uu = warp_sum(uu);
+                        vv = warp_sum(vv);
+                        if (lane == 0) {
+                            S.red3[par][wid][0] = s2;
+                            S.red3[par][wid][1] = uu;
+                            S.red3[par][wid][2] = vv;
+                        }
+                        __syncthreads();
+                        int st = 0;
+                        if (lane == 0) {
+                            A t0 = 0, t1 = 0, t2 = 0;
+                            for (int w = 0; w < nwarps; ++w) {
+                                t0 += S.red3[par][w][0];
+                                t1 += S.red3[par][w][1];
+                                t2 += S.red3[par][w][2];
+                            }
+                            st = sqrt((double)t1 * (double)t2) <= p.eps_aca * sqrt((double)t0);
+                        }
+                        stop = __shfl_sync(0xffffffffu, st, 0) != 0;
                     }
-                    block_sum<3>(sums, S.redd);
                     const bool have_next = !(am2.i == 0x7fffffff || am2.v < 0);
                     ++kf;
-                    if (sqrt(sums[1] * sums[2]) <= p.eps_aca * sqrt(sums[0]) || !have_next) {
+                    if (stop || !have_next) {
                         converged = true;
                         break;
                     }
