@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(128) k_near_aca(NearArgs a, TensorOut o, AcaPa
                 for (int d = 0; d < l; ++d) cross += s_g[d].x * s_gf[d].x - s_g[d].y * s_gf[d].y;
                 const double hl2 = s_g[l].x, fl2 = s_gf[l].x;
                 s_normC2 += 2.0 * cross + hl2 * fl2;
-                s_stop = sqrt(hl2 * fl2) <= p.eps * sqrt(s_normC2);
+                s_stop = hl2 * fl2 <= p.eps * p.eps * s_normC2;  // ||H_l|| ||f_l|| <= eps ||C||, squared
             }
             __syncthreads();
             if (s_stop) {
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                                 t1 += S.red3[par][w][1];
                                 t2 += S.red3[par][w][2];
                             }
-                            st = sqrt((double)t1 * (double)t2) <= p.eps_aca * sqrt((double)t0);
+                            st = (double)t1 * (double)t2 <= p.eps_aca * p.eps_aca * (double)t0;  // squared test, no FP64 sqrt
                         }
                         stop = __shfl_sync(0xffffffffu, st, 0) != 0;
                     }
@@ -815,7 +815,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     for (int t = pend0; t <= kf; ++t) {
                         const double uu = S.nu[t], vv = S.nv[t];
                         n2 += 2.0 * (double)S.nrow[t] + uu * vv;
-                        if (sqrt(uu * vv) <= p.eps_aca * sqrt(n2)) {
+                        if (uu * vv <= p.eps_aca * p.eps_aca * n2) {
                             kstop = t;
                             break;
                         }
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 for (int d = 0; d < l; ++d) cross += (double)F.gH[2 * d] * F.gf[d].x - (double)F.gH[2 * d + 1] * F.gf[d].y;
                 const double hl2 = F.gH[2 * l], fl2 = F.gf[l].x;
                 S.normC2 += 2.0 * cross + hl2 * fl2;
-                S.stop = sqrt(fabs(hl2) * fl2) <= p.eps * sqrt(S.normC2);
+                S.stop = fabs(hl2) * fl2 <= p.eps * p.eps * S.normC2;  // ||H_l|| ||f_l|| <= eps ||C||, squared
             }
             __syncthreads();
             if (S.stop) {
