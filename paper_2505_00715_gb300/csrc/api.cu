@@ -473,7 +473,10 @@ extern "C" int tdbem_tree_build(tdbem_mesh_t mesh, int32_t row_basis, int32_t co
     t->leaf = leaf;
     t->eta = eta;
     td_plan_tree(mesh, row_basis, leaf, t->side[0]);
-    td_plan_tree(mesh, col_basis, leaf, t->side[1]);
+    if (col_basis == row_basis)
+        t->side[1] = t->side[0];  // the same DOF points give the same tree
+    else
+        td_plan_tree(mesh, col_basis, leaf, t->side[1]);
     td_plan_blocks(t->side[0], t->side[1], eta, t->blocks);
     *out = t;
     return TDBEM_OK;
