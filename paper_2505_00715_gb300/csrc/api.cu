@@ -961,6 +961,21 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     }
     for (int64_t b = 0; b < nb; ++b)
         if (bgroup[b] >= 0) zbase[b] = groups[bgroup[b]].zoff + brow[b] * groups[bgroup[b]].L;
+    // far terms and their T offsets (k_d from the device copy of the face ranks)
+    std::vector<int32_t> frank((size_t)nb * t->Nu);
+    TD_CUDA(ctx, cudaMemcpy(frank.data(), t->dfrank, sizeof(int32_t) * frank.size(), cudaMemcpyDeviceToHost));
+    std::vector<int2> ftab;
+    std::vector<int64_t> toff((size_t)nb * t->Nu, -1);
+    int64_t tsize = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        if (!t->blocks[5 * b + 4]) continue;
+        for (int d = 0; d < t->rank[b]; ++d) {
+            const int kd = frank[(size_t)b * t->Nu + d];
+            ftab.push_back(make_int2((int)b, d));
+            toff[(size_t)b * t->Nu + d] = tsize;
+            tsize += (int64_t)rpt * std::max(kd, 0) * nrhs;
+        }
+    }
     if (jobs.size() > (size_t)INT32_MAX || rowtab.size() > (size_t)INT32_MAX)
         return td_fail(ctx, TDBEM_ERR_ARG, "apply plan too large");
     if (t->plan_mem || t->plan_Z) TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // an earlier apply may still read them
@@ -969,15 +984,17 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     t->plan_mem = t->plan_Z = nullptr;
     t->plan_nrhs = 0;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[5];
+    size_t off[7];
     off[0] = 0;
     off[1] = off[0] + al(sizeof(ZGroup) * groups.size());
     off[2] = off[1] + al(sizeof(int2) * rowtab.size());
     off[3] = off[2] + al(sizeof(ZJob) * jobs.size());
     off[4] = off[3] + al(sizeof(int64_t) * nb);
+    off[5] = off[4] + al(sizeof(int2) * ftab.size());
+    off[6] = off[5] + al(sizeof(int64_t) * toff.size());
     char *mem = nullptr;
-    if (cudaMalloc(&mem, std::max<size_t>(off[4], 256)) != cudaSuccess ||
-        cudaMalloc(&t->plan_Z, sizeof(c32) * std::max<int64_t>(zsize, 1)) != cudaSuccess) {
+    if (cudaMalloc(&mem, std::max<size_t>(off[6], 256)) != cudaSuccess ||
+        cudaMalloc(&t->plan_Z, sizeof(c32) * (std::max<int64_t>(zsize, 1) + tsize)) != cudaSuccess) {
         cudaGetLastError();
         if (mem) cudaFree(mem);
         t->plan_Z = nullptr;
@@ -988,7 +1005,11 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     TD_CUDA(ctx, cudaMemcpy(mem + off[1], rowtab.data(), sizeof(int2) * rowtab.size(), cudaMemcpyHostToDevice));
     TD_CUDA(ctx, cudaMemcpy(mem + off[2], jobs.data(), sizeof(ZJob) * jobs.size(), cudaMemcpyHostToDevice));
     TD_CUDA(ctx, cudaMemcpy(mem + off[3], zbase.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice));
-    for (int k = 0; k < 4; ++k) t->plan_off[k] = off[k];
+    TD_CUDA(ctx, cudaMemcpy(mem + off[4], ftab.data(), sizeof(int2) * ftab.size(), cudaMemcpyHostToDevice));
+    TD_CUDA(ctx, cudaMemcpy(mem + off[5], toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
+    for (int k = 0; k < 6; ++k) t->plan_off[k] = off[k];
+    t->plan_nft = (int)ftab.size();
+    t->plan_tz = std::max<int64_t>(zsize, 1);  // T follows Z in plan_Z
     t->plan_rpt = rpt;
     t->plan_njobs = (int)jobs.size();
     t->plan_maxI = t->plan_maxJ = 1;
@@ -1025,8 +1046,10 @@ int apply_tc(tdbem_tensor *t, const void *W, int nrhs, void *y) {
     a.zbase = zbase;
     a.Z = (const c32 *)t->plan_Z;
     a.y = (c32 *)y;
-    a.kcap = t->kcap;
-    a.max_near_rows = t->max_near_rows;
+    a.nft = t->plan_nft;
+    a.ftab = (const int2 *)(mem + t->plan_off[4]);
+    a.toff = (const int64_t *)(mem + t->plan_off[5]);
+    a.T = (c32 *)t->plan_Z + t->plan_tz;
     e = td_launch_apply_z(ctx->stream, a, tensor_out(t, nullptr), ctx->num_sms);
     if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "face apply kernel failed: %s", cudaGetErrorString((cudaError_t)e));
     return TDBEM_OK;

@@ -150,18 +150,61 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
     }
 }
 
-// Second phase of the tensor-core apply: the frequency contraction
-// z_(b,d,p) = sum_l f_d(l) W_l[J] is already in Z (k_zgemm.cu); the faces are
-// applied as in k_apply (near: y_I += H_d z1 + conj(H_d) z2; far:
-// y_I += U_d (V_d^T z1) + conj(U_d) (V_d^H z2)).  Z rows of a block are
-// (term d, half p) at zbase[b] + (rpt d + p) nJ nrhs.
-// dynamic shared memory (complex64): acc [acc_max]
-__global__ void __launch_bounds__(256) k_apply_z(ApplyZArgs a, TensorOut o) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    c32 *acc = reinterpret_cast<c32 *>(smem_raw);
-    const int nrhs = a.nrhs, Nu = a.Nu, RC = 4;
+// Second phase of the tensor-core apply.  The frequency contraction
+// z_(b,d,p) = sum_l f_d(l) W_l[J] is already in Z (k_zgemm.cu); Z rows of a
+// block are (term d, half p) at zbase[b] + (rpt d + p) nJ nrhs.
+//   k_apply_t: one warp per far term: T_p = V_d^T z_p (p = 1: conj V_d),
+//              16 ranks at a time in registers, lanes over (half, rhs);
+//   k_apply_y: one CTA per block, one thread per output (row, rhs), all
+//              terms accumulated in registers: far y_I += U_d T1 + conj(U_d) T2,
+//              near y_I += H_d z1 + conj(H_d) z2; one atomic add per output
+//              and block.  No shared memory and no barriers in either kernel.
+__global__ void __launch_bounds__(256) k_apply_t(ApplyZArgs a, TensorOut o) {
+    const int nrhs = a.nrhs, Nu = a.Nu, rpt = a.rpt, lane = threadIdx.x & 31;
     const c32 *pool = (const c32 *)o.face;
-    const int tid = threadIdx.x;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < a.nft; it += nwt) {
+        const int2 bd = a.ftab[it];
+        const int *bl = a.blocks + 5 * bd.x;
+        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
+        const int64_t tb = (int64_t)bd.x * Nu + bd.y;
+        const int kd = o.frank[tb];
+        const c32 *V = pool + o.foff[tb] + (int64_t)kd * nI;
+        const int64_t L = (int64_t)nJ * nrhs;
+        const c32 *z1 = a.Z + a.zbase[bd.x] + (int64_t)rpt * bd.y * L;
+        c32 *Tout = a.T + a.toff[tb];
+        for (int pc = lane; pc < rpt * nrhs; pc += 32) {
+            const int p = pc / nrhs, c = pc - p * nrhs;
+            const c32 *z = z1 + p * L + c;
+            for (int t0 = 0; t0 < kd; t0 += 16) {
+                const int nt = min(16, kd - t0);
+                c32 acc[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] = c32{0.f, 0.f};
+                for (int j = 0; j < nJ; ++j) {
+                    const c32 zj = z[(int64_t)j * nrhs];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (q < nt) {
+                            const c32 v = V[(int64_t)(t0 + q) * nJ + j];
+                            cfma(acc[q], p ? cconj(v) : v, zj);
+                        }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (q < nt) Tout[((int64_t)p * kd + t0 + q) * nrhs + c] = acc[q];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_apply_y(ApplyZArgs a, TensorOut o) {
+    // each thread: one row i and four consecutive right-hand sides (face
+    // loads shared by the four)
+    const int nrhs = a.nrhs, Nu = a.Nu, rpt = a.rpt;
+    const int nc4 = (nrhs + 3) >> 2;
+    const c32 *pool = (const c32 *)o.face;
     for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
         const int *bl = a.blocks + 5 * b;
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
@@ -169,83 +212,44 @@ __global__ void __launch_bounds__(256) k_apply_z(ApplyZArgs a, TensorOut o) {
         const int r = o.rank[b];
         if (r == 0 || a.zbase[b] < 0) continue;
         const int64_t tb = (int64_t)b * Nu, L = (int64_t)nJ * nrhs;
-        const c32 *Zb = a.Z + a.zbase[b];
-        for (int d0 = 0; d0 < r; d0 += RC) {
-            const int rc = min(RC, r - d0);
-            int sumk = 0;
-            if (far)
-                for (int d = d0; d < d0 + rc; ++d) sumk += o.frank[tb + d];
-            const int nacc = far ? sumk * 2 * nrhs : nI * nrhs;
-            __syncthreads();
-            for (int e = tid; e < nacc; e += blockDim.x) acc[e] = {0.f, 0.f};
-            __syncthreads();
-            if (!far) {
-                for (int e = tid; e < nI * nrhs; e += blockDim.x) {
-                    const int c = e % nrhs, i = e / nrhs;
-                    c32 s = {0.f, 0.f};
-                    for (int dd = 0; dd < rc; ++dd) {
-                        const c32 *H = pool + o.foff[tb + d0 + dd] + (int64_t)i * nJ;
-                        const c32 *z1 = Zb + (int64_t)a.rpt * (d0 + dd) * L + c;
-                        const c32 *z2 = z1 + L;
-                        if (a.rpt == 2) {
-                            for (int j = 0; j < nJ; ++j) {
-                                const c32 h = H[j];
-                                cfma(s, h, z1[(int64_t)j * nrhs]);
-                                cfma(s, cconj(h), z2[(int64_t)j * nrhs]);
-                            }
-                        } else {
-                            for (int j = 0; j < nJ; ++j) cfma(s, H[j], z1[(int64_t)j * nrhs]);
-                        }
-                    }
-                    acc[e] = s;
+        for (int e = threadIdx.x; e < nI * nc4; e += blockDim.x) {
+            const int i = e / nc4, c0 = 4 * (e - i * nc4), nc = min(4, nrhs - c0);
+            c32 acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = c32{0.f, 0.f};
+            for (int d = 0; d < r; ++d) {
+                const c32 *X1, *X2, *M;
+                int K;
+                int64_t ms;
+                if (far) {
+                    K = o.frank[tb + d];
+                    M = pool + o.foff[tb + d] + i;  // U[t][i], stride nI
+                    ms = nI;
+                    X1 = a.T + a.toff[tb + d] + c0;
+                    X2 = X1 + (int64_t)K * nrhs;
+                } else {
+                    K = nJ;
+                    M = pool + o.foff[tb + d] + (int64_t)i * nJ;  // H[i][j], stride 1
+                    ms = 1;
+                    X1 = a.Z + a.zbase[b] + (int64_t)rpt * d * L + c0;
+                    X2 = X1 + L;
                 }
-            } else {
-                // acc[(tau, p, c)] = sum_j V[tau][j] z_p[j][c]  (p = 1 uses conj V)
-                for (int e = tid; e < sumk * nrhs; e += blockDim.x) {
-                    const int c = e % nrhs;
-                    int t = e / nrhs, dd = 0;
-                    while (t >= o.frank[tb + d0 + dd]) {
-                        t -= o.frank[tb + d0 + dd];
-                        ++dd;
+#pragma unroll 2
+                for (int t = 0; t < K; ++t) {
+                    const c32 mv = M[(int64_t)t * ms], mc = cconj(mv);
+                    const c32 *x1 = X1 + (int64_t)t * nrhs, *x2 = X2 + (int64_t)t * nrhs;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q >= nc) continue;
+                        cfma(acc[q], mv, x1[q]);
+                        if (rpt == 2) cfma(acc[q], mc, x2[q]);
                     }
-                    const int kd = o.frank[tb + d0 + dd];
-                    const c32 *V = pool + o.foff[tb + d0 + dd] + (int64_t)kd * nI + (int64_t)t * nJ;
-                    const c32 *z1 = Zb + (int64_t)a.rpt * (d0 + dd) * L + c;
-                    const c32 *z2 = z1 + L;
-                    c32 s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
-                    for (int j = 0; j < nJ; ++j) {
-                        const c32 v = V[j];
-                        cfma(s1, v, z1[(int64_t)j * nrhs]);
-                        if (a.rpt == 2) cfma(s2, cconj(v), z2[(int64_t)j * nrhs]);
-                    }
-                    acc[(e / nrhs) * 2 * nrhs + c] = s1;
-                    acc[(e / nrhs) * 2 * nrhs + nrhs + c] = s2;
                 }
             }
-            __syncthreads();
-            if (!far) {
-                for (int e = tid; e < nI * nrhs; e += blockDim.x) {
-                    const int c = e % nrhs, i = e / nrhs;
-                    atomic_add_c(a.y + (int64_t)a.perm_r[bl[0] + i] * nrhs + c, acc[e]);
-                }
-            } else {
-                for (int e = tid; e < nI * nrhs; e += blockDim.x) {
-                    const int c = e % nrhs, i = e / nrhs;
-                    c32 s = {0.f, 0.f};
-                    int base = 0;
-                    for (int dd = 0; dd < rc; ++dd) {
-                        const int kd = o.frank[tb + d0 + dd];
-                        const c32 *U = pool + o.foff[tb + d0 + dd];
-                        for (int t = 0; t < kd; ++t) {
-                            const c32 u = U[(int64_t)t * nI + i];
-                            cfma(s, u, acc[(int64_t)(base + t) * 2 * nrhs + c]);
-                            cfma(s, cconj(u), acc[(int64_t)(base + t) * 2 * nrhs + nrhs + c]);
-                        }
-                        base += kd;
-                    }
-                    atomic_add_c(a.y + (int64_t)a.perm_r[bl[0] + i] * nrhs + c, s);
-                }
-            }
+            c32 *yr = a.y + (int64_t)a.perm_r[bl[0] + i] * nrhs + c0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nc) atomic_add_c(yr + q, acc[q]);
         }
     }
 }
@@ -327,14 +331,12 @@ int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorO
 }
 
 int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms) {
-    ApplyZArgs aa = a;
-    aa.acc_max = (int64_t)std::max(2 * 4 * a.kcap, a.max_near_rows) * a.nrhs;
-    const size_t sm = sizeof(c32) * aa.acc_max;
-    if (sm > (size_t)(220 * 1024)) return (int)cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_apply_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
-    const int grid = std::min(a.nb, num_sms * 4);
-    k_apply_z<<<grid, 256, sm, st>>>(aa, o);
+    if (a.nft > 0) {
+        const int grid = (int)std::min<int64_t>(((int64_t)a.nft * 32 + 255) / 256, (int64_t)num_sms * 8);
+        k_apply_t<<<grid, 256, 0, st>>>(a, o);
+    }
+    const int grid = std::min(a.nb, num_sms * 8);
+    k_apply_y<<<grid, 256, 0, st>>>(a, o);
     return (int)cudaGetLastError();
 }
 

@@ -116,8 +116,11 @@ struct ApplyZArgs {
     const int64_t *zbase;   // [nb] Z offset of the block's first row (-1: rank 0)
     const c32 *Z;
     c32 *y;
-    int kcap, max_near_rows;
-    int64_t acc_max;
+    // far terms: T = V_d^T z1 and V_d^H z2, at toff[b Nu + d] + (p k_d + tau) nrhs + c
+    int nft;                // number of far terms
+    const int2 *ftab;       // (block, term) of every far term
+    const int64_t *toff;    // [nb][Nu]
+    c32 *T;
 };
 int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms);
 int td_launch_tensor_entries(cudaStream_t st, int prec, const TensorOut &o, const int *blocks,
