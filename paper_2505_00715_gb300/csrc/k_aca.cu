@@ -568,6 +568,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             // dense-path blocks: C(k) = sum_d f_d[k] H_d from the rebuilt faces, once per
             // term, and the face's own approximation S = 0 (it becomes H_l)
             cx<T> *Sd = Hs + (int64_t)l * dcap;
+            for (int t = tid; t < 64; t += blockDim.x) S.nrow[t] = A(0);
             if (small) {
                 for (int e = tid; e < nI * nJ; e += blockDim.x) {
                     cx<T> acc = {0, 0};
@@ -587,22 +588,20 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 // ---- dense path: R = A(k) - C(k) - S, S = sum_t u_t v_t^T kept densely
                 while (kf < p.kcap && guard < nI + p.kcap) {
                     ++guard;
-                    // residual row fibre at i*: entries, then minus C and S
+                    // residual row fibre at i*: entry minus C and S, by the group leader
+                    AM am = {-1, 0x7fffffff};
                     for (int j0 = wid * 4; j0 < nJ; j0 += nwarps * 4) {
                         const int j = j0 + (lane >> 3);
-                        const cx<T> v = group_entry<T, OP>(m, rows[istar], cols[min(j, nJ - 1)], sr, si, j < nJ);
-                        if (j < nJ && (lane & 7) == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
+                        const cx<T> ent = group_entry<T, OP>(m, rows[istar], cols[min(j, nJ - 1)], sr, si, j < nJ);
+                        if (j < nJ && (lane & 7) == 0) {
+                            const int64_t e = (int64_t)istar * nJ + j;
+                            const cx<T> v = ent - Cd[e] - Sd[e];
+                            Vw[(int64_t)kf * a.maxJ + j] = v;
+                            const auto key = pivot_key(v);
+                            if (am_better(key, j, am.v, am.i)) am = {key, j};
+                        }
                     }
                     ev_reg += nJ;
-                    __syncthreads();
-                    AM am = {-1, 0x7fffffff};
-                    for (int j = tid; j < nJ; j += blockDim.x) {
-                        const int64_t e = (int64_t)istar * nJ + j;
-                        const cx<T> v = Vw[(int64_t)kf * a.maxJ + j] - Cd[e] - Sd[e];
-                        Vw[(int64_t)kf * a.maxJ + j] = v;
-                        const auto key = pivot_key(v);
-                        if (am_better(key, j, am.v, am.i)) am = {key, j};
-                    }
                     am = block_argmax_1sync(am, S.red[par]);
                     par ^= 1;
                     if (tid == 0) used[istar >> 5] |= 1u << (istar & 31);
@@ -625,22 +624,21 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     const int jstar = am.i;
                     const cx<T> piv = Vw[(int64_t)kf * a.maxJ + jstar];
                     // residual column fibre at j*, divided by the pivot
+                    AM am2 = {-1, 0x7fffffff};
                     for (int i0 = wid * 4; i0 < nI; i0 += nwarps * 4) {
                         const int i = i0 + (lane >> 3);
-                        const cx<T> v = group_entry<T, OP>(m, rows[min(i, nI - 1)], cols[jstar], sr, si, i < nI);
-                        if (i < nI && (lane & 7) == 0) Uw[(int64_t)kf * a.maxI + i] = v;
+                        const cx<T> ent = group_entry<T, OP>(m, rows[min(i, nI - 1)], cols[jstar], sr, si, i < nI);
+                        if (i < nI && (lane & 7) == 0) {
+                            const int64_t e = (int64_t)i * nJ + jstar;
+                            const cx<T> u = cdiv(ent - Cd[e] - Sd[e], piv);
+                            Uw[(int64_t)kf * a.maxI + i] = u;
+                            if (i != istar && !(used[i >> 5] & (1u << (i & 31)))) {
+                                const auto key = pivot_key(u);
+                                if (am_better(key, i, am2.v, am2.i)) am2 = {key, i};
+                            }
+                        }
                     }
                     ev_reg += nI;
-                    __syncthreads();
-                    AM am2 = {-1, 0x7fffffff};
-                    for (int i = tid; i < nI; i += blockDim.x) {
-                        const int64_t e = (int64_t)i * nJ + jstar;
-                        const cx<T> u = cdiv(Uw[(int64_t)kf * a.maxI + i] - Cd[e] - Sd[e], piv);
-                        Uw[(int64_t)kf * a.maxI + i] = u;
-                        if (i == istar || (used[i >> 5] & (1u << (i & 31)))) continue;
-                        const auto key = pivot_key(u);
-                        if (am_better(key, i, am2.v, am2.i)) am2 = {key, i};
-                    }
                     am2 = block_argmax_1sync(am2, S.red[par]);
                     par ^= 1;
                     // S += u v^T with ||S||_F^2, |u|^2 and |v|^2: FP32 partial and block sums,
