@@ -190,15 +190,19 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
                 for (int q = lane; q < nq; q += 32) {
                     double d[3], w, lam[3];
                     ss_point(G, q, m.ng, m.gx, m.gw, d, w, lam);
-                    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                    double base;
+                    // the transformed point and the difference x - y in FP64 (no
+                    // cancellation near the singularity); |d|^2 is exact to FP64
+                    // rounding, so the square root, the division and the rest run
+                    // in FP32 at FP32 relative accuracy
+                    const float r2 = (float)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    const float rinv = rsqrtf(r2), rf = r2 * rinv;
+                    float bf;
                     if (OP == TD_SLP) {
-                        base = w / r;
+                        bf = (float)w * rinv;
                     } else {
-                        const double dn = -(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]);
-                        base = w * dn / (r * r * r);
+                        const float dn = (float)(-(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]));
+                        bf = (float)w * dn * rinv * rinv * rinv;
                     }
-                    const float rf = (float)r, bf = (float)base;
                     float lf[3] = {(float)lam[0], (float)lam[1], (float)lam[2]};
 #pragma unroll
                     for (int j = 0; j < FC; ++j) {
@@ -223,9 +227,10 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
 #pragma unroll
             for (int j = 0; j < FC; ++j) {
                 c64 outv[NV];
+                // the lane partial sums are FP32: reduce them in FP32 (no FP64 shuffles)
 #pragma unroll
                 for (int k = 0; k < NV; ++k)
-                    outv[k] = {warp_sum((double)acc[j][k].x) * inv4pi, warp_sum((double)acc[j][k].y) * inv4pi};
+                    outv[k] = {(double)warp_sum(acc[j][k].x) * inv4pi, (double)warp_sum(acc[j][k].y) * inv4pi};
                 if (lane == 0 && f0 + j < nf) {
                     c64 *o = table + ((int64_t)p * nf + f0 + j) * 3;
                     const c64 z = {0.0, 0.0};
