@@ -698,21 +698,37 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     if (j < nJ && (lane & 7) == 0) Vw[(int64_t)kf * a.maxJ + j] = v;
                 }
                 ev_reg += nJ;
-                for (int c0 = 0;; c0 += kNCoef) {
+                if (small) {
+                    // previous terms from C(k); the face's own terms by each thread
+                    // (u_t[i*] broadcast, v_t[j] coalesced), no coefficient list
                     __syncthreads();
-                    total = build_coef(S, F, 0, istar, small ? 0 : l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
-                    __syncthreads();
-                    correct_fibre(S, Vw + (int64_t)kf * a.maxJ, nJ, min(kNCoef, total - c0));
-                    if (c0 + kNCoef >= total) break;
-                }
-                for (int j = tid; j < nJ; j += blockDim.x) {
-                    cx<T> v = Vw[(int64_t)kf * a.maxJ + j];
-                    if (small) {  // previous terms from C(k)
-                        v = v - Cd[(int64_t)istar * nJ + j];
+                    for (int j = tid; j < nJ; j += blockDim.x) {
+                        cx<T> v = Vw[(int64_t)kf * a.maxJ + j] - Cd[(int64_t)istar * nJ + j];
+                        cx<T> c4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+                        int t = 0;
+                        for (; t + 4 <= kf; t += 4) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                cfma(c4[q], Uw[(int64_t)(t + q) * a.maxI + istar], Vw[(int64_t)(t + q) * a.maxJ + j]);
+                        }
+                        for (; t < kf; ++t) cfma(c4[0], Uw[(int64_t)t * a.maxI + istar], Vw[(int64_t)t * a.maxJ + j]);
+                        v = v - ((c4[0] + c4[1]) + (c4[2] + c4[3]));
                         Vw[(int64_t)kf * a.maxJ + j] = v;
+                        const auto key = pivot_key(v);
+                        if (am_better(key, j, am.v, am.i)) am = {key, j};
                     }
-                    const auto key = pivot_key(v);
-                    if (am_better(key, j, am.v, am.i)) am = {key, j};
+                } else {
+                    for (int c0 = 0;; c0 += kNCoef) {
+                        __syncthreads();
+                        total = build_coef(S, F, 0, istar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                        __syncthreads();
+                        correct_fibre(S, Vw + (int64_t)kf * a.maxJ, nJ, min(kNCoef, total - c0));
+                        if (c0 + kNCoef >= total) break;
+                    }
+                    for (int j = tid; j < nJ; j += blockDim.x) {
+                        const auto key = pivot_key(Vw[(int64_t)kf * a.maxJ + j]);
+                        if (am_better(key, j, am.v, am.i)) am = {key, j};
+                    }
                 }
                 am = block_argmax_1sync(am, S.red[par]);
                 par ^= 1;
@@ -747,19 +763,31 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     if (i < nI && (lane & 7) == 0) Uw[(int64_t)kf * a.maxI + i] = v;
                 }
                 ev_reg += nI;
-                for (int c0 = 0;; c0 += kNCoef) {
-                    __syncthreads();
-                    total = build_coef(S, F, 1, jstar, small ? 0 : l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
-                    __syncthreads();
-                    correct_fibre(S, Uw + (int64_t)kf * a.maxI, nI, min(kNCoef, total - c0));
-                    if (c0 + kNCoef >= total) break;
+                if (!small) {
+                    for (int c0 = 0;; c0 += kNCoef) {
+                        __syncthreads();
+                        total = build_coef(S, F, 1, jstar, l, kf, k, Nu, tb, nI, nJ, pool, fib, Uw, Vw, a.maxI, a.maxJ, c0);
+                        __syncthreads();
+                        correct_fibre(S, Uw + (int64_t)kf * a.maxI, nI, min(kNCoef, total - c0));
+                        if (c0 + kNCoef >= total) break;
+                    }
                 }
                 __syncthreads();
                 AM am2 = {-1, 0x7fffffff};
                 for (int i = tid; i < nI; i += blockDim.x) {
                     cx<T> u = Uw[(int64_t)kf * a.maxI + i];
                     if (small) {
+                        // previous terms from C(k); the face's own terms by each thread
                         u = u - Cd[(int64_t)i * nJ + jstar];
+                        cx<T> c4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+                        int t = 0;
+                        for (; t + 4 <= kf; t += 4) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                cfma(c4[q], Vw[(int64_t)(t + q) * a.maxJ + jstar], Uw[(int64_t)(t + q) * a.maxI + i]);
+                        }
+                        for (; t < kf; ++t) cfma(c4[0], Vw[(int64_t)t * a.maxJ + jstar], Uw[(int64_t)t * a.maxI + i]);
+                        u = u - ((c4[0] + c4[1]) + (c4[2] + c4[3]));
                         Uw[(int64_t)kf * a.maxI + i] = u;
                     }
                     if (used[i >> 5] & (1u << (i & 31))) continue;
