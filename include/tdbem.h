@@ -83,7 +83,8 @@ typedef struct {
     double eps;      /* tolerance of Algorithm 1 on each block (e.g. 1e-4) */
     double eps_aca;  /* tolerance of the ACA of every far-field face (e.g. 1e-6) */
     int32_t max_face_rank; /* cap of the face ACA rank, 1..64 (<= 0: 64) */
-    int32_t flags;         /* bit 0: launch the phases without graph capture */
+    int32_t flags;         /* bit 0: launch the phases without graph capture; bit 1: no dense
+                              working faces (low-rank corrections and Grams for every far block) */
     tdbem_model_t model;   /* nullable: rank predictor (see the rank-predictor section) */
 } tdbem_aca_cfg;
 

@@ -259,10 +259,11 @@ class Tensor:
 
 
 def compress(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64,
-             use_graph=True, model=None):
+             use_graph=True, model=None, dense_faces=True):
     ctx = mesh.ctx
     o = _op(op, prec, c, ng)
-    cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, 0 if use_graph else 1, model.h if model is not None else None)
+    flags = (0 if use_graph else 1) | (0 if dense_faces else 2)
+    cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, flags, model.h if model is not None else None)
     h = C.c_void_p()
     ctx.check(ctx.L.tdbem_compress(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), C.byref(h)),
               "tdbem_compress")

@@ -689,6 +689,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         const int64_t budget = (int64_t)8 << 30;
         const int64_t per = (int64_t)es * (Nu + 1) * std::max(1, nctas_far);
         dense_cap = std::min<int64_t>(dense_cap, budget / per);
+        if (cfg->flags & 2) dense_cap = 0;  // low-rank evaluation for every far block
     }
     const int64_t sper_far = (int64_t)kcap * (maxI + maxJ) + (int64_t)(Nu + 1) * dense_cap;
     if ((rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size())) ||

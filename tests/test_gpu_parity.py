@@ -127,18 +127,21 @@ def _dense_all(om, orc, op, f, nrows, ncols):
     return om.entries(getattr(orc, op), np.arange(nrows), np.arange(ncols), f.s, ng=5)
 
 
+@pytest.mark.parametrize("dense_faces", [True, False])
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
 @pytest.mark.parametrize("op", ["SLP", "DLP"])
-def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op):
+def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op, dense_faces):
     """320-triangle sphere, leaf 16 (leaf 32 has no admissible block here),
-    eta 2, BDF2 N = 16: rebuilt tensor and apply vs the dense oracle."""
+    eta 2, BDF2 N = 16: rebuilt tensor and apply vs the dense oracle, with the
+    far blocks' dense working faces and with the low-rank evaluation."""
     import torch
     V, T, gm, om = sphere2
     f = td.Freqs.bdf2(ctx, 16, 0.1)
     cols_b = td.P0 if op == "SLP" else td.P1
     tree = td.Tree(gm, td.P0, cols_b, 16, 2.0)
     eps = 1e-4
-    X = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec))
+    X = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec),
+                    dense_faces=dense_faces)
     st = X.stats()
     assert st["nfar"] > 0 and st["nnear"] > 0
     nr, nc = len(T), (len(T) if op == "SLP" else len(V))
@@ -163,28 +166,32 @@ def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op):
     assert np.linalg.norm(yh - y) <= 1e-5 * np.linalg.norm(y)
 
 
-@pytest.mark.parametrize("prec", ["MIXED", "FP64"])
-def test_config2_sampled_apply(td, ctx, orc, prec):
-    """5120-triangle sphere, SLP, BDF2 N = 64, dt = 0.05, leaf 32, eta 2,
-    eps 1e-4: apply on sampled rows vs the dense FP64 oracle apply."""
+@pytest.mark.parametrize("op,prec", [("SLP", "MIXED"), ("SLP", "FP64"), ("DLP", "MIXED")])
+def test_config2_sampled_apply(td, ctx, orc, op, prec):
+    """5120-triangle sphere, SLP (P0 x P0) and DLP (P0 x P1), BDF2 N = 64,
+    dt = 0.05, leaf 32, eta 2, eps 1e-4: apply on sampled rows vs the dense
+    FP64 oracle apply."""
     import torch
     V, T = icosphere(4)
     gm, om = td.Mesh(ctx, V, T), orc.Mesh(V, T)
     f = td.Freqs.bdf2(ctx, 64, 0.05)
-    tree = td.Tree(gm, td.P0, td.P0, 32, 2.0)
+    cols_b = td.P0 if op == "SLP" else td.P1
+    ncols = len(T) if op == "SLP" else len(V)
+    tree = td.Tree(gm, td.P0, cols_b, 32, 2.0)
     eps = 1e-4
-    X = td.compress(gm, td.SLP, f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec))
+    X = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec))
     st = X.stats()
-    print("config2 %s stats: %s" % (prec, st))
+    print("config2 %s %s stats: %s" % (op, prec, st))
     assert st["stored_complex"] < 0.5 * st["dense_complex"]
     nrhs = 2
-    W = random_weights(64, len(T), nrhs, seed=1)
+    W = random_weights(64, ncols, nrhs, seed=1)
     ct = torch.complex128 if prec == "FP64" else torch.complex64
     y = X.apply_weighted(torch.as_tensor(W, dtype=ct, device="cuda")).cpu().numpy()
     rng = np.random.default_rng(7)
     rows = np.sort(rng.choice(len(T), 12, replace=False)).astype(np.int32)
-    yd = om.dense_apply_rows(orc.SLP, f.s, rows, W, ng=5)
+    yd = om.dense_apply_rows(getattr(orc, op), f.s, rows, W, ng=5)
     err = np.linalg.norm(y[rows] - yd) / np.linalg.norm(yd)
+    print("config2 %s %s sampled apply error %.2e" % (op, prec, err))
     assert err < 3 * eps, err
 
 
