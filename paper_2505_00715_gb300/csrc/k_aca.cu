@@ -245,20 +245,27 @@ TD_D cx<T> group_entry(const MeshDev &m, int row, int col, T sr, T si, bool vali
     cx<T> acc = {0, 0};
     if (valid && sub < 7) {
         if (OP == TD_SLP) {
-            // two independent point pairs in flight per iteration
-            cx<T> acc2 = {0, 0};
+            // independent point pairs in flight: 3 + 3 + 1
+            cx<T> acc2 = {0, 0}, acc3 = {0, 0};
 #pragma unroll 1
-            for (int b = 0; b < 6; b += 2) {
+            for (int b = 0; b < 6; b += 3) {
                 acc = acc + point_pair(m, OP, row, sub, col, b, 0, sr, si);
                 acc2 = acc2 + point_pair(m, OP, row, sub, col, b + 1, 0, sr, si);
+                acc3 = acc3 + point_pair(m, OP, row, sub, col, b + 2, 0, sr, si);
             }
-            acc = acc + point_pair(m, OP, row, sub, col, 6, 0, sr, si) + acc2;
+            acc = acc + point_pair(m, OP, row, sub, col, 6, 0, sr, si) + (acc2 + acc3);
         } else {
             const int p1 = m.v2t_ptr[col + 1];
             for (int p = m.v2t_ptr[col]; p < p1; ++p) {
                 const int tj = m.v2t[p], loc = m.v2t_loc[p];
+                cx<T> acc2 = {0, 0}, acc3 = {0, 0};
 #pragma unroll 1
-                for (int b = 0; b < 7; ++b) acc = acc + point_pair(m, OP, row, sub, tj, b, loc, sr, si);
+                for (int b = 0; b < 6; b += 3) {
+                    acc = acc + point_pair(m, OP, row, sub, tj, b, loc, sr, si);
+                    acc2 = acc2 + point_pair(m, OP, row, sub, tj, b + 1, loc, sr, si);
+                    acc3 = acc3 + point_pair(m, OP, row, sub, tj, b + 2, loc, sr, si);
+                }
+                acc = acc + point_pair(m, OP, row, sub, tj, 6, loc, sr, si) + (acc2 + acc3);
             }
         }
     }
