@@ -42,6 +42,19 @@ WORKLOADS = {
 }
 
 
+def job_throughput(local_ms_total, units_per_step, steps, world, dist=None):
+    """Whole-job throughput of N independent replicas (weak scaling): the
+    timed region is the slowest rank's (max over ranks), every rank processed
+    units_per_step units per step.  Returns (value per second, max ms)."""
+    total_ms = float(local_ms_total)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * float(units_per_step) * steps / (total_ms / 1e3), total_ms
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -262,16 +275,11 @@ def main():
     with ClockSampler(local) as clk:
         res = timed(args.steps)
     ms = [r[0] for r in res]
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     st = res[-1][2]
     X = res[-1][3]
     apply_ms = statistics.median([r[1] for r in res])
     represented = float(nrows) * ncols * NQ
-    value = world * represented * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(sum(ms), represented, args.steps, world, dist)
     blocks = X.tree.blocks
     apply_gflops = apply_flops(X, blocks, NQ, nrhs) / (apply_ms / 1e3) / 1e9
 
