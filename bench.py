@@ -326,7 +326,7 @@ def main():
 
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
-    roof = roofline(st, X, cfg, blocks, peaks, peak_kind, clocks)
+    roof = roofline(st, X, cfg, blocks, peaks, peak_kind, clocks, args.workload)
     if rank == 0:
         line = {
             "metric": "entries/s", "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
@@ -411,7 +411,25 @@ def apply_flops(X, blocks, NQ, nrhs):
     return flops_a + face_entries * 8.0 * nrhs * 2.0
 
 
-def roofline(st, X, cfg, blocks, peaks, peak_kind, clocks):
+# DRAM bytes (read + write) of one far-kernel launch on the 5120-triangle
+# sphere, from a one-pass ncu capture of the kernel built from the sources
+# whose digest is recorded; reported only while those sources are unchanged.
+FAR_TRAFFIC = {"workload": "sphere5120_slp_bdf2_N64", "bytes": 23.96e9 + 7.42e9,
+               "sources": ("k_aca.cu", "pair.cuh", "kernels.h", "internal.h"), "sha256_16": "5f559c4aa7713779"}
+
+
+def far_traffic(workload):
+    import hashlib
+    if workload != FAR_TRAFFIC["workload"]:
+        return None
+    h = hashlib.sha256()
+    for f in FAR_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2505_00715_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return FAR_TRAFFIC["bytes"] if h.hexdigest()[:16] == FAR_TRAFFIC["sha256_16"] else None
+
+
+def roofline(st, X, cfg, blocks, peaks, peak_kind, clocks, workload=None):
     """Dominant phase of the compression against its ALU roofline.
 
     Far-field 3D-ACA kernel: its algorithmic work is the entry generation,
@@ -431,7 +449,8 @@ def roofline(st, X, cfg, blocks, peaks, peak_kind, clocks):
     far_pairs = (st["entries_regular"] - near_entries + st["entries_tube"]) * pairs_per_entry
     achieved_far = far_pairs * 4.0 / (st["ms_far"] / 1e3) / 1e12
     out = {"bound": "alu", "kernel": "far 3D-ACA (k_far_aca)" if dom == "far" else dom, "unit": "TSFU-op/s",
-           "achieved": achieved_far, "peak": sfu_peak, "frac": achieved_far / sfu_peak, "traffic": None,
+           "achieved": achieved_far, "peak": sfu_peak, "frac": achieved_far / sfu_peak, "traffic": far_traffic(workload),
+           "traffic_unit": "bytes per far launch (DRAM read + write, ncu)",
            "work": "%.3e point pairs x 4 SFU ops in %.1f ms" % (far_pairs, st["ms_far"]),
            "peak_source": "derived: 16 SFU ops/clk/SM x 152 SMs x %.0f MHz (sampled median)" % clock_mhz,
            "phase_ms": phases, "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_kind}
