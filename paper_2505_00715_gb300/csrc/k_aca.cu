@@ -16,6 +16,8 @@
 // (Sec. 4); the frequency tube at the pivot is evaluated with one warp per
 // frequency.  Persistent CTAs take far blocks from an atomic work queue
 // ordered by decreasing size.
+#include <type_traits>
+
 #include "internal.h"
 #include "kernels.h"
 #include "pair.cuh"
@@ -534,8 +536,94 @@ TD_D void gram_sums(const FarFreq<T> &F, GramTiles<T> &G, int l, int kf, int nI,
     __syncthreads();
 }
 
+// Rebuild of a large face H = sum_{t<kf} u_t v_t^T with its arg-max (FP32
+// form).  The face is swept in tiles of (NT/16)*4 rows x 64 columns; chunks
+// of KC factor columns are staged in shared memory (the Gram tiles' space),
+// and every thread accumulates a 4 x 4 register tile: rows 4*ty .. 4*ty+3
+// and columns tx, tx+16, tx+32, tx+48 (8 shared loads per 16 complex MACs,
+// conflict-free).  Entries are summed over t in the same order as the plain
+// rebuild.  Dense-face blocks also store the face to Sd.
+template <int NT>
+struct RebuildTile {
+    static constexpr int TI = NT / 16 * 4, TJ = 64, KC = NT <= 128 ? 16 : 8;
+};
+
+template <int NT, class AM>
+TD_D void rebuild_tiled(void *smem, const c32 *Uw, const c32 *Vw, int64_t maxI, int64_t maxJ, int kf, int nI, int nJ,
+                        c32 *Sd, AM &am) {
+    constexpr int TI = RebuildTile<NT>::TI, TJ = RebuildTile<NT>::TJ, KC = RebuildTile<NT>::KC;
+    c32(*su)[TI] = reinterpret_cast<c32(*)[TI]>(smem);
+    c32(*sv)[TJ] = reinterpret_cast<c32(*)[TJ]>(reinterpret_cast<c32 *>(smem) + KC * TI);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int i0 = 0; i0 < nI; i0 += TI) {
+        for (int j0 = 0; j0 < nJ; j0 += TJ) {
+            c32 h[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) h[x][y] = c32{0.f, 0.f};
+            for (int t0 = 0; t0 < kf; t0 += KC) {
+                const int kc = min(KC, kf - t0);
+                __syncthreads();
+                for (int e = tid; e < KC * TI; e += NT) {
+                    const int t = e / TI, x = e - t * TI;
+                    su[t][x] = (t < kc && i0 + x < nI) ? Uw[(int64_t)(t0 + t) * maxI + i0 + x] : c32{0.f, 0.f};
+                }
+                for (int e = tid; e < KC * TJ; e += NT) {
+                    const int t = e / TJ, y = e - t * TJ;
+                    sv[t][y] = (t < kc && j0 + y < nJ) ? Vw[(int64_t)(t0 + t) * maxJ + j0 + y] : c32{0.f, 0.f};
+                }
+                __syncthreads();
+                for (int t = 0; t < kc; ++t) {
+                    c32 u[4], v[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) u[x] = su[t][4 * ty + x];
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) v[y] = sv[t][tx + 16 * y];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) cfma(h[x][y], u[x], v[y]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int i = i0 + 4 * ty + x;
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int j = j0 + tx + 16 * y;
+                    if (i >= nI || j >= nJ) continue;
+                    const int e = i * nJ + j;
+                    if (Sd) Sd[e] = h[x][y];
+                    const auto key = pivot_key(h[x][y]);
+                    if (am_better(key, e, am.v, am.i)) am = {key, e};
+                }
+            }
+        }
+    }
+}
+
+// The tiled rebuild for FP32 faces whose tiles are at least half filled;
+// returns false (nothing done) otherwise and in the FP64 form.
+template <int NT, class T, class AM>
+TD_D bool rebuild_tiled_fp32(void *smem, const cx<T> *Uw, const cx<T> *Vw, int64_t maxI, int64_t maxJ, int kf, int nI,
+                             int nJ, cx<T> *Sd, AM &am) {
+    if constexpr (std::is_same<T, float>::value) {
+        constexpr int TI = RebuildTile<NT>::TI, TJ = RebuildTile<NT>::TJ;
+        const int64_t padded = (int64_t)((nI + TI - 1) / TI) * TI * (((nJ + TJ - 1) / TJ) * TJ);
+        if (2 * (int64_t)nI * nJ < padded) return false;
+        rebuild_tiled<NT>(smem, Uw, Vw, maxI, maxJ, kf, nI, nJ, Sd, am);
+        return true;
+    } else {
+        return false;
+    }
+}
+
 template <class T, int OP, int NT>
 __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
+    static_assert(sizeof(GramTiles<float>) >=
+                      RebuildTile<NT>::KC * (RebuildTile<NT>::TI + RebuildTile<NT>::TJ) * sizeof(c32),
+                  "rebuild tiles must fit in the Gram tiles' shared memory");
     using AM = typename AmOf<T>::type;
     using A = AccT<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -891,6 +979,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     const auto key = pivot_key(Sd[e]);
                     if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
                 }
+            } else if (rebuild_tiled_fp32<NT>(gt, Uw, Vw, a.maxI, a.maxJ, kf, nI, nJ, small ? Sd : nullptr, am)) {
+                // large face: tiled rebuild done
             } else {
                 // H = sum_t u_t v_t^T in 2 x 4 register tiles (6 loads per 8 complex MACs);
                 // dense-face blocks store it
