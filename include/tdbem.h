@@ -84,7 +84,10 @@ typedef struct {
     double eps_aca;  /* tolerance of the ACA of every far-field face (e.g. 1e-6) */
     int32_t max_face_rank; /* cap of the face ACA rank, 1..64 (<= 0: 64) */
     int32_t flags;         /* bit 0: launch the phases without graph capture; bit 1: no dense
-                              working faces (low-rank corrections and Grams for every far block) */
+                              working faces (low-rank corrections and Grams for every far block);
+                              bit 2: compress on the tree's partition as it is (by default far
+                              blocks with more than twice the mean far entries per persistent
+                              CTA are compressed as the blocks of their clusters' sons) */
     tdbem_model_t model;   /* nullable: rank predictor (see the rank-predictor section) */
 } tdbem_aca_cfg;
 
@@ -208,6 +211,12 @@ int tdbem_tensor_entries(tdbem_tensor_t t, const int32_t *rows, const int32_t *c
 /* Per-block results (host, nullable): ranks [nblocks], face rank sums
  * [nblocks], selected frequencies [nblocks][Nu+1] (-1 padded). */
 int tdbem_tensor_blocks(tdbem_tensor_t t, int32_t *rank, int32_t *face_rank_sum, int32_t *kpiv);
+/* The partition the tensor was compressed on (host, nullable): *nb blocks,
+ * blocks [nb][5] = row begin, row end, column begin, column end (permuted
+ * DOF ranges, as tdbem_tree_export) and 1 for far / 0 for near.  It refines
+ * the tree's partition (see flags bit 2 of tdbem_aca_cfg); the per-block
+ * results of tdbem_tensor_blocks follow its order. */
+int tdbem_tensor_partition(tdbem_tensor_t t, int64_t *nb, int32_t *blocks);
 int tdbem_tensor_destroy(tdbem_tensor_t t);
 /* Project-written autotuner of the persistent far-field phase (Sec. 4
  * Algorithm 1 on the admissible blocks): times complete compressions of the

@@ -192,6 +192,15 @@ class Tensor:
         self.ctx.check(self.ctx.L.tdbem_tensor_stats(self.h, C.byref(st)), "tdbem_tensor_stats")
         return st.as_dict()
 
+    def partition(self):
+        """The compression partition [nblocks][5] (row/column ranges in the
+        tree's permuted order, far flag); it refines the tree's blocks."""
+        nb = C.c_int64()
+        self.ctx.check(self.ctx.L.tdbem_tensor_partition(self.h, C.byref(nb), None), "tdbem_tensor_partition")
+        out = np.zeros((nb.value, 5), dtype=np.int32)
+        self.ctx.check(self.ctx.L.tdbem_tensor_partition(self.h, C.byref(nb), _np_ptr(out)), "tdbem_tensor_partition")
+        return out
+
     def blocks(self):
         nb = self.stats()["nblocks"]
         r = np.zeros(nb, dtype=np.int32)
@@ -259,10 +268,14 @@ class Tensor:
 
 
 def compress(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64,
-             use_graph=True, model=None, dense_faces=True):
+             use_graph=True, model=None, dense_faces=True, balance=True):
+    """3D-ACA compression of the operator tensor on the tree's blocks.
+    balance=False keeps the tree's partition; by default far blocks larger
+    than twice the mean far work of one persistent CTA are compressed as the
+    blocks of their clusters' sons (Tensor.partition())."""
     ctx = mesh.ctx
     o = _op(op, prec, c, ng)
-    flags = (0 if use_graph else 1) | (0 if dense_faces else 2)
+    flags = (0 if use_graph else 1) | (0 if dense_faces else 2) | (0 if balance else 4)
     cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, flags, model.h if model is not None else None)
     h = C.c_void_p()
     ctx.check(ctx.L.tdbem_compress(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), C.byref(h)),

@@ -74,6 +74,7 @@ EXPORTS = {
     "tdbem_tensor_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "tdbem_tensor_entries": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "tdbem_tensor_blocks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tdbem_tensor_partition": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "tdbem_tensor_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_apply_weighted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_apply_freq": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),

@@ -581,8 +581,15 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     T->ncols = tree->side[1].n;
     T->Nu = Nu;
     T->NQ = f->NQ;
-    T->blocks = tree->blocks;
-    const int64_t nb = (int64_t)tree->blocks.size() / 5;
+    const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
+    // compression partition: the tree's blocks, with far blocks that would
+    // outlast the rest of the persistent far phase split into sub-blocks
+    if (cfg->flags & 4)
+        T->blocks = tree->blocks;
+    else
+        td_balance_partition(tree->side[0], tree->side[1], tree->blocks, (int64_t)ctx->num_sms * ctx->far_cps[pf],
+                             T->blocks);
+    const int64_t nb = (int64_t)T->blocks.size() / 5;
     T->nblocks = nb;
     const size_t es = op->prec == TDBEM_FP64 ? sizeof(c64) : sizeof(c32);
     auto fail = [&](int code) {
@@ -595,7 +602,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     int64_t nent = 0, ntens = 0, maxIJ = 1, sum_far_len = 0;
     int maxI = 1, maxJ = 1, max_near_rows = 1;
     for (int64_t b = 0; b < nb; ++b) {
-        const int32_t *bl = &tree->blocks[5 * b];
+        const int32_t *bl = &T->blocks[5 * b];
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         if (bl[4]) {
             far_ids.push_back((int32_t)b);
@@ -613,7 +620,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         }
     }
     std::sort(far_ids.begin(), far_ids.end(), [&](int32_t x, int32_t y) {
-        const int32_t *a = &tree->blocks[5 * x], *b = &tree->blocks[5 * y];
+        const int32_t *a = &T->blocks[5 * x], *b = &T->blocks[5 * y];
         const int64_t sa = (int64_t)(a[1] - a[0]) * (a[3] - a[2]), sb = (int64_t)(b[1] - b[0]) * (b[3] - b[2]);
         return sa != sb ? sa > sb : x < y;
     });
@@ -626,7 +633,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         std::vector<double> cost;
         std::vector<int32_t> ks;
         if ((rc = dalloc(ctx, &dkpred, nb * Nu, &gk.p))) return fail(rc);
-        if ((rc = td_predict_kpred(cfg->model, tree, mesh, f, op->c, far_ids, kcap, dkpred, cost, ks))) return fail(rc);
+        if ((rc = td_predict_kpred(cfg->model, tree, T->blocks, mesh, f, op->c, far_ids, kcap, dkpred, cost, ks))) return fail(rc);
         std::vector<size_t> order(far_ids.size());
         for (size_t q = 0; q < order.size(); ++q) order[q] = q;
         std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
@@ -634,7 +641,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         pred_far_cap = 0;
         for (size_t q = 0; q < order.size(); ++q) {
             sorted[q] = far_ids[order[q]];
-            const int32_t *bl = &tree->blocks[5 * sorted[q]];
+            const int32_t *bl = &T->blocks[5 * sorted[q]];
             pred_far_cap += (int64_t)((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks[order[q]];
         }
         far_ids.swap(sorted);
@@ -655,7 +662,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     char *fib = nullptr;
     if ((rc = dalloc(ctx, &fib, es * nb * Nu * Nu, &T->owned))) return fail(rc);
     T->dfib = fib;
-    if ((rc = upload(ctx, T->dblocks, tree->blocks.data(), 5 * nb)) ||
+    if ((rc = upload(ctx, T->dblocks, T->blocks.data(), 5 * nb)) ||
         (rc = upload(ctx, T->dperm_r, tree->side[0].perm.data(), T->nrows)) ||
         (rc = upload(ctx, T->dperm_c, tree->side[1].perm.data(), T->ncols)) ||
         (rc = upload(ctx, T->dinv_r, inv_r.data(), T->nrows)) || (rc = upload(ctx, T->dinv_c, inv_c.data(), T->ncols)) ||
@@ -677,12 +684,11 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     int64_t *deprefix, *dnoff, *evals;
     unsigned int *counter;
     const int nctas_near = std::min<int64_t>(std::max<int64_t>(1, (int64_t)near_ids.size()), (int64_t)ctx->num_sms * 8);
-    const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
     const int nctas_far = std::min<int64_t>(std::max<int64_t>(1, (int64_t)far_ids.size()), (int64_t)ctx->num_sms * ctx->far_cps[pf]);
     // dense faces for far blocks up to dense_cap entries, within a scratch budget of 8 GB
     int64_t dense_cap = 0;
     for (int32_t b : far_ids) {
-        const int32_t *bl = &tree->blocks[5 * b];
+        const int32_t *bl = &T->blocks[5 * b];
         dense_cap = std::max<int64_t>(dense_cap, (int64_t)(bl[1] - bl[0]) * (bl[3] - bl[2]));
     }
     {
@@ -832,7 +838,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     st.nfar = (int64_t)far_ids.size();
     T->frank_sum.assign(nb, 0);
     for (int64_t b = 0; b < nb; ++b) {
-        const int32_t *bl = &tree->blocks[5 * b];
+        const int32_t *bl = &T->blocks[5 * b];
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         st.sum_rank += T->rank[b];
         st.max_rank = std::max<int64_t>(st.max_rank, T->rank[b]);
@@ -863,6 +869,13 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
 extern "C" int tdbem_tensor_stats(tdbem_tensor_t t, tdbem_stats *st) {
     if (!t || !st) return TDBEM_ERR_ARG;
     *st = t->stats;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_tensor_partition(tdbem_tensor_t t, int64_t *nb, int32_t *blocks) {
+    if (!t) return TDBEM_ERR_ARG;
+    if (nb) *nb = t->nblocks;
+    if (blocks) std::memcpy(blocks, t->blocks.data(), sizeof(int32_t) * 5 * t->nblocks);
     return TDBEM_OK;
 }
 
@@ -1149,7 +1162,7 @@ extern "C" int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op 
     if (capacity < *count) return td_fail(ctx, TDBEM_ERR_ARG, "capacity %lld < %lld samples", (long long)capacity, (long long)*count);
     if (*count == 0) return TDBEM_OK;
     std::vector<float> x;
-    td_block_features(tree, mesh, f, op->c, far_ids, x);
+    td_block_features(tree, tree->blocks, mesh, f, op->c, far_ids, x);
     if ((rc = upload(ctx, feats, x.data(), x.size()))) return rc;
     const int kcap = cfg->max_face_rank > 0 ? std::min(cfg->max_face_rank, 64) : 64;
     Guard g;

@@ -133,10 +133,15 @@ void td_mesh_adjacency(tdbem_mesh *m);
 int td_gauss01(int n, double *x, double *w);
 void td_rule7(double bary[7][3], double w[7]);
 
-// model.cu
+// planner.cpp: the tree's partition with far blocks above twice the mean far
+// work of one of nctas persistent CTAs split into their sons' blocks
+void td_balance_partition(const HostTree &R, const HostTree &C, const std::vector<int32_t> &blocks, int64_t nctas,
+                          std::vector<int32_t> &out);
+
+// model.cu (blocks: a partition of the tree's clusters, [nb][5])
 struct tdbem_model;
-void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
-                       const std::vector<int32_t> &far, std::vector<float> &x);
-int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
-                     const std::vector<int32_t> &far, int kcap, int32_t *dkpred, std::vector<double> &cost,
-                     std::vector<int32_t> &ks);
+void td_block_features(const tdbem_tree *t, const std::vector<int32_t> &blocks, const tdbem_mesh *m,
+                       const tdbem_freqs *f, double c, const std::vector<int32_t> &far, std::vector<float> &x);
+int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const std::vector<int32_t> &blocks, const tdbem_mesh *m,
+                     const tdbem_freqs *f, double c, const std::vector<int32_t> &far, int kcap, int32_t *dkpred,
+                     std::vector<double> &cost, std::vector<int32_t> &ks);

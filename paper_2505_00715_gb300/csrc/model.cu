@@ -79,8 +79,8 @@ double gap(const ClusterNode &a, const ClusterNode &b) {
 }  // namespace
 
 // Host features [far.size() * Nu][6] for the far blocks listed in `far`.
-void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
-                       const std::vector<int32_t> &far, std::vector<float> &x) {
+void td_block_features(const tdbem_tree *t, const std::vector<int32_t> &blocks, const tdbem_mesh *m,
+                       const tdbem_freqs *f, double c, const std::vector<int32_t> &far, std::vector<float> &x) {
     double h = 0.0;
     for (int64_t e = 0; e < m->nt; ++e)
         for (int k = 0; k < 3; ++k) {
@@ -91,7 +91,7 @@ void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_fre
     const int Nu = f->Nu;
     x.assign(far.size() * Nu * TD_MLP_NFEAT, 0.0f);
     for (size_t n = 0; n < far.size(); ++n) {
-        const int32_t *bl = &t->blocks[5 * far[n]];
+        const int32_t *bl = &blocks[5 * far[n]];
         const ClusterNode *A = find_node(t->side[0], bl[0], bl[1]), *B = find_node(t->side[1], bl[2], bl[3]);
         const double da = A ? diag(*A) : 0.0, db = B ? diag(*B) : 0.0;
         const double ds = (A && B) ? std::max(gap(*A, *B), 1e-300) : 1.0;
@@ -114,9 +114,9 @@ void td_block_features(const tdbem_tree *t, const tdbem_mesh *m, const tdbem_fre
 // ks = sum_u min(kp, kcap) (face-pool presizing).  The block features are
 // formed on the host (7652 blocks: a fraction of a millisecond), the
 // frequency features and the MLP on the device.
-int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const tdbem_mesh *m, const tdbem_freqs *f, double c,
-                     const std::vector<int32_t> &far, int kcap, int32_t *dkpred, std::vector<double> &cost,
-                     std::vector<int32_t> &ks) {
+int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const std::vector<int32_t> &blocks, const tdbem_mesh *m,
+                     const tdbem_freqs *f, double c, const std::vector<int32_t> &far, int kcap, int32_t *dkpred,
+                     std::vector<double> &cost, std::vector<int32_t> &ks) {
     tdbem_ctx *ctx = M->ctx;
     const int Nu = f->Nu;
     const int nfar = (int)far.size();
@@ -138,7 +138,7 @@ int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const tdbem_mesh *m, c
     int32_t *hfar = reinterpret_cast<int32_t *>(ff + (size_t)Nu * 2);
     int32_t *hlen = hfar + nfar;
     for (int q = 0; q < nfar; ++q) {
-        const int32_t *bl = &t->blocks[5 * far[q]];
+        const int32_t *bl = &blocks[5 * far[q]];
         const ClusterNode *A = find_node(t->side[0], bl[0], bl[1]), *B = find_node(t->side[1], bl[2], bl[3]);
         const double da = A ? diag(*A) : 0.0, db = B ? diag(*B) : 0.0;
         const double ds = (A && B) ? std::max(gap(*A, *B), 1e-300) : 1.0;

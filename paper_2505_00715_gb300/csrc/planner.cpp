@@ -303,3 +303,57 @@ void td_plan_blocks(const HostTree &rows, const HostTree &cols, double eta,
     blocks.clear();
     block_rec(rows, cols, 0, 0, eta, blocks);
 }
+
+// ---------------------------------------------------------------------------
+// Compression partition for the persistent far phase: far blocks whose
+// entry count exceeds twice the mean far work of one persistent CTA
+// (total far entries / nctas) are replaced by the blocks of their clusters'
+// sons (both sides where both have sons), recursively.  Sub-blocks of an
+// admissible block are admissible (smaller boxes, larger distance), so the
+// result is again an admissible partition; near blocks are kept.
+namespace {
+int node_of(const HostTree &t, int32_t b, int32_t e) {
+    int id = 0;
+    for (;;) {
+        const ClusterNode &n = t.nodes[id];
+        if (n.begin == b && n.end == e) return id;
+        if (n.son0 < 0) return -1;
+        id = (b < t.nodes[n.son0].end) ? n.son0 : n.son1;
+    }
+}
+
+void split_far(const HostTree &R, const HostTree &C, int a, int b, double lim, std::vector<int32_t> &out) {
+    const ClusterNode &x = R.nodes[a], &y = C.nodes[b];
+    const double e = (double)(x.end - x.begin) * (double)(y.end - y.begin);
+    const bool sx = x.son0 >= 0, sy = y.son0 >= 0;
+    if (e <= lim || (!sx && !sy)) {
+        const int32_t bl[5] = {x.begin, x.end, y.begin, y.end, 1};
+        out.insert(out.end(), bl, bl + 5);
+        return;
+    }
+    const int xs[2] = {sx ? x.son0 : a, sx ? x.son1 : -1};
+    const int ys[2] = {sy ? y.son0 : b, sy ? y.son1 : -1};
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 2; ++q)
+            if (xs[p] >= 0 && ys[q] >= 0) split_far(R, C, xs[p], ys[q], lim, out);
+}
+}  // namespace
+
+void td_balance_partition(const HostTree &R, const HostTree &C, const std::vector<int32_t> &blocks, int64_t nctas,
+                          std::vector<int32_t> &out) {
+    const size_t nb = blocks.size() / 5;
+    double tot = 0.0;
+    for (size_t b = 0; b < nb; ++b)
+        if (blocks[5 * b + 4]) tot += (double)(blocks[5 * b + 1] - blocks[5 * b]) * (double)(blocks[5 * b + 3] - blocks[5 * b + 2]);
+    const double lim = 2.0 * tot / (double)(nctas > 0 ? nctas : 1);
+    out.clear();
+    out.reserve(blocks.size());
+    for (size_t b = 0; b < nb; ++b) {
+        const int32_t *bl = &blocks[5 * b];
+        const int a = bl[4] ? node_of(R, bl[0], bl[1]) : -1, c = bl[4] ? node_of(C, bl[2], bl[3]) : -1;
+        if (a < 0 || c < 0)
+            out.insert(out.end(), bl, bl + 5);
+        else
+            split_far(R, C, a, c, lim, out);
+    }
+}

@@ -210,3 +210,49 @@ def test_autotune_keeps_results(td, ctx, orc, sphere2):
     y0 = X0.apply_weighted(W).cpu().numpy()
     y1 = X1.apply_weighted(W).cpu().numpy()
     assert np.linalg.norm(y1 - y0) <= 1e-5 * np.linalg.norm(y0)
+
+
+# ---------------------------------------------------------------- balanced partition
+@pytest.mark.parametrize("op", ["SLP", "DLP"])
+def test_balanced_partition_refines_tree(td, ctx, orc, op):
+    """The compression partition refines the tree's partition (every block
+    lies inside one tree block of the same kind, the blocks tile the matrix
+    once), splits the largest far blocks, and both partitions compress to
+    3 eps of the dense FP64 apply."""
+    import torch
+    V, T = icosphere(3)
+    gm, om = td.Mesh(ctx, V, T), orc.Mesh(V, T)
+    f = td.Freqs.bdf2(ctx, 64, 0.05)
+    cols = td.P0 if op == "SLP" else td.P1
+    tree = td.Tree(gm, td.P0, cols, 32, 2.0)
+    eps = 1e-4
+    Xb = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=td.MIXED)
+    Xt = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=td.MIXED, balance=False)
+    tb, pb, pt = np.asarray(tree.blocks), Xb.partition(), Xt.partition()
+    assert np.array_equal(pt, tb)
+    assert len(pb) > len(tb) and Xb.stats()["nblocks"] == len(pb)
+    nr, nc = Xb.nrows, Xb.ncols
+    label = np.full((nr, nc), -1, dtype=np.int64)
+    for q, (i0, i1, j0, j1, far) in enumerate(tb):
+        label[i0:i1, j0:j1] = q
+    cover = np.zeros((nr, nc), dtype=np.int32)
+    for i0, i1, j0, j1, far in pb:
+        cover[i0:i1, j0:j1] += 1
+        lab = np.unique(label[i0:i1, j0:j1])
+        assert len(lab) == 1 and tb[lab[0], 4] == far
+    assert np.all(cover == 1)
+    e_t = (tb[:, 1] - tb[:, 0]) * (tb[:, 3] - tb[:, 2])
+    e_b = (pb[:, 1] - pb[:, 0]) * (pb[:, 3] - pb[:, 2])
+    assert e_b[pb[:, 4] == 1].max() < e_t[tb[:, 4] == 1].max()
+    nrhs = 2
+    W = random_weights(64, nc, nrhs, seed=5)
+    Wt = torch.as_tensor(W, dtype=torch.complex64, device="cuda")
+    rows = np.sort(np.random.default_rng(2).choice(nr, 24, replace=False)).astype(np.int32)
+    orc_op = getattr(orc, op)
+    yd = om.dense_apply_rows(orc_op, f.s, rows, W, ng=5)
+    for X in (Xb, Xt):
+        y = X.apply_weighted(Wt).cpu().numpy()
+        err = np.linalg.norm(y[rows] - yd) / np.linalg.norm(yd)
+        print("%s %s partition: %d blocks, sampled apply error %.2e" % (op, "balanced" if X is Xb else "tree",
+                                                                       X.stats()["nblocks"], err))
+        assert err < 3 * eps, err
