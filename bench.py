@@ -5,6 +5,10 @@ Workload (default, the 5120-triangle configuration): icosphere R = 1 with
 convolution quadrature N = 64, dt = 0.05 (33 unique frequencies), PCA cluster
 tree with leaf size 32 and eta = 2, 3D-ACA at eps = 1e-4 (face ACA 1e-6),
 Sauter-Schwab with 5 Gauss points per variable; apply with 16 right-hand sides.
+Other workloads (--workload): the 1280-triangle sphere, the double layer on
+the 5120-triangle sphere, and finned machine housings of about 30k, 60k and
+80k triangles (c = 343 m/s, gCQ with 256 / 256 / 512 contour points, leaf
+64; 32 right-hand sides at 80k).
 
 One step = the whole path: block cluster tree, compression (touching-pair
 table, near-field entries, near and far 3D-ACA, one graph) and one
@@ -14,7 +18,7 @@ region; the e2e figure repeats the step through the host-buffer API (mesh
 upload, tree, compression, apply with host W and y).
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
-comparison) on a bounded sample of the same workload.
+comparison) on a bounded sample of the same workload (sphere workloads).
 """
 import argparse
 import json
@@ -30,16 +34,38 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from paper_2505_00715_gb300.inputs import icosphere, random_weights  # noqa: E402
+from paper_2505_00715_gb300.inputs import graded_steps, housing, icosphere, random_weights  # noqa: E402
 
 WORKLOADS = {
+    # icospheres (R = 1, c = 1) with BDF2 convolution quadrature
     "sphere1280_slp_bdf2_N64": dict(level=3, op="SLP", N=64, dt=0.05, leaf=32, eta=2.0, eps=1e-4, eps_aca=1e-6,
                                     ng=5, nrhs=16, c=1.0),
     "sphere5120_slp_bdf2_N64": dict(level=4, op="SLP", N=64, dt=0.05, leaf=32, eta=2.0, eps=1e-4, eps_aca=1e-6,
                                     ng=5, nrhs=16, c=1.0),
     "sphere5120_dlp_bdf2_N64": dict(level=4, op="DLP", N=64, dt=0.05, leaf=32, eta=2.0, eps=1e-4, eps_aca=1e-6,
                                     ng=5, nrhs=16, c=1.0),
+    # finned machine housings (c = 343 m/s) with the gCQ contour of 2-stage Radau
+    # IIA over geometrically graded steps (T = 0.015 s); 512 steps are graded so
+    # that dt_max / dt_min equals that of 256 steps of ratio 1.01
+    "housing30k_slp_gcq256": dict(housing=30000, op="SLP", gcq=(256, 1.01, 0.015), leaf=64, eta=2.0, eps=1e-4,
+                                  eps_aca=1e-6, ng=5, nrhs=16, c=343.0),
+    "housing60k_slp_gcq256": dict(housing=60000, op="SLP", gcq=(256, 1.01, 0.015), leaf=64, eta=2.0, eps=1e-4,
+                                  eps_aca=1e-6, ng=5, nrhs=16, c=343.0),
+    "housing80k_slp_gcq512": dict(housing=80000, op="SLP", gcq=(512, 1.01 ** (255.0 / 511.0), 0.015), leaf=64,
+                                  eta=2.0, eps=1e-4, eps_aca=1e-6, ng=5, nrhs=32, c=343.0),
 }
+
+
+def workload_mesh(cfg):
+    return housing(cfg["housing"], seed=0) if "housing" in cfg else icosphere(cfg["level"])
+
+
+def workload_freqs(td, ctx, cfg):
+    if "gcq" in cfg:
+        nq, ratio, T_end = cfg["gcq"]
+        dts = graded_steps(nq, ratio, T_end)
+        return td.Freqs.gcq(ctx, dts.min(), dts.max(), td.RADAU2, nq)
+    return td.Freqs.bdf2(ctx, cfg["N"], cfg["dt"])
 
 
 def job_throughput(local_ms_total, units_per_step, steps, world, dist=None):
@@ -131,6 +157,8 @@ def oracle_baseline(cfg, target_s=15.0, max_stride=None):
     """Oracle compression of every stride-th block of the workload, timed on
     the host cores; returns dense-equivalent entries/s of the sampled blocks."""
     import oracle as orc
+    if "level" not in cfg:
+        return None
     V, T = icosphere(cfg["level"])
     m = orc.Mesh(V, T)
     s = orc.freqs_bdf2(cfg["N"], cfg["dt"])
@@ -165,6 +193,10 @@ def run_reference(args, cfg, wl_name):
         return 0
     vals = []
     info = None
+    if "level" not in cfg:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on the sphere workloads only "
+                          "(its FP64 compression of the housing's largest blocks exceeds the run's time bound)"}))
+        return 0
     for k in range(args.warmup + args.steps):
         info = oracle_baseline(cfg, target_s=args.ref_seconds)
         if k >= args.warmup:
@@ -214,9 +246,10 @@ def main():
 
     ctx = td.Context(local)
     stream = ctx.stream
-    V, T = icosphere(cfg["level"])
+    V, T = workload_mesh(cfg)
     mesh = td.Mesh(ctx, V, T)
-    freqs = td.Freqs.bdf2(ctx, cfg["N"], cfg["dt"])
+    freqs = workload_freqs(td, ctx, cfg)
+    cfg = dict(cfg, Nu=freqs.Nu)
     op = getattr(td, cfg["op"])
     colb = td.P0 if cfg["op"] == "SLP" else td.P1
     nrows, ncols = mesh.ndof(td.P0), mesh.ndof(colb)
@@ -255,8 +288,13 @@ def main():
         return X, (e_apply0, e_apply1)
 
     def timed(n, prec=td.MIXED, Wd=W, yd=y, use_model=True):
+        # keeps the last step's tensor only (a housing tensor holds tens of GB)
         out = []
-        for _ in range(n):
+        X = None
+        for i in range(n):
+            if out:
+                out[-1] = out[-1][:3] + (None,)
+            X = None
             flush.fill_(1.0)
             torch.cuda.synchronize()
             if dist:
@@ -282,12 +320,15 @@ def main():
     value, total_ms = job_throughput(sum(ms), represented, args.steps, world, dist)
     blocks = X.partition()
     apply_gflops = apply_flops(X, blocks, NQ, nrhs) / (apply_ms / 1e3) / 1e9
+    X = None
+    res = [r[:3] for r in res]
 
     # same step without the predictor, and the plain FP64 GPU form
     r_np = timed(2, use_model=False)
     no_pred = {"step_ms": statistics.median([r[0] for r in r_np]),
                "time_to_tensor_s": statistics.median([r[2]["ms_total"] for r in r_np]) / 1e3,
                "phase_ms": {k: r_np[-1][2][k] for k in ("ms_plan", "ms_singular", "ms_near", "ms_far")}}
+    del r_np
     fp64 = None
     if not args.no_fp64:
         W64 = torch.as_tensor(W_host, dtype=torch.complex128, device=dev)
@@ -301,7 +342,7 @@ def main():
                 "entries_per_s": represented / (r64[0][0] / 1e3),
                 "phase_ms": {k: s64[k] for k in ("ms_plan", "ms_singular", "ms_near", "ms_far")},
                 "sum_rank": s64["sum_rank"], "stored_complex": s64["stored_complex"]}
-        del X64, W64, y64
+        del X64, W64, y64, r64
 
     # e2e through the host-buffer API
     yh = torch.empty((nrows, nrhs), dtype=torch.complex64).pin_memory()
@@ -326,7 +367,7 @@ def main():
 
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
-    roof = roofline(st, X, cfg, blocks, peaks, peak_kind, clocks, args.workload)
+    roof = roofline(st, cfg, blocks, peaks, peak_kind, clocks, args.workload)
     if rank == 0:
         line = {
             "metric": "entries/s", "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
@@ -372,10 +413,10 @@ def train_predictor(td, ctx, cfg, dev):
     for lev, leaf in ((2, 16), (3, 32)):
         V, T = icosphere(lev)
         m = td.Mesh(ctx, V, T)
-        f = td.Freqs.bdf2(ctx, cfg["N"], cfg["dt"])
+        f = td.Freqs.bdf2(ctx, 64, 0.05)
         for op, cb in ((td.SLP, td.P0), (td.DLP, td.P1)):
-            tr = td.Tree(m, td.P0, cb, leaf, cfg["eta"])
-            x, r = td.harvest(m, op, f, tr, eps_aca=cfg["eps_aca"], c=cfg["c"], ng=cfg["ng"])
+            tr = td.Tree(m, td.P0, cb, leaf, 2.0)
+            x, r = td.harvest(m, op, f, tr, eps_aca=1e-6, c=1.0, ng=5)
             xs.append(x)
             ys.append(torch.as_tensor(np.searchsorted(BIN_EDGES, r.cpu().numpy()).astype(np.int32), device=dev))
     x = torch.cat(xs)
@@ -384,9 +425,9 @@ def train_predictor(td, ctx, cfg, dev):
     loss = model.train(x, y, epochs=30, batch=2048, lr=3e-3, seed=3)
     t_train = time.perf_counter() - t0
     # accuracy on the benchmark workload itself (unseen mesh size)
-    V, T = icosphere(cfg["level"])
+    V, T = workload_mesh(cfg)
     m = td.Mesh(ctx, V, T)
-    f = td.Freqs.bdf2(ctx, cfg["N"], cfg["dt"])
+    f = workload_freqs(td, ctx, cfg)
     tr = td.Tree(m, td.P0, td.P0 if cfg["op"] == "SLP" else td.P1, cfg["leaf"], cfg["eta"])
     op = getattr(td, cfg["op"])
     xw, rw = td.harvest(m, op, f, tr, eps_aca=cfg["eps_aca"], c=cfg["c"], ng=cfg["ng"])
@@ -429,7 +470,7 @@ def far_traffic(workload):
     return FAR_TRAFFIC["bytes"] if h.hexdigest()[:16] == FAR_TRAFFIC["sha256_16"] else None
 
 
-def roofline(st, X, cfg, blocks, peaks, peak_kind, clocks, workload=None):
+def roofline(st, cfg, blocks, peaks, peak_kind, clocks, workload=None):
     """Dominant phase of the compression against its ALU roofline.
 
     Far-field 3D-ACA kernel: its algorithmic work is the entry generation,
@@ -444,7 +485,7 @@ def roofline(st, X, cfg, blocks, peaks, peak_kind, clocks, workload=None):
     sfu_peak = 16.0 * 152 * clock_mhz * 1e6 / 1e12  # T SFU-ops/s
     nI = (blocks[:, 1] - blocks[:, 0]).astype(np.int64)
     nJ = (blocks[:, 3] - blocks[:, 2]).astype(np.int64)
-    near_entries = int(np.sum((nI * nJ)[blocks[:, 4] == 0])) * int(cfg["N"] // 2 + 1)
+    near_entries = int(np.sum((nI * nJ)[blocks[:, 4] == 0])) * int(cfg["Nu"])
     pairs_per_entry = 49 if cfg["op"] == "SLP" else 49 * 6
     far_pairs = (st["entries_regular"] - near_entries + st["entries_tube"]) * pairs_per_entry
     achieved_far = far_pairs * 4.0 / (st["ms_far"] / 1e3) / 1e12

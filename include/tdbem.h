@@ -101,6 +101,8 @@ typedef struct {
     int64_t entries_tube;           /* fibre (all-frequency) entries evaluated */
     int64_t pairs_singular;         /* touching pairs integrated (per frequency) */
     double ms_plan, ms_singular, ms_near, ms_far, ms_total;
+    int64_t pool_growths;           /* face pool grown during compression: far blocks redone
+                                       (or all phases rerun after a near-field overflow) */
 } tdbem_stats;
 
 /* ---- context -------------------------------------------------------------- */
@@ -112,6 +114,17 @@ const char *tdbem_last_error(tdbem_ctx_t ctx);
 /* Block until all work of the context's stream has finished; TDBEM_ERR_CUDA
  * if a tensor-core wait of an earlier asynchronous call gave up. */
 int tdbem_ctx_sync(tdbem_ctx_t ctx);
+/* Size in bytes of the buffer in which tdbem_compress forms and compresses
+ * the near-field tensor, batch by batch of near blocks (default 16 GiB; a
+ * block larger than the buffer forms a batch of its own).  TDBEM_ERR_ARG if
+ * bytes <= 0. */
+int tdbem_ctx_set_near_batch(tdbem_ctx_t ctx, int64_t bytes);
+/* Scale (> 0, default 1) of the far-field part of the first face-pool size
+ * of tdbem_compress (estimated from the far blocks' sizes or the predicted
+ * ranks).  A pool that fills up grows, keeping its contents, and the far
+ * blocks it stopped are redone (tdbem_stats.pool_growths counts this).
+ * TDBEM_ERR_ARG if scale <= 0. */
+int tdbem_ctx_set_pool_scale(tdbem_ctx_t ctx, double scale);
 
 /* ---- mesh (Sec. 3 eq. geomapprox, spaces X_D = P1, X_N = P0) -------------- */
 /* verts: host [nv][3] FP64; tris: host [nt][3] int32.  Builds the element

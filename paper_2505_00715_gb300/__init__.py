@@ -60,6 +60,14 @@ class Context:
     def sync(self):
         self.check(self.L.tdbem_ctx_sync(self.h), "tdbem_ctx_sync")
 
+    def set_pool_scale(self, scale):
+        """Scale of the far part of the first face-pool size in compress."""
+        self.check(self.L.tdbem_ctx_set_pool_scale(self.h, float(scale)), "tdbem_ctx_set_pool_scale")
+
+    def set_near_batch(self, nbytes):
+        """Buffer size (bytes) of the batched near-field tensor in compress."""
+        self.check(self.L.tdbem_ctx_set_near_batch(self.h, int(nbytes)), "tdbem_ctx_set_near_batch")
+
     def __del__(self):
         if getattr(self, "h", None) and _lib._lib is not None:
             _lib._lib.tdbem_ctx_destroy(self.h)

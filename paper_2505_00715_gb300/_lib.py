@@ -38,7 +38,8 @@ class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("nblocks", "nnear", "nfar", "sum_rank", "max_rank", "sum_face_rank",
                                          "stored_complex", "dense_complex", "entries_regular", "entries_tube",
                                          "pairs_singular")] + \
-               [(n, C.c_double) for n in ("ms_plan", "ms_singular", "ms_near", "ms_far", "ms_total")]
+               [(n, C.c_double) for n in ("ms_plan", "ms_singular", "ms_near", "ms_far", "ms_total")] + \
+               [("pool_growths", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -51,6 +52,8 @@ EXPORTS = {
     "tdbem_ctx_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_last_error": (C.c_char_p, [C.c_void_p]),
     "tdbem_ctx_sync": (C.c_int, [C.c_void_p]),
+    "tdbem_ctx_set_near_batch": (C.c_int, [C.c_void_p, C.c_int64]),
+    "tdbem_ctx_set_pool_scale": (C.c_int, [C.c_void_p, C.c_double]),
     "tdbem_mesh_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.POINTER(C.c_void_p)]),
     "tdbem_mesh_destroy": (C.c_int, [C.c_void_p]),

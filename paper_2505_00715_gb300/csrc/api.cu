@@ -55,12 +55,18 @@ int upload(tdbem_ctx *ctx, T *dst, const T *src, size_t count) {
     return TDBEM_OK;
 }
 
+// terms of Algorithm 1 per far block assumed when the face pool is presized
+// from predicted face ranks (the blocks of the benchmark meshes take 5-16)
+constexpr int64_t kTermsEst = 12;
+
 struct Guard {
-    // frees transient device buffers at scope exit
+    // frees transient device buffers at scope exit (or earlier, by release())
     std::vector<void *> p;
-    ~Guard() {
+    void release() {
         for (void *q : p) cudaFree(q);
+        p.clear();
     }
+    ~Guard() { release(); }
 };
 
 MeshDev mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw,
@@ -191,6 +197,20 @@ extern "C" int tdbem_ctx_destroy(tdbem_ctx_t ctx) {
 }
 
 extern "C" const char *tdbem_last_error(tdbem_ctx_t ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+extern "C" int tdbem_ctx_set_near_batch(tdbem_ctx_t ctx, int64_t bytes) {
+    if (!ctx) return TDBEM_ERR_ARG;
+    if (bytes <= 0) return td_fail(ctx, TDBEM_ERR_ARG, "near batch size must be > 0");
+    ctx->near_batch_bytes = bytes;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_ctx_set_pool_scale(tdbem_ctx_t ctx, double scale) {
+    if (!ctx) return TDBEM_ERR_ARG;
+    if (!(scale > 0.0)) return td_fail(ctx, TDBEM_ERR_ARG, "pool scale must be > 0");
+    ctx->pool_scale = scale;
+    return TDBEM_OK;
+}
 
 extern "C" int tdbem_ctx_sync(tdbem_ctx_t ctx) {
     if (!ctx) return TDBEM_ERR_ARG;
@@ -619,6 +639,40 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
             max_near_rows = std::max(max_near_rows, nI);
         }
     }
+    // The near tensor [Nu][nI][nJ] per near block is formed and compressed in
+    // batches of consecutive near blocks of at most ctx->near_batch_bytes (one
+    // batch when it fits); every batch reuses one buffer.  eprefix / noff
+    // become offsets within the batch.
+    std::vector<int> nbatch(1, 0);
+    std::vector<int64_t> batch_nent;
+    int64_t max_batch_tens = 1;
+    {
+        const int64_t budget = std::max<int64_t>(1, ctx->near_batch_bytes / (int64_t)es);
+        const int nn = (int)near_ids.size();
+        int64_t acc = 0;
+        for (int q = 0; q < nn; ++q) {
+            const int64_t next_e = q + 1 < nn ? eprefix[q + 1] : nent;
+            const int64_t sz = (next_e - eprefix[q]) * Nu;
+            if (acc > 0 && acc + sz > budget) {
+                nbatch.push_back(q);
+                acc = 0;
+            }
+            acc += sz;
+        }
+        nbatch.push_back(nn);
+        for (size_t bt = 0; bt + 1 < nbatch.size(); ++bt) {
+            const int q0 = nbatch[bt], q1 = nbatch[bt + 1];
+            if (q0 >= q1) continue;
+            const int64_t e0 = eprefix[q0], t0b = noff[q0];
+            const int64_t e1 = q1 < nn ? eprefix[q1] : nent, t1b = q1 < nn ? noff[q1] : ntens;
+            batch_nent.push_back(e1 - e0);
+            max_batch_tens = std::max(max_batch_tens, t1b - t0b);
+            for (int q = q0; q < q1; ++q) {
+                eprefix[q] -= e0;
+                noff[q] -= t0b;
+            }
+        }
+    }
     std::sort(far_ids.begin(), far_ids.end(), [&](int32_t x, int32_t y) {
         const int32_t *a = &T->blocks[5 * x], *b = &T->blocks[5 * y];
         const int64_t sa = (int64_t)(a[1] - a[0]) * (a[3] - a[2]), sb = (int64_t)(b[1] - b[0]) * (b[3] - b[2]);
@@ -642,7 +696,9 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         for (size_t q = 0; q < order.size(); ++q) {
             sorted[q] = far_ids[order[q]];
             const int32_t *bl = &T->blocks[5 * sorted[q]];
-            pred_far_cap += (int64_t)((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks[order[q]];
+            // about kTermsEst terms of Algorithm 1 per block, each with a face
+            // rank of at most the largest predicted one
+            pred_far_cap += (int64_t)((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks[order[q]] * kTermsEst;
         }
         far_ids.swap(sorted);
     }
@@ -680,7 +736,8 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     }
     c64 *table;
     char *nearbuf, *scr_near, *scr_far;
-    int32_t *dnear_ids, *dfar_ids, *flags;
+    int32_t *dnear_ids, *dfar_ids, *flags, *redo_a, *redo_b;
+    unsigned int *redo_count;
     int64_t *deprefix, *dnoff, *evals;
     unsigned int *counter;
     const int nctas_near = std::min<int64_t>(std::max<int64_t>(1, (int64_t)near_ids.size()), (int64_t)ctx->num_sms * 8);
@@ -699,12 +756,14 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     }
     const int64_t sper_far = (int64_t)kcap * (maxI + maxJ) + (int64_t)(Nu + 1) * dense_cap;
     if ((rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size())) ||
-        (rc = dalloc(ctx, &table, (size_t)npairs * Nu * 3, &g.p)) || (rc = dalloc(ctx, &nearbuf, es * ntens, &g.p)) ||
+        (rc = dalloc(ctx, &table, (size_t)npairs * Nu * 3, &g.p)) || (rc = dalloc(ctx, &nearbuf, es * max_batch_tens, &g.p)) ||
         (rc = dalloc(ctx, &scr_near, es * maxIJ * nctas_near, &g.p)) ||
         (rc = dalloc(ctx, &scr_far, es * sper_far * nctas_far, &g.p)) ||
         (rc = dalloc(ctx, &dnear_ids, near_ids.size(), &g.p)) || (rc = dalloc(ctx, &dfar_ids, far_ids.size(), &g.p)) ||
         (rc = dalloc(ctx, &deprefix, eprefix.size(), &g.p)) || (rc = dalloc(ctx, &dnoff, noff.size(), &g.p)) ||
-        (rc = dalloc(ctx, &flags, 4, &g.p)) || (rc = dalloc(ctx, &evals, 4, &g.p)) || (rc = dalloc(ctx, &counter, 4, &g.p)))
+        (rc = dalloc(ctx, &flags, 4, &g.p)) || (rc = dalloc(ctx, &evals, 4, &g.p)) || (rc = dalloc(ctx, &counter, 4, &g.p)) ||
+        (rc = dalloc(ctx, &redo_a, far_ids.size(), &g.p)) || (rc = dalloc(ctx, &redo_b, far_ids.size(), &g.p)) ||
+        (rc = dalloc(ctx, &redo_count, 4, &g.p)))
         return fail(rc);
     if ((rc = upload(ctx, dnear_ids, near_ids.data(), near_ids.size())) ||
         (rc = upload(ctx, dfar_ids, far_ids.data(), far_ids.size())) ||
@@ -739,15 +798,35 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     fa.dense_cap = dense_cap;
     fa.counter = counter;
     fa.evals = evals;
+    fa.redo = redo_a;
+    fa.redo_count = redo_count;
     const double t_plan = now_ms();
     // face pool: every near term fits (r <= Nu), far terms get a generous
     // estimate; on overflow the far phase is rerun with a larger pool.
-    int64_t cap = ntens + (pred_far_cap >= 0 ? pred_far_cap + pred_far_cap / 4 : sum_far_len * 256) + 1024;
+    // face pool: near terms reserved for min(Nu, max(16, Nu / 4)) terms per
+    // near block, far terms from the predicted ranks or a generous estimate;
+    // on overflow the phases are rerun with a pool twice as large.
+    const int64_t near_res = nent * std::min<int64_t>(Nu, std::max<int64_t>(16, Nu / 4));
+    // need: the size the attempt must have; cap: the size it asks for first
+    // (more where the device has room: the pool is trimmed after the phases)
+    auto device_room = [&]() {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) cudaGetLastError();
+        return std::max<int64_t>(0, ((int64_t)(0.85 * (double)fr) - ((int64_t)2 << 30)) / (int64_t)es);
+    };
+    const double far_est = (double)(pred_far_cap >= 0 ? pred_far_cap + pred_far_cap / 4 : sum_far_len * 256);
+    // an estimate beyond the device's room starts from the room (a pool that
+    // fills up grows where it can)
+    int64_t need = std::min(near_res + (int64_t)(ctx->pool_scale * far_est) + 1024,
+                            std::max<int64_t>(near_res + 1024, device_room()));
+    int64_t cap = std::max(need, std::min(2 * need, device_room()));
     if (dkpred) fa.kpred = dkpred;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) cudaEventCreate(&ev[k]);
     int hflags = 0;
     long long hev[2] = {0, 0};
+    float ms_redo = 0.0f;  // far blocks redone after the pool grew
+    int st_redo = 0;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if (T->dface) {
             cudaFree(T->dface);
@@ -755,7 +834,8 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
             T->dface = nullptr;
         }
         char *face = nullptr;
-        if ((rc = dalloc(ctx, &face, es * cap, &T->owned))) {
+        while ((rc = dalloc(ctx, &face, es * cap, &T->owned)) && cap > need) cap = std::max(need, cap - cap / 4);
+        if (rc) {
             for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
             return fail(rc);
         }
@@ -782,12 +862,27 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                 cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ls);
                 cudaMemsetAsync(evals, 0, sizeof(int64_t) * 4, ls);
                 cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ls);
+                cudaMemsetAsync(redo_count, 0, sizeof(unsigned int) * 4, ls);
                 cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ls);
                 lrc |= td_launch_sing_table(ls, md, op->op, op->prec, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
-            } else if (ph == 1) {
-                lrc |= td_launch_near_entries(ls, md, op->op, op->prec, na, table, ctx->num_sms);
-            } else if (ph == 2) {
-                lrc |= td_launch_near_aca(ls, op->prec, na, o, ap, scr_near, maxIJ, nctas_near);
+            } else if (ph == 1 || ph == 2) {
+                // one batch: entries (phase 1) and 3D-ACA (phase 2); several: both per
+                // batch in phase 1
+                const int nbt = (int)batch_nent.size();
+                for (int bt = 0; bt < nbt; ++bt) {
+                    NearArgs nab = na;
+                    const int q0 = nbatch[bt];
+                    nab.nnear = nbatch[bt + 1] - q0;
+                    nab.near_ids = dnear_ids + q0;
+                    nab.eprefix = deprefix + q0;
+                    nab.noff = dnoff + q0;
+                    nab.nentries = batch_nent[bt];
+                    const int nct = std::min(nctas_near, nab.nnear);
+                    if (ph == 1)
+                        lrc |= td_launch_near_entries(ls, md, op->op, op->prec, nab, table, ctx->num_sms);
+                    if ((ph == 2 && nbt == 1) || (ph == 1 && nbt > 1))
+                        lrc |= td_launch_near_aca(ls, op->prec, nab, o, ap, scr_near, maxIJ, nct);
+                }
             } else {
                 lrc |= td_launch_far_aca(ls, md, op->op, op->prec, fa, o, ap, nctas_far, ctx->far_nt[pf]);
             }
@@ -811,11 +906,84 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
             return fail(td_fail(ctx, TDBEM_ERR_CUDA, "compression kernels failed: %s", cudaGetErrorString(se)));
         }
         cudaMemcpy(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost);
+        // far blocks stopped by a full pool (and no near block): grow the pool
+        // keeping its contents, and redo only those blocks
+        int32_t *rec = fa.redo, *nxt = fa.redo == redo_a ? redo_b : redo_a;  // records of the last launch / next
+        for (int round = 0; round < 4 && !(hflags & TD_DEV_POOL_OVERFLOW) && (hflags & TD_DEV_FAR_OVERFLOW);
+             ++round) {
+            unsigned int nredo = 0;
+            cudaMemcpy(&nredo, redo_count, sizeof nredo, cudaMemcpyDeviceToHost);
+            // the old pool is held during the copy: grow within the room left
+            const int64_t room = device_room();
+            int64_t gneed = std::min(2 * cap, room), gcap = std::max(gneed, room);
+            if (gneed <= cap) {
+                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+                return fail(td_fail(ctx, TDBEM_ERR_OOM, "face pool full and no device memory left to grow it"));
+            }
+            char *bigger = nullptr;
+            int grc;
+            while ((grc = dalloc(ctx, &bigger, es * gcap)) && gcap > gneed) gcap = std::max(gneed, gcap - gcap / 4);
+            if (grc) {
+                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+                return fail(grc);
+            }
+            // every stored face lies below the old capacity
+            const int64_t used = cap;
+            if (cudaMemcpy(bigger, T->dface, es * cap, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+                cudaMemcpy(T->dface_used, &used, sizeof used, cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaFree(bigger);
+                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+                return fail(td_fail(ctx, TDBEM_ERR_CUDA, "growing the face pool failed"));
+            }
+            cudaFree(T->dface);
+            *std::find(T->owned.begin(), T->owned.end(), T->dface) = bigger;
+            T->dface = bigger;
+            T->face_cap = cap = gcap;
+            cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ctx->stream);
+            cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ctx->stream);
+            cudaMemsetAsync(redo_count, 0, sizeof(unsigned int) * 4, ctx->stream);
+            FarArgs fr = fa;
+            fr.nfar = (int)nredo;
+            fr.far_ids = rec;
+            fr.redo = nxt;
+            TensorOut o2 = tensor_out(T, flags);
+            cudaEvent_t r0, r1;
+            cudaEventCreate(&r0);
+            cudaEventCreate(&r1);
+            cudaEventRecord(r0, ctx->stream);
+            const int lr = td_launch_far_aca(ctx->stream, md, op->op, op->prec, fr, o2, ap,
+                                             std::min<int>(nctas_far, (int)nredo), ctx->far_nt[pf]);
+            cudaEventRecord(r1, ctx->stream);
+            const cudaError_t re = cudaStreamSynchronize(ctx->stream);
+            float mr = 0.0f;
+            if (cudaEventElapsedTime(&mr, r0, r1) == cudaSuccess) ms_redo += mr;
+            cudaEventDestroy(r0);
+            cudaEventDestroy(r1);
+            if (lr || re != cudaSuccess) {
+                for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+                return fail(td_fail(ctx, TDBEM_ERR_CUDA, "far-field redo failed: %s", cudaGetErrorString(re)));
+            }
+            cudaMemcpy(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost);
+            std::swap(rec, nxt);
+            ++st_redo;
+        }
         cudaMemcpy(hev, evals, sizeof hev, cudaMemcpyDeviceToHost);
-        if (!(hflags & TD_DEV_POOL_OVERFLOW)) break;
-        cap *= 2;
+        if (!(hflags & (TD_DEV_POOL_OVERFLOW | TD_DEV_FAR_OVERFLOW))) break;
+        // grow to twice the pool or to the device memory left (less a reserve
+        // for the apply plan), whichever is larger; the pool is trimmed below
+        cudaFree(T->dface);
+        T->owned.erase(std::find(T->owned.begin(), T->owned.end(), T->dface));
+        T->dface = nullptr;
+        const int64_t room = device_room();
+        if (std::min(2 * cap, room) <= cap) {
+            for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+            return fail(td_fail(ctx, TDBEM_ERR_OOM, "face pool full and no device memory left to grow it"));
+        }
+        need = std::min(2 * cap, room);
+        cap = std::max(need, room);
+        ++st_redo;
     }
-    if (hflags & TD_DEV_POOL_OVERFLOW) {
+    if (hflags & (TD_DEV_POOL_OVERFLOW | TD_DEV_FAR_OVERFLOW)) {
         for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
         return fail(td_fail(ctx, TDBEM_ERR_CAPACITY, "face pool overflow after retries"));
     }
@@ -826,6 +994,30 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
             ms[k] = -1.0f;
         }
     for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    // trim the face pool to the stored faces when more than 4 GB would stay
+    // unused (after the transient buffers are returned)
+    g.release();
+    gk.release();
+    {
+        int64_t used = 0;
+        if (cudaMemcpy(&used, T->dface_used, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(td_fail(ctx, TDBEM_ERR_CUDA, "reading the face pool size failed"));
+        if ((T->face_cap - used) * (int64_t)es > ((int64_t)4 << 30)) {
+            char *tight = nullptr;
+            if (cudaMalloc((void **)&tight, es * std::max<int64_t>(used, 1)) == cudaSuccess) {
+                if (used > 0 && cudaMemcpy(tight, T->dface, es * used, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+                    cudaFree(tight);
+                    return fail(td_fail(ctx, TDBEM_ERR_CUDA, "trimming the face pool failed"));
+                }
+                cudaFree(T->dface);
+                *std::find(T->owned.begin(), T->owned.end(), T->dface) = tight;
+                T->dface = tight;
+                T->face_cap = std::max<int64_t>(used, 1);
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
     // ---- host copies of the per-block results and statistics
     T->rank.resize(nb);
     std::vector<int32_t> frank(nb * Nu);
@@ -858,7 +1050,8 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     st.ms_plan = t_plan - t0;
     st.ms_singular = ms[0];
     st.ms_near = ms[1] + ms[2];
-    st.ms_far = ms[3];
+    st.ms_far = ms[3] + ms_redo;
+    st.pool_growths = st_redo;
     st.ms_total = now_ms() - t0;
     if (hflags & TD_DEV_RANK_CAP)
         td_fail(ctx, TDBEM_OK, "note: some far faces reached the rank cap %d", kcap);

@@ -154,4 +154,5 @@ template <class T> struct DotAcc {
 };
 
 // Device-side error word: kernels record a code and keep going safely.
-enum { TD_DEV_OK = 0, TD_DEV_POOL_OVERFLOW = 1, TD_DEV_BAD_INDEX = 2, TD_DEV_RANK_CAP = 4, TD_DEV_TIMEOUT = 8 };
+enum { TD_DEV_OK = 0, TD_DEV_POOL_OVERFLOW = 1, TD_DEV_BAD_INDEX = 2, TD_DEV_RANK_CAP = 4, TD_DEV_TIMEOUT = 8,
+       TD_DEV_FAR_OVERFLOW = 16 };

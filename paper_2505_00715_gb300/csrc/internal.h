@@ -16,6 +16,8 @@ struct tdbem_ctx {
     // threads per CTA and CTAs per SM (set by tdbem_autotune)
     int far_nt[2] = {128, 128};
     int far_cps[2] = {4, 5};
+    int64_t near_batch_bytes = (int64_t)16 << 30;  // buffer of the batched near-field tensor
+    double pool_scale = 1.0;                       // far part of the first face-pool size
     std::string err;
     int num_sms = 0;
     int *dflags = nullptr;  // device status word of asynchronous kernels (TD_DEV_* bits)

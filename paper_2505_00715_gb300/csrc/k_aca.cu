@@ -1098,7 +1098,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             if (tid == 0) {
                 unsigned long long off = atomicAdd(o.face_used, (unsigned long long)need);
                 if ((int64_t)(off + need) > o.face_cap) {
-                    atomicOr(o.dev_flags, TD_DEV_POOL_OVERFLOW);
+                    // the block is recorded and redone once the pool has grown
+                    atomicOr(o.dev_flags, a.redo ? TD_DEV_FAR_OVERFLOW : TD_DEV_POOL_OVERFLOW);
+                    if (a.redo) a.redo[atomicAdd(a.redo_count, 1u)] = b;
                     S.off = -1;
                 } else {
                     S.off = (long long)off;

@@ -56,6 +56,8 @@ struct FarArgs {
     int *harvest;           // non-null: record face-ACA ranks per (far block, frequency), [nfar][Nu]
     const int *kpred;       // nullable: predicted face rank per (block id, frequency) [nb][Nu]
     int64_t dense_cap;      // largest |I||J| handled with dense faces (0: none)
+    int *redo;              // nullable: ids of blocks stopped by a full face pool [nfar]
+    unsigned int *redo_count;
 };
 
 int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,

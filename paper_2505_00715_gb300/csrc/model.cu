@@ -111,7 +111,7 @@ void td_block_features(const tdbem_tree *t, const std::vector<int32_t> &blocks, 
 // Predicted first trip counts per (block id, unique frequency) for the far
 // blocks, written to the device array dkpred [nb][Nu] (entries of other
 // blocks untouched); per far block the predicted cost len * sum kp^2 and
-// ks = sum_u min(kp, kcap) (face-pool presizing).  The block features are
+// ks = max_u min(kp, kcap) (face-pool presizing).  The block features are
 // formed on the host (7652 blocks: a fraction of a millisecond), the
 // frequency features and the MLP on the device.
 int td_predict_kpred(tdbem_model *M, const tdbem_tree *t, const std::vector<int32_t> &blocks, const tdbem_mesh *m,

@@ -218,8 +218,10 @@ int gmres(tdbem_tensor *t, int fidx, const cx<T> *b, int n, cx<T> *x, double tol
         }
         if (rc) break;
     }
-    if (!rc) {
-        // explicit final residual
+    if (!rc && !done) {
+        // explicit final residual (when the loop ended by the true residual
+        // test, res holds the explicit residuals of the final x already; a
+        // second product would differ from it by the rounding of the apply)
         if (!(rc = tdbem_apply_freq(t, fidx, x, n, w))) {
             cudaMemcpyAsync(r, b, sizeof(cx<T>) * M * n, cudaMemcpyDeviceToDevice, ctx->stream);
             if (!(rc = ops.axpby(r, w, mone, 1.0)) && !(rc = ops.dot(r, r, tmp)))

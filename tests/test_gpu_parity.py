@@ -256,3 +256,57 @@ def test_balanced_partition_refines_tree(td, ctx, orc, op):
         print("%s %s partition: %d blocks, sampled apply error %.2e" % (op, "balanced" if X is Xb else "tree",
                                                                        X.stats()["nblocks"], err))
         assert err < 3 * eps, err
+
+
+def test_near_batches_give_the_same_tensor(td, ctx):
+    """Forming and compressing the near-field tensor in several batches of
+    near blocks (a small batch buffer) gives the same blocks and entries as
+    one batch."""
+    import torch
+    V, T = icosphere(3)
+    gm = td.Mesh(ctx, V, T)
+    f = td.Freqs.bdf2(ctx, 64, 0.05)
+    tree = td.Tree(gm, td.P0, td.P0, 32, 2.0)
+    X1 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
+    ctx.set_near_batch(8 << 20)
+    try:
+        X2 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
+    finally:
+        ctx.set_near_batch(16 << 30)
+    with pytest.raises(td.TdbemError):
+        ctx.set_near_batch(0)
+    for a, b in zip(X1.blocks(), X2.blocks()):
+        assert np.array_equal(a, b)
+    s1, s2 = X1.stats(), X2.stats()
+    assert s1["stored_complex"] == s2["stored_complex"] and s1["entries_regular"] == s2["entries_regular"]
+    rng = np.random.default_rng(9)
+    rows, cols, fid = rng.integers(0, len(T), 4000), rng.integers(0, len(T), 4000), rng.integers(0, 64, 4000)
+    assert torch.equal(X1.entries(rows, cols, fid), X2.entries(rows, cols, fid))
+
+
+def test_face_pool_growth_redoes_far_blocks(td, ctx):
+    """A first face pool far too small: the pool grows (keeping the stored
+    faces), the far blocks it stopped are redone, and the tensor equals the
+    one compressed with a large enough pool."""
+    import torch
+    V, T = icosphere(3)
+    gm = td.Mesh(ctx, V, T)
+    f = td.Freqs.bdf2(ctx, 64, 0.05)
+    tree = td.Tree(gm, td.P0, td.P0, 32, 2.0)
+    X1 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
+    assert X1.stats()["pool_growths"] == 0
+    ctx.set_pool_scale(1e-3)
+    try:
+        X2 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
+    finally:
+        ctx.set_pool_scale(1.0)
+    with pytest.raises(td.TdbemError):
+        ctx.set_pool_scale(0.0)
+    s1, s2 = X1.stats(), X2.stats()
+    assert s2["pool_growths"] >= 1
+    for a, b in zip(X1.blocks(), X2.blocks()):
+        assert np.array_equal(a, b)
+    assert s1["stored_complex"] == s2["stored_complex"]
+    rng = np.random.default_rng(10)
+    rows, cols, fid = rng.integers(0, len(T), 4000), rng.integers(0, len(T), 4000), rng.integers(0, 64, 4000)
+    assert torch.equal(X1.entries(rows, cols, fid), X2.entries(rows, cols, fid))
