@@ -103,6 +103,7 @@ typedef struct {
     double ms_plan, ms_singular, ms_near, ms_far, ms_total;
     int64_t pool_growths;           /* face pool grown during compression: far blocks redone
                                        (or all phases rerun after a near-field overflow) */
+    int64_t launches;               /* kernel launches of the compression */
 } tdbem_stats;
 
 /* ---- context -------------------------------------------------------------- */

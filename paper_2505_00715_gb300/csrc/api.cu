@@ -827,6 +827,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     long long hev[2] = {0, 0};
     float ms_redo = 0.0f;  // far blocks redone after the pool grew
     int st_redo = 0;
+    int64_t nlaunch = 0;  // kernel launches (graph nodes included)
     for (int attempt = 0; attempt < 4; ++attempt) {
         if (T->dface) {
             cudaFree(T->dface);
@@ -865,6 +866,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                 cudaMemsetAsync(redo_count, 0, sizeof(unsigned int) * 4, ls);
                 cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ls);
                 lrc |= td_launch_sing_table(ls, md, op->op, op->prec, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
+                nlaunch += npairs > 0;
             } else if (ph == 1 || ph == 2) {
                 // one batch: entries (phase 1) and 3D-ACA (phase 2); several: both per
                 // batch in phase 1
@@ -878,13 +880,18 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                     nab.noff = dnoff + q0;
                     nab.nentries = batch_nent[bt];
                     const int nct = std::min(nctas_near, nab.nnear);
-                    if (ph == 1)
+                    if (ph == 1) {
                         lrc |= td_launch_near_entries(ls, md, op->op, op->prec, nab, table, ctx->num_sms);
-                    if ((ph == 2 && nbt == 1) || (ph == 1 && nbt > 1))
+                        nlaunch += nab.nentries > 0;
+                    }
+                    if ((ph == 2 && nbt == 1) || (ph == 1 && nbt > 1)) {
                         lrc |= td_launch_near_aca(ls, op->prec, nab, o, ap, scr_near, maxIJ, nct);
+                        nlaunch += nab.nnear > 0;
+                    }
                 }
             } else {
                 lrc |= td_launch_far_aca(ls, md, op->op, op->prec, fa, o, ap, nctas_far, ctx->far_nt[pf]);
+                nlaunch += fa.nfar > 0;
             }
             if (use_graph) {
                 ge = cudaStreamEndCapture(ls, &graph);
@@ -953,6 +960,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
             cudaEventRecord(r0, ctx->stream);
             const int lr = td_launch_far_aca(ctx->stream, md, op->op, op->prec, fr, o2, ap,
                                              std::min<int>(nctas_far, (int)nredo), ctx->far_nt[pf]);
+            ++nlaunch;
             cudaEventRecord(r1, ctx->stream);
             const cudaError_t re = cudaStreamSynchronize(ctx->stream);
             float mr = 0.0f;
@@ -1052,6 +1060,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     st.ms_near = ms[1] + ms[2];
     st.ms_far = ms[3] + ms_redo;
     st.pool_growths = st_redo;
+    st.launches = nlaunch;
     st.ms_total = now_ms() - t0;
     if (hflags & TD_DEV_RANK_CAP)
         td_fail(ctx, TDBEM_OK, "note: some far faces reached the rank cap %d", kcap);
