@@ -47,6 +47,23 @@ TD_D cx<T> apply_coef(cx<T> v, const cx<T> *coef, const cx<T> *const *base, int 
     return v - coef_sum(coef, base, cn, idx);
 }
 
+// dst[t n + i] = src[t ld + i] for t < k, i < n, by the whole block; the
+// index pair of an element is advanced incrementally (one division per thread).
+template <class T>
+TD_D void copy_cols(cx<T> *dst, const cx<T> *src, int64_t ld, int k, int n) {
+    int t = threadIdx.x / n, i = threadIdx.x - (threadIdx.x / n) * n;
+    const int dt = blockDim.x / n, di = blockDim.x - (blockDim.x / n) * n;
+    for (int e = threadIdx.x; e < k * n; e += blockDim.x) {
+        dst[e] = src[(int64_t)t * ld + i];
+        t += dt;
+        i += di;
+        if (i >= n) {
+            i -= n;
+            ++t;
+        }
+    }
+}
+
 // h = sum_{t < kf} U[t * su + i] V[t * sv + j] with independent accumulators.
 template <class T>
 TD_D cx<T> lowrank_at(const cx<T> *U, int64_t su, const cx<T> *V, int64_t sv, int kf, int i, int j) {
@@ -748,12 +765,20 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     {
                         A s2 = 0, uu = 0, vv = 0;
                         const cx<T> *uk = Uw + (int64_t)kf * a.maxI, *vk = Vw + (int64_t)kf * a.maxJ;
-                        for (int64_t e = tid; e < (int64_t)nI * nJ; e += blockDim.x) {
-                            const int i = (int)(e / nJ), j = (int)(e - (e / nJ) * nJ);
+                        // (i, j) of e advanced incrementally: no division per element
+                        int ie = tid / nJ, je = tid - (tid / nJ) * nJ;
+                        const int di = NT / nJ, dj = NT - (NT / nJ) * nJ;
+                        for (int e = tid; e < nI * nJ; e += NT) {
                             cx<T> sv = Sd[e];
-                            cfma(sv, uk[i], vk[j]);
+                            cfma(sv, uk[ie], vk[je]);
                             Sd[e] = sv;
                             s2 += cabs2(sv);
+                            ie += di;
+                            je += dj;
+                            if (je >= nJ) {
+                                je -= nJ;
+                                ++ie;
+                            }
                         }
                         for (int i = tid; i < nI; i += blockDim.x) uu += cabs2(uk[i]);
                         for (int j = tid; j < nJ; j += blockDim.x) vv += cabs2(vk[j]);
@@ -1112,10 +1137,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 r = l;
                 break;
             }
-            for (int64_t e = tid; e < (int64_t)kf * nI; e += blockDim.x)
-                pool[off + e] = Uw[(e / nI) * a.maxI + e % nI];
-            for (int64_t e = tid; e < (int64_t)kf * nJ; e += blockDim.x)
-                pool[off + (int64_t)kf * nI + e] = Vw[(e / nJ) * a.maxJ + e % nJ];
+            copy_cols(pool + off, Uw, a.maxI, kf, nI);
+            copy_cols(pool + off + (int64_t)kf * nI, Vw, a.maxJ, kf, nJ);
             for (int kk = tid; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = F.fl[kk];
             if (tid == 0) {
                 o.kpiv[tb + l] = k;
