@@ -641,12 +641,14 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
     static_assert(sizeof(GramTiles<float>) >=
                       RebuildTile<NT>::KC * (RebuildTile<NT>::TI + RebuildTile<NT>::TJ) * sizeof(c32),
                   "rebuild tiles must fit in the Gram tiles' shared memory");
+    static_assert(sizeof(GramTiles<T>) >= kDenseS * sizeof(cx<T>), "S of a dense-S face must fit in the Gram tiles");
     using AM = typename AmOf<T>::type;
     using A = AccT<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FarShared<T> &S = *reinterpret_cast<FarShared<T> *>(smem_raw);
     size_t soff = align16(sizeof(FarShared<T>));
     GramTiles<T> *gt = reinterpret_cast<GramTiles<T> *>(smem_raw + soff);
+    cx<T> *Ss = reinterpret_cast<cx<T> *>(gt);  // S of dense-S blocks (no Gram tiles needed there)
     soff += align16(sizeof(GramTiles<T>));
     const int Nu = a.nf;
     FarFreq<T> F = far_freq<T>(smem_raw + soff, Nu);
@@ -684,7 +686,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             // ------------------------------------------------ ACA of the residual face
             for (int w = tid; w < (nI + 31) / 32; w += blockDim.x) used[w] = 0u;
             // dense-path blocks: C(k) = sum_d f_d[k] H_d from the rebuilt faces, once per
-            // term, and the face's own approximation S = 0 (it becomes H_l)
+            // term; dense-S blocks also start the face's own approximation S = 0 in shared
+            // memory (the Gram tiles' space, unused by these blocks), copied to H_l at the end
             cx<T> *Sd = Hs + (int64_t)l * dcap;
             for (int t = tid; t < 64; t += blockDim.x) S.nrow[t] = A(0);
             if (small) {
@@ -692,7 +695,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     cx<T> acc = {0, 0};
                     for (int d = 0; d < l; ++d) cfma(acc, fib[(tb + d) * Nu + k], Hs[(int64_t)d * dcap + e]);
                     Cd[e] = acc;
-                    Sd[e] = cx<T>{0, 0};
+                    if (dense_s) Ss[e] = cx<T>{0, 0};
                 }
             }
             __syncthreads();
@@ -713,7 +716,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                         const cx<T> ent = group_entry<T, OP>(m, rows[istar], cols[min(j, nJ - 1)], sr, si, j < nJ);
                         if (j < nJ && (lane & 7) == 0) {
                             const int64_t e = (int64_t)istar * nJ + j;
-                            const cx<T> v = ent - Cd[e] - Sd[e];
+                            const cx<T> v = ent - Cd[e] - Ss[e];
                             Vw[(int64_t)kf * a.maxJ + j] = v;
                             const auto key = pivot_key(v);
                             if (am_better(key, j, am.v, am.i)) am = {key, j};
@@ -748,7 +751,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                         const cx<T> ent = group_entry<T, OP>(m, rows[min(i, nI - 1)], cols[jstar], sr, si, i < nI);
                         if (i < nI && (lane & 7) == 0) {
                             const int64_t e = (int64_t)i * nJ + jstar;
-                            const cx<T> u = cdiv(ent - Cd[e] - Sd[e], piv);
+                            const cx<T> u = cdiv(ent - Cd[e] - Ss[e], piv);
                             Uw[(int64_t)kf * a.maxI + i] = u;
                             if (i != istar && !(used[i >> 5] & (1u << (i & 31)))) {
                                 const auto key = pivot_key(u);
@@ -769,9 +772,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                         int ie = tid / nJ, je = tid - (tid / nJ) * nJ;
                         const int di = NT / nJ, dj = NT - (NT / nJ) * nJ;
                         for (int e = tid; e < nI * nJ; e += NT) {
-                            cx<T> sv = Sd[e];
+                            cx<T> sv = Ss[e];
                             cfma(sv, uk[ie], vk[je]);
-                            Sd[e] = sv;
+                            Ss[e] = sv;
                             s2 += cabs2(sv);
                             ie += di;
                             je += dj;
@@ -999,10 +1002,12 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             AM am = {-1, 0x7fffffff};
             const int64_t nIJ = (int64_t)nI * nJ;
             if (dense_s) {
-                // dense-S path: the rebuilt face is S itself
-                for (int64_t e = tid; e < nIJ; e += blockDim.x) {
-                    const auto key = pivot_key(Sd[e]);
-                    if (am_better(key, (int)e, am.v, am.i)) am = {key, (int)e};
+                // dense-S path: the rebuilt face is S itself (stored as H_l)
+                for (int e = tid; e < (int)nIJ; e += blockDim.x) {
+                    const cx<T> v = Ss[e];
+                    Sd[e] = v;
+                    const auto key = pivot_key(v);
+                    if (am_better(key, e, am.v, am.i)) am = {key, e};
                 }
             } else if (rebuild_tiled_fp32<NT>(gt, Uw, Vw, a.maxI, a.maxJ, kf, nI, nJ, small ? Sd : nullptr, am)) {
                 // large face: tiled rebuild done
