@@ -234,8 +234,26 @@ __global__ void __launch_bounds__(256) k_apply_y(ApplyZArgs a, TensorOut o) {
                     X1 = a.Z + a.zbase[b] + (int64_t)rpt * d * L + c0;
                     X2 = X1 + L;
                 }
-#pragma unroll 2
-                for (int t = 0; t < K; ++t) {
+                // face entries four at a time, loaded before use (the loop is bound by
+                // the latency of these loads from HBM)
+                int t = 0;
+                for (; t + 4 <= K; t += 4) {
+                    c32 mv[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) mv[s] = M[(int64_t)(t + s) * ms];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const c32 mc = cconj(mv[s]);
+                        const c32 *x1 = X1 + (int64_t)(t + s) * nrhs, *x2 = X2 + (int64_t)(t + s) * nrhs;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (q >= nc) continue;
+                            cfma(acc[q], mv[s], x1[q]);
+                            if (rpt == 2) cfma(acc[q], mc, x2[q]);
+                        }
+                    }
+                }
+                for (; t < K; ++t) {
                     const c32 mv = M[(int64_t)t * ms], mc = cconj(mv);
                     const c32 *x1 = X1 + (int64_t)t * nrhs, *x2 = X2 + (int64_t)t * nrhs;
 #pragma unroll
