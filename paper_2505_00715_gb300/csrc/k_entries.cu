@@ -162,6 +162,11 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     constexpr int NV = OP == TD_SLP ? 1 : 3;
+    // s / c of every frequency in shared memory (nf <= 256, checked by the caller):
+    // a pass over FC frequencies reads them by broadcast instead of holding them
+    __shared__ float2 s_sig[256];
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) s_sig[k] = make_float2((float)sig[2 * k], (float)sig[2 * k + 1]);
+    __syncthreads();
     for (int p = warp; p < npairs; p += nwarps) {
         int ti = pti[p], tj = ptj[p];
         if (OP == TD_SLP && ti > tj) {
@@ -174,13 +179,6 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
         const int nq = ss_npoints(G.cls, m.ng);
         const bool zero = (OP == TD_DLP && G.cls == 3) || G.cls == 0;
         for (int f0 = 0; f0 < nf; f0 += FC) {
-            float sg[FC][2];
-#pragma unroll
-            for (int j = 0; j < FC; ++j) {
-                const int k = min(f0 + j, nf - 1);
-                sg[j][0] = (float)sig[2 * k];
-                sg[j][1] = (float)sig[2 * k + 1];
-            }
             c32 acc[FC][NV];
 #pragma unroll
             for (int j = 0; j < FC; ++j)
@@ -206,12 +204,13 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
                     float lf[3] = {(float)lam[0], (float)lam[1], (float)lam[2]};
 #pragma unroll
                     for (int j = 0; j < FC; ++j) {
-                        const c32 e = expm_sr(sg[j][0], sg[j][1], rf);
+                        const float2 sgj = s_sig[min(f0 + j, nf - 1)];
+                        const c32 e = expm_sr(sgj.x, sgj.y, rf);
                         c32 v;
                         if (OP == TD_SLP) {
                             v = {bf * e.x, bf * e.y};
                         } else {
-                            const float pr = fmaf(sg[j][0], rf, 1.0f), pi = sg[j][1] * rf;
+                            const float pr = fmaf(sgj.x, rf, 1.0f), pi = sgj.y * rf;
                             v = {bf * (pr * e.x - pi * e.y), bf * (pr * e.y + pi * e.x)};
                         }
 #pragma unroll
@@ -423,9 +422,9 @@ int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, co
     int grid = std::min((npairs + 3) / 4, num_sms * 8);
     if (prec == TDBEM_MIXED) {
         if (op == TD_SLP)
-            k_sing_table_mixed<TD_SLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            k_sing_table_mixed<TD_SLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         else
-            k_sing_table_mixed<TD_DLP, 6><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            k_sing_table_mixed<TD_DLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         return (int)cudaGetLastError();
     }
     if (op == TD_SLP)
