@@ -329,7 +329,8 @@ def main():
     r_np = timed(2, use_model=False)
     no_pred = {"step_ms": statistics.median([r[0] for r in r_np]),
                "time_to_tensor_s": statistics.median([r[2]["ms_total"] for r in r_np]) / 1e3,
-               "phase_ms": {k: r_np[-1][2][k] for k in ("ms_plan", "ms_singular", "ms_near", "ms_far")}}
+               "phase_ms": {k: r_np[-1][2][k] for k in ("ms_plan", "ms_singular", "ms_near", "ms_far")},
+               "aca_tests": r_np[-1][2]["aca_tests"]}
     del r_np
     fp64 = None
     if not args.no_fp64:
@@ -388,7 +389,8 @@ def main():
             "compression": {"stored_complex": st["stored_complex"], "dense_complex": st["dense_complex"],
                             "rate": st["stored_complex"] / st["dense_complex"], "sum_rank": st["sum_rank"],
                             "max_rank": st["max_rank"], "nblocks": st["nblocks"], "nfar": st["nfar"],
-                            "sum_face_rank": st["sum_face_rank"], "pool_growths": st["pool_growths"]},
+                            "sum_face_rank": st["sum_face_rank"], "pool_growths": st["pool_growths"],
+                            "aca_tests": st["aca_tests"]},
             "predictor": dict(pinfo, without=no_pred),
             "autotuned_far_launch": tuned and {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1]},
             "fp64_form": fp64,

@@ -104,6 +104,10 @@ typedef struct {
     int64_t pool_growths;           /* face pool grown during compression: far blocks redone
                                        (or all phases rerun after a near-field overflow) */
     int64_t launches;               /* kernel launches of the compression */
+    int64_t aca_tests;              /* synchronised stopping tests of the far faces' ACA on the
+                                       factor-norm path (faces above 1600 entries); the rank
+                                       predictor batches the tests of the steps below its
+                                       predicted rank into one */
 } tdbem_stats;
 
 /* ---- context -------------------------------------------------------------- */

@@ -824,7 +824,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) cudaEventCreate(&ev[k]);
     int hflags = 0;
-    long long hev[2] = {0, 0};
+    long long hev[3] = {0, 0, 0};
     float ms_redo = 0.0f;  // far blocks redone after the pool grew
     int st_redo = 0;
     int64_t nlaunch = 0;  // kernel launches (graph nodes included)
@@ -1054,6 +1054,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     st.dense_complex = T->nrows * T->ncols * (int64_t)Nu;
     st.entries_regular = nent * Nu + hev[0];
     st.entries_tube = hev[1];
+    st.aca_tests = hev[2];
     st.pairs_singular = (int64_t)npairs * Nu;
     st.ms_plan = t_plan - t0;
     st.ms_singular = ms[0];

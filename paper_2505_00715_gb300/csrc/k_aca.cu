@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
     const int64_t dcap = a.dense_cap;
     cx<T> *fib = (cx<T> *)o.fib;
     cx<T> *pool = (cx<T> *)o.face;
-    long long ev_reg = 0, ev_tube = 0;
+    long long ev_reg = 0, ev_tube = 0, ev_tests = 0;  // entries; synchronised ACA stopping tests
     for (;;) {
         if (tid == 0) S.idx = (int)atomicAdd(a.counter, 1u);
         __syncthreads();
@@ -939,6 +939,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     continue;
                 }
                 for (int t = tid; t <= kf; t += blockDim.x) S.nrow[t] = A(0);
+                ++ev_tests;
                 __syncthreads();
                 {
                     int npairs = 0;
@@ -1181,6 +1182,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
     if (tid == 0 && a.evals) {
         atomicAdd((unsigned long long *)&a.evals[0], (unsigned long long)ev_reg);
         atomicAdd((unsigned long long *)&a.evals[1], (unsigned long long)ev_tube);
+        atomicAdd((unsigned long long *)&a.evals[2], (unsigned long long)ev_tests);
     }
 }
 

@@ -52,7 +52,8 @@ struct FarArgs {
                             // and the correction C(k) [dense_cap]
     int64_t scratch_per_cta;  // complex units
     unsigned int *counter;  // work queue head
-    int64_t *evals;         // [2] regular, tube entries evaluated
+    int64_t *evals;         // [3] regular, tube entries evaluated; ACA stopping tests of the
+                            // low-rank-norm faces (one per synchronised test round)
     int *harvest;           // non-null: record face-ACA ranks per (far block, frequency), [nfar][Nu]
     const int *kpred;       // nullable: predicted face rank per (block id, frequency) [nb][Nu]
     int64_t dense_cap;      // largest |I||J| handled with dense faces (0: none)

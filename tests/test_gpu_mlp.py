@@ -143,3 +143,23 @@ def test_predictor_keeps_the_adaptive_result(td, ctx, orc, trained):
     assert np.linalg.norm(y1 - y0) <= 1e-4 * np.linalg.norm(y0)
     s0, s1 = X0.stats(), X1.stats()
     print("far phase without / with predictor: %.1f / %.1f ms" % (s0["ms_far"], s1["ms_far"]))
+
+
+def test_predictor_gain_fewer_aca_tests(td, ctx, trained):
+    """What the trained network gains over the method without it: on faces
+    whose ACA norm comes from the factor Grams (above 1600 entries), the
+    steps below the predicted face rank run without their synchronised
+    stopping test and are tested in one batched round, so a compression
+    takes fewer test rounds (block barriers); the ranks stay those of the
+    adaptive criterion (previous test)."""
+    M = trained[0]
+    V, T = icosphere(4)
+    gm = td.Mesh(ctx, V, T)
+    f = td.Freqs.bdf2(ctx, 64, 0.05)
+    tree = td.Tree(gm, td.P0, td.P0, 32, 2.0)
+    s0 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED).stats()
+    s1 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED, model=M).stats()
+    print("ACA stopping-test rounds without / with predictor: %d / %d (%.2f); far %.1f / %.1f ms"
+          % (s0["aca_tests"], s1["aca_tests"], s1["aca_tests"] / max(1, s0["aca_tests"]), s0["ms_far"], s1["ms_far"]))
+    assert s0["aca_tests"] > 0
+    assert s1["aca_tests"] < s0["aca_tests"]
