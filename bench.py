@@ -248,6 +248,9 @@ def main():
 
     ctx = td.Context(local)
     stream = ctx.stream
+    # roofline denominators of the compression's pipes, measured on this GPU
+    # before any timed work (special-function unit, FP32 and FP64 FMA)
+    pipe_peaks = {k: ctx.measure_peak(k) for k in ("sfu", "fma32", "fma64")}
     V, T = workload_mesh(cfg)
     mesh = td.Mesh(ctx, V, T)
     freqs = workload_freqs(td, ctx, cfg)
@@ -370,7 +373,7 @@ def main():
 
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
-    roof = roofline(st, cfg, blocks, peaks, peak_kind, clocks, args.workload)
+    roof = roofline(st, cfg, blocks, peaks, peak_kind, clocks, args.workload, pipe_peaks)
     if rank == 0:
         line = {
             "metric": "entries/s", "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
@@ -476,19 +479,25 @@ def far_traffic(workload):
     return FAR_TRAFFIC["bytes"] if h.hexdigest()[:16] == FAR_TRAFFIC["sha256_16"] else None
 
 
-def roofline(st, cfg, blocks, peaks, peak_kind, clocks, workload=None):
+def roofline(st, cfg, blocks, peaks, peak_kind, clocks, workload=None, pipe_peaks=None):
     """Dominant phase of the compression against its ALU roofline.
 
     Far-field 3D-ACA kernel: its algorithmic work is the entry generation,
     point-pair evaluations (49 per P0 x P0 entry) of which each needs four
-    special-function-unit operations (rsqrt, exp2, sin, cos); peak = 16 SFU
-    operations per clock per SM x 152 SMs x the median SM clock sampled during
-    the timed region.  The fraction shows how far the kernel is from being
+    special-function-unit operations (rsqrt, exp2, sin, cos); peak = the
+    special-function throughput measured on this GPU by tdbem_measure_peak
+    (the same four operations), else 16 per clock per SM x 152 SMs x the
+    sampled SM clock.  The fraction shows how far the kernel is from being
     bound by its entry arithmetic (the rest is ACA bookkeeping and latency)."""
     phases = {"singular": st["ms_singular"], "near": st["ms_near"], "far": st["ms_far"]}
     dom = max(phases, key=phases.get)
     clock_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    sfu_peak = 16.0 * 152 * clock_mhz * 1e6 / 1e12  # T SFU-ops/s
+    if pipe_peaks and pipe_peaks.get("sfu"):
+        sfu_peak = pipe_peaks["sfu"] / 1e12  # T SFU-ops/s, measured
+        peak_source = "measured: tdbem_measure_peak special-function microbenchmark (rsqrt, ex2, sin, cos)"
+    else:
+        sfu_peak = 16.0 * 152 * clock_mhz * 1e6 / 1e12
+        peak_source = "derived: 16 SFU ops/clk/SM x 152 SMs x %.0f MHz (sampled median)" % clock_mhz
     nI = (blocks[:, 1] - blocks[:, 0]).astype(np.int64)
     nJ = (blocks[:, 3] - blocks[:, 2]).astype(np.int64)
     near_entries = int(np.sum((nI * nJ)[blocks[:, 4] == 0])) * int(cfg["Nu"])
@@ -499,7 +508,8 @@ def roofline(st, cfg, blocks, peaks, peak_kind, clocks, workload=None):
            "achieved": achieved_far, "peak": sfu_peak, "frac": achieved_far / sfu_peak, "traffic": far_traffic(workload),
            "traffic_unit": "bytes per far launch (DRAM read + write, ncu)",
            "work": "%.3e point pairs x 4 SFU ops in %.1f ms" % (far_pairs, st["ms_far"]),
-           "peak_source": "derived: 16 SFU ops/clk/SM x 152 SMs x %.0f MHz (sampled median)" % clock_mhz,
+           "peak_source": peak_source,
+           "measured_pipe_peaks_per_s": pipe_peaks,
            "phase_ms": phases, "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_kind}
     if dom != "far":
         out["note"] = "dominant phase is %s; the far-kernel figures are reported for comparison" % dom

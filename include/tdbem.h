@@ -275,6 +275,16 @@ int tdbem_apply_weighted_host(tdbem_tensor_t t, const void *W_host, int32_t nrhs
 int tdbem_zgemm(tdbem_ctx_t ctx, int32_t M, int32_t N, int32_t K, const void *A, int64_t lda, const void *B,
                 int64_t ldb, void *D, int64_t ldd);
 
+/* Measured throughput of a pipe the compression runs on, the denominator of
+ * its roofline (no counterpart in the paper): what = 0: FP32 fused
+ * multiply-adds per second; 1: special-function operations per second
+ * (reciprocal square root, base-2 exponential, sine, cosine in equal
+ * parts: the four operations of a far-field point pair); 2: FP64 fused
+ * multiply-adds per second.  Independent dependency chains on every SM, one
+ * warm-up launch, then one launch timed with CUDA events (a few to tens of
+ * milliseconds).  Synchronous.  TDBEM_ERR_ARG for another `what`. */
+int tdbem_measure_peak(tdbem_ctx_t ctx, int32_t what, double *ops_per_s);
+
 /* ---- per-frequency solve (Sec. 2, the Laplace-domain systems of the gCQ
  * step; Sec. 5 solves them iteratively) --------------------------------------
  * Solves A(s_fidx) x = b for nrhs right-hand sides with restarted GMRES

@@ -60,6 +60,13 @@ class Context:
     def sync(self):
         self.check(self.L.tdbem_ctx_sync(self.h), "tdbem_ctx_sync")
 
+    def measure_peak(self, what):
+        """Measured operations per second: "fma32", "sfu" or "fma64"."""
+        code = {"fma32": 0, "sfu": 1, "fma64": 2}[what]
+        v = C.c_double()
+        self.check(self.L.tdbem_measure_peak(self.h, code, C.byref(v)), "tdbem_measure_peak")
+        return v.value
+
     def set_pool_scale(self, scale):
         """Scale of the far part of the first face-pool size in compress."""
         self.check(self.L.tdbem_ctx_set_pool_scale(self.h, float(scale)), "tdbem_ctx_set_pool_scale")

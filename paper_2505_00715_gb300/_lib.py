@@ -54,6 +54,7 @@ EXPORTS = {
     "tdbem_ctx_sync": (C.c_int, [C.c_void_p]),
     "tdbem_ctx_set_near_batch": (C.c_int, [C.c_void_p, C.c_int64]),
     "tdbem_ctx_set_pool_scale": (C.c_int, [C.c_void_p, C.c_double]),
+    "tdbem_measure_peak": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_mesh_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.POINTER(C.c_void_p)]),
     "tdbem_mesh_destroy": (C.c_int, [C.c_void_p]),

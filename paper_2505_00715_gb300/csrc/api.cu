@@ -205,6 +205,32 @@ extern "C" int tdbem_ctx_set_near_batch(tdbem_ctx_t ctx, int64_t bytes) {
     return TDBEM_OK;
 }
 
+extern "C" int tdbem_measure_peak(tdbem_ctx_t ctx, int32_t what, double *ops_per_s) {
+    if (!ctx || !ops_per_s || what < 0 || what > 2) return TDBEM_ERR_ARG;
+    const int grid = ctx->num_sms * 8;
+    const int iters = what == 2 ? 64 : 2048;
+    double *out = nullptr;
+    int rc = dalloc(ctx, &out, (size_t)grid);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double ops = 0.0;
+    int lr = td_launch_peak(ctx->stream, what, grid, iters, out, &ops);  // warm-up
+    cudaEventRecord(e0, ctx->stream);
+    lr |= td_launch_peak(ctx->stream, what, grid, iters, out, &ops);
+    cudaEventRecord(e1, ctx->stream);
+    const cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    float ms = 0.0f;
+    const bool timed = se == cudaSuccess && !lr && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (!timed) return td_fail(ctx, TDBEM_ERR_CUDA, "peak microbenchmark failed: %s", cudaGetErrorString(se));
+    *ops_per_s = ops / (ms * 1e-3);
+    return TDBEM_OK;
+}
+
 extern "C" int tdbem_ctx_set_pool_scale(tdbem_ctx_t ctx, double scale) {
     if (!ctx) return TDBEM_ERR_ARG;
     if (!(scale > 0.0)) return td_fail(ctx, TDBEM_ERR_ARG, "pool scale must be > 0");

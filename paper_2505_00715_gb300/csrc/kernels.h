@@ -61,6 +61,9 @@ struct FarArgs {
     unsigned int *redo_count;
 };
 
+// k_peak.cu: throughput microbenchmark (what: 0 FP32 FMA, 1 special-function
+// unit, 2 FP64 FMA); *ops = operations performed by the launch
+int td_launch_peak(cudaStream_t st, int what, int grid, int iters, void *out, double *ops);
 int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
                       const int *rows, int64_t nr, const int *cols, int64_t nc, const int *fidx,
                       int64_t nf, void *out);
