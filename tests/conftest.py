@@ -9,7 +9,7 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
-    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (run with -m gpu on the GPU box)")
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (select with -m gpu)")
     config.addinivalue_line("markers", "slow: longer CPU test")
 
 
