@@ -148,45 +148,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
             const int kc = min(kTK, K - k0);
             // ---- A tile: item it -> (kstep s, row group g, core matrix kh, row rr);
             // its 16 bytes sit at byte offset 16 * it of the canonical layout
-            for (int it = tid; it < kTM * 16; it += kThreads) {
-                const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 15, s = it >> 8;
-                const int r = g * 8 + rr, kr = s * 16 + kh * 8;  // real k of the first element
-                float v[8];
-                const bool imag = kr >= kTK;
-                const int kk = imag ? kr - kTK : kr;
-                c32 x[8];
-                if (r < mr) {
-                    ops.a8(job, job.m0 + r, k0 + kk, k0 + kc, x);
-                } else {
+            // two items per pass: both items' loads are issued before either is split
+            for (int it0 = tid; it0 < kTM * 16; it0 += 2 * kThreads) {
+                c32 x[2][8];
+                bool imag[2];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] = c32{0.f, 0.f};
+                for (int u = 0; u < 2; ++u) {
+                    const int it = it0 + u * kThreads;
+                    const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 15, s = it >> 8;
+                    const int r = g * 8 + rr, kr = s * 16 + kh * 8;  // real k of the first element
+                    imag[u] = kr >= kTK;
+                    const int kk = imag[u] ? kr - kTK : kr;
+                    if (it < kTM * 16 && r < mr) {
+                        ops.a8(job, job.m0 + r, k0 + kk, k0 + kc, x[u]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[u][e] = c32{0.f, 0.f};
+                    }
                 }
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = imag ? x[e].y : x[e].x;
-                const SplitPack p = split8(v);
-                *reinterpret_cast<uint4 *>(Ah + 16 * it) = p.hi;
-                *reinterpret_cast<uint4 *>(Al + 16 * it) = p.lo;
+                for (int u = 0; u < 2; ++u) {
+                    const int it = it0 + u * kThreads;
+                    if (it >= kTM * 16) continue;
+                    float v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = imag[u] ? x[u][e].y : x[u][e].x;
+                    const SplitPack p = split8(v);
+                    *reinterpret_cast<uint4 *>(Ah + 16 * it) = p.hi;
+                    *reinterpret_cast<uint4 *>(Al + 16 * it) = p.lo;
+                }
             }
             // ---- B tile: 2 kTN real rows (re / im row of every complex column)
-            for (int it = tid; it < 2 * kTN * 16; it += kThreads) {
-                const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 31, s = it >> 9;
-                const int nr = g * 8 + rr, kr = s * 16 + kh * 8;
-                const int n = nr >> 1, im_row = nr & 1;
-                const bool second = kr >= kTK;
-                const int kk = second ? kr - kTK : kr;
-                float v[8];
-                c32 x[8];
-                if (n < nc) {
-                    ops.b8(job, k0 + kk, k0 + kc, job.n0 + n, x);
-                } else {
+            for (int it0 = tid; it0 < 2 * kTN * 16; it0 += 2 * kThreads) {
+                c32 x[2][8];
+                bool second[2];
+                int im_row[2];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] = c32{0.f, 0.f};
+                for (int u = 0; u < 2; ++u) {
+                    const int it = it0 + u * kThreads;
+                    const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 31, s = it >> 9;
+                    const int nr = g * 8 + rr, kr = s * 16 + kh * 8;
+                    const int n = nr >> 1;
+                    im_row[u] = nr & 1;
+                    second[u] = kr >= kTK;
+                    const int kk = second[u] ? kr - kTK : kr;
+                    if (it < 2 * kTN * 16 && n < nc) {
+                        ops.b8(job, k0 + kk, k0 + kc, job.n0 + n, x[u]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[u][e] = c32{0.f, 0.f};
+                    }
                 }
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = im_row ? (second ? x[e].x : x[e].y) : (second ? -x[e].y : x[e].x);
-                const SplitPack p = split8(v);
-                *reinterpret_cast<uint4 *>(Bh + 16 * it) = p.hi;
-                *reinterpret_cast<uint4 *>(Bl + 16 * it) = p.lo;
+                for (int u = 0; u < 2; ++u) {
+                    const int it = it0 + u * kThreads;
+                    if (it >= 2 * kTN * 16) continue;
+                    float v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        v[e] = im_row[u] ? (second[u] ? x[u][e].x : x[u][e].y) : (second[u] ? -x[u][e].y : x[u][e].x);
+                    const SplitPack p = split8(v);
+                    *reinterpret_cast<uint4 *>(Bh + 16 * it) = p.hi;
+                    *reinterpret_cast<uint4 *>(Bl + 16 * it) = p.lo;
+                }
             }
             fence_async_shared();
             __syncthreads();
