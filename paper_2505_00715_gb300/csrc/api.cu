@@ -1055,8 +1055,9 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     // ---- host copies of the per-block results and statistics
     T->rank.resize(nb);
     std::vector<int32_t> frank(nb * Nu);
-    TD_CUDA(ctx, cudaMemcpy(T->rank.data(), T->drank, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
-    TD_CUDA(ctx, cudaMemcpy(frank.data(), T->dfrank, sizeof(int32_t) * nb * Nu, cudaMemcpyDeviceToHost));
+    if (cudaMemcpy(T->rank.data(), T->drank, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(frank.data(), T->dfrank, sizeof(int32_t) * nb * Nu, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(td_fail(ctx, TDBEM_ERR_CUDA, "reading the block results failed"));
     tdbem_stats &st = T->stats;
     std::memset(&st, 0, sizeof st);
     st.nblocks = nb;
