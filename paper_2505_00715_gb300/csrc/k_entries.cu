@@ -419,6 +419,7 @@ int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const
 int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, const int *pti, const int *ptj,
                          int npairs, const double *sig, int nf, c64 *table, int num_sms) {
     if (npairs == 0) return 0;
+    if (nf > 256) return (int)cudaErrorInvalidValue;  // the frequencies are staged in shared memory
     int grid = std::min((npairs + 3) / 4, num_sms * 8);
     if (prec == TDBEM_MIXED) {
         if (op == TD_SLP)
