@@ -397,6 +397,11 @@ def main():
             # (faces and fibres) + W read once + y written once
             "apply_roofline": apply_roof,
             "entries_evaluated_per_s": (st["entries_regular"] + st["entries_tube"]) / (st["ms_total"] / 1e3),
+            # entries the compression evaluated, by kind: regular FP32 entries (near tensor
+            # and far fibres), frequency tubes at the pivots, touching pairs (FP64 geometry)
+            # integrated per unique frequency
+            "entries_evaluated": {"regular_fp32": st["entries_regular"], "tube_fp32": st["entries_tube"],
+                                  "touching_pair_frequencies": st["pairs_singular"]},
             "compression": {"stored_complex": st["stored_complex"], "dense_complex": st["dense_complex"],
                             "rate": st["stored_complex"] / st["dense_complex"], "sum_rank": st["sum_rank"],
                             "max_rank": st["max_rank"], "nblocks": st["nblocks"], "nfar": st["nfar"],
