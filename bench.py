@@ -1,24 +1,31 @@
 """Benchmark of the GB300 3D-ACA tensor path (one JSON line on rank 0).
 
-Workload (default, the 5120-triangle configuration): icosphere R = 1 with
-5120 flat triangles, Galerkin single layer P0 x P0, wave speed 1, BDF2
-convolution quadrature N = 64, dt = 0.05 (33 unique frequencies), PCA cluster
-tree with leaf size 32 and eta = 2, 3D-ACA at eps = 1e-4 (face ACA 1e-6),
-Sauter-Schwab with 5 Gauss points per variable; apply with 16 right-hand sides.
-Other workloads (--workload): the 1280-triangle sphere, the double layer on
-the 5120-triangle sphere, and finned machine housings of about 30k, 60k and
-80k triangles (c = 343 m/s, gCQ with 256 / 256 / 512 contour points, leaf
-64; 32 right-hand sides at 80k).
+Workload (default): the batched, uneven-block configuration, a finned
+machine housing (closed cylinder r = 0.1 m, length 0.3 m, 12 fins 5 mm thick,
+end caps; 28,704 flat triangles, 1 % vertex jitter), Galerkin single layer
+P0 x P0, c = 343 m/s, gCQ contour of 2-stage Radau IIA for 256 geometrically
+graded steps (ratio 1.01, T = 0.015 s; 256 contour points, 128 unique), PCA
+cluster tree with leaf size 64 and eta = 2, 3D-ACA at eps = 1e-4 (face ACA
+1e-6), Sauter-Schwab with 5 Gauss points per variable, one persistent launch
+per phase under captured graphs, autotuned far launch; apply with 16
+right-hand sides.  Other workloads (--workload): icospheres with 1280 and
+5120 triangles (BDF2 N = 64, c = 1; single and double layer) and housings of
+about 60k and 80k triangles (256 / 512 contour points; 32 right-hand sides at
+80k).  The 80k housing is not the default: one step takes about 13 s, so the
+default 20 timed + 5 warm-up steps would hold the GPU for over 5 minutes.
 
 One step = the whole path: block cluster tree, compression (touching-pair
-table, near-field entries, near and far 3D-ACA, one graph) and one
-multi-frequency apply.  Metric: dense-equivalent tensor entries per second,
-rows * cols * N_Q / step time.  Inputs are resident in HBM before the timed
-region; the e2e figure repeats the step through the host-buffer API (mesh
-upload, tree, compression, apply with host W and y).
+table, near-field entries, near and far 3D-ACA) and one multi-frequency
+apply.  Metric (value): operator entries evaluated per second, every entry
+A(i, j, s_k) that the compression's kernels evaluate counted once per
+evaluation (near-field tensor, far-field fibres, frequency tubes); the
+dense-equivalent rate (rows * cols * N_Q / step) and the time to the tensor
+are reported beside it.  Inputs are resident in HBM before the timed region;
+the e2e figure repeats the step through the host-buffer API (mesh upload,
+tree, compression, apply with host W and y).
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
-comparison) on a bounded sample of the same workload (sphere workloads).
+comparison) on a bounded block sample of the same workload.
 """
 import argparse
 import json
@@ -64,7 +71,7 @@ def workload_freqs(td, ctx, cfg):
     if "gcq" in cfg:
         nq, ratio, T_end = cfg["gcq"]
         dts = graded_steps(nq, ratio, T_end)
-        return td.Freqs.gcq(ctx, dts.min(), dts.max(), td.RADAU2, nq)
+        return td.Freqs.gcq(ctx, dts, td.RADAU2, nq)
     return td.Freqs.bdf2(ctx, cfg["N"], cfg["dt"])
 
 
@@ -153,62 +160,96 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def oracle_baseline(cfg, target_s=15.0, max_stride=None):
-    """Oracle compression of every stride-th block of the workload, timed on
-    the host cores; returns dense-equivalent entries/s of the sampled blocks."""
+def oracle_problem(cfg):
+    """The workload for the oracle: mesh, unique frequencies, tree, operator."""
     import oracle as orc
-    if "level" not in cfg:
-        return None
-    V, T = icosphere(cfg["level"])
+    V, T = workload_mesh(cfg)
     m = orc.Mesh(V, T)
-    s = orc.freqs_bdf2(cfg["N"], cfg["dt"])
-    Nu = cfg["N"] // 2 + 1
+    if "gcq" in cfg:
+        nq, ratio, T_end = cfg["gcq"]
+        dts = graded_steps(nq, ratio, T_end)
+        s, _, _ = orc.freqs_gcq(dts.min(), dts.max(), 1, nq)
+        su = s[:nq // 2]  # points l and NQ-1-l are conjugate
+    else:
+        s = orc.freqs_bdf2(cfg["N"], cfg["dt"])
+        su = s[:cfg["N"] // 2 + 1]  # points k and N-k are conjugate
     cols = 0 if cfg["op"] == "SLP" else 1
     tr = orc.Tree(m, 0, cols, cfg["leaf"], cfg["eta"])
-    blocks = tr.blocks
+    return m, su, tr, getattr(orc, cfg["op"])
+
+
+def oracle_sample_mask(blocks, per_sample, offset, seed=3):
+    """Deterministic block sample stratified by size: the blocks in
+    decreasing order of rows * cols (ties by depth-first index) are cut into
+    strata of k = ceil(nblocks / per_sample) consecutive blocks, the members
+    of every stratum are put in a seeded random order, and sample `offset`
+    takes member `offset` of every stratum.  Every sample then has the
+    workload's size mix, each block is equally likely to be in it, and
+    offsets 0..k-1 give disjoint samples."""
     nb = len(blocks)
-    op = getattr(orc, cfg["op"])
-    # pilot: a sparse sample to estimate the cost per represented entry
-    stride = max_stride or max(1, nb // 40)
+    sz = (blocks[:, 1] - blocks[:, 0]).astype(np.int64) * (blocks[:, 3] - blocks[:, 2])
+    order = np.lexsort((np.arange(nb), -sz))
+    k = max(1, -(-nb // max(1, per_sample)))
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(nb, dtype=bool)
+    for a in range(0, nb, k):
+        stratum = order[a:a + k]
+        mask[stratum[rng.permutation(len(stratum))[offset % len(stratum)]]] = True
+    return mask, k
+
+
+def oracle_baseline(cfg, problem=None, per_sample=24, offset=0):
+    """Oracle 3D-ACA compression (FP64, OpenMP over blocks) of a stratified
+    block sample of the workload (oracle_sample_mask), timed on the host
+    cores block by block.  Cost model: the blocks are independent and the
+    whole workload (thousands of blocks) spreads over the host cores, so its
+    rate is cores x (entries evaluated / summed single-block seconds); value
+    is that rate in entries evaluated per second (the unit of the GPU line).
+    The wall-clock rate of the sample itself is reported beside it (a small
+    sample leaves cores idle behind its largest block)."""
+    import oracle as orc
+    m, su, tr, op = problem or oracle_problem(cfg)
+    mask, k = oracle_sample_mask(tr.blocks, per_sample, offset)
     t0 = time.perf_counter()
-    orc.Tensor(m, op, s[:Nu], tr, cfg["eps"], cfg["eps_aca"], c=cfg["c"], ng=cfg["ng"], block_stride=stride)
-    t1 = time.perf_counter() - t0
-    for _ in range(3):  # denser samples until the sample takes about target_s
-        if t1 >= target_s / 2 or stride == 1:
-            break
-        stride = max(1, int(stride * t1 / target_s))
-        t0 = time.perf_counter()
-        orc.Tensor(m, op, s[:Nu], tr, cfg["eps"], cfg["eps_aca"], c=cfg["c"], ng=cfg["ng"], block_stride=stride)
-        t1 = time.perf_counter() - t0
-    sel = blocks[np.arange(nb) % stride == 0]
-    rep = float(np.sum((sel[:, 1] - sel[:, 0]).astype(np.int64) * (sel[:, 3] - sel[:, 2]))) * cfg["N"]
-    return {"value": rep / t1, "unit": "entries/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle 3D-ACA compression (FP64, OpenMP over blocks) of every %d-th block (%d of %d blocks) "
-                      "of the same workload, %.1f s; value = sampled blocks' rows*cols*N_Q / time" % (
-                          stride, len(sel), nb, t1),
-            "seconds": t1}
+    X = orc.Tensor(m, op, su, tr, cfg["eps"], cfg["eps_aca"], c=cfg["c"], ng=cfg["ng"], block_mask=mask)
+    wall = time.perf_counter() - t0
+    ev, secs = X.stats["evals"], X.stats["block_seconds"]
+    cores = os.cpu_count()
+    return {"value": cores * ev / secs, "unit": "entries/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle 3D-ACA compression (FP64, OpenMP over blocks) of %d of the workload's %d blocks "
+                      "(stratified by size: one block of each run of %d in size order, sample %d), %.3e entries "
+                      "evaluated in %.1f s summed over the blocks (%.1f s wall); value = cores x entries / summed "
+                      "block seconds (independent blocks spread over the cores)" % (
+                          int(mask.sum()), len(mask), k, offset, ev, secs, wall),
+            "evals": ev, "block_seconds": secs, "wall_seconds": wall, "wall_value": ev / wall}
 
 
 def run_reference(args, cfg, wl_name):
+    """The oracle as the reference arm: step j compresses the j-th of the
+    disjoint stratified block samples (oracle_sample_mask); value = cores x
+    entries evaluated / summed block seconds over the timed steps."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    vals = []
+    prob = oracle_problem(cfg)
+    ev = secs = wall = 0.0
     info = None
-    if "level" not in cfg:
-        print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on the sphere workloads only "
-                          "(its FP64 compression of the housing's largest blocks exceeds the run's time bound)"}))
-        return 0
     for k in range(args.warmup + args.steps):
-        info = oracle_baseline(cfg, target_s=args.ref_seconds)
+        info = oracle_baseline(cfg, problem=prob, per_sample=args.ref_blocks, offset=k)
         if k >= args.warmup:
-            vals.append(info["value"])
-    v = statistics.median(vals)
+            ev += info["evals"]
+            secs += info["block_seconds"]
+            wall += info["wall_seconds"]
+    v = info["cores"] * ev / secs
+    sample = ("oracle 3D-ACA compression (FP64, OpenMP over blocks), one stratified sample of about %d blocks per "
+              "step (disjoint samples), %.3e entries evaluated in %.1f s summed over the blocks of the timed steps "
+              "(%.1f s wall); value = cores x entries / summed block seconds" % (args.ref_blocks, ev, secs, wall))
     line = {"impl": "reference", "metric": "entries/s", "value": v, "unit": "entries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": wl_name},
+            "ms_per_step": 1e3 * wall / args.steps, "wall_value": ev / wall,
             "cpu_baseline": {"value": v, "unit": "entries/s", "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"]},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -220,10 +261,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere5120_slp_bdf2_N64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="housing30k_slp_gcq256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form")
-    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-blocks", type=int, default=24, help="blocks per oracle sample (each step of "
+                    "--impl reference; twice as many for cpu_baseline)")
     ap.add_argument("--no-predictor", action="store_true", help="time the form without the rank predictor")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
@@ -244,13 +286,13 @@ def main():
 
     cpu_base = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu_base = oracle_baseline(cfg)  # host cores, before any timed GPU work
+        cpu_base = oracle_baseline(cfg, per_sample=2 * args.ref_blocks)  # host cores, before any timed GPU work
 
     ctx = td.Context(local)
     stream = ctx.stream
     # roofline denominators of the compression's pipes, measured on this GPU
     # before any timed work (special-function unit, FP32 and FP64 FMA)
-    pipe_peaks = {k: ctx.measure_peak(k) for k in ("sfu", "fma32", "fma64")}
+    pipe_peaks = {k: ctx.measure_peak(k) for k in ("sfu", "fma32", "fma64", "pair64")}
     V, T = workload_mesh(cfg)
     mesh = td.Mesh(ctx, V, T)
     freqs = workload_freqs(td, ctx, cfg)
@@ -277,7 +319,9 @@ def main():
         tr0 = td.Tree(mesh, td.P0, colb, cfg["leaf"], cfg["eta"])
         tuned = td.autotune(mesh, op, freqs, tr0, eps=cfg["eps"], eps_aca=cfg["eps_aca"], prec=td.MIXED, c=cfg["c"],
                             ng=cfg["ng"], model=model)
-        if not args.no_fp64:
+        if not args.no_fp64 and "level" in cfg:
+            # (on the housings one FP64 compression takes tens of seconds: the
+            # FP64 form keeps the default launch shape there)
             td.autotune(mesh, op, freqs, tr0, eps=cfg["eps"], eps_aca=cfg["eps_aca"], prec=td.FP64, c=cfg["c"],
                         ng=cfg["ng"])
 
@@ -322,7 +366,9 @@ def main():
     X = res[-1][3]
     apply_ms = statistics.median([r[1] for r in res])
     represented = float(nrows) * ncols * NQ
-    value, total_ms = job_throughput(sum(ms), represented, args.steps, world, dist)
+    # units of a step: the operator entries its compression evaluated
+    evaluated = statistics.mean([float(r[2]["entries_regular"] + r[2]["entries_tube"]) for r in res])
+    value, total_ms = job_throughput(sum(ms), evaluated, args.steps, world, dist)
     blocks = X.partition()
     apply_gflops = apply_flops(X, blocks, NQ, nrhs) / (apply_ms / 1e3) / 1e9
     X = None
@@ -339,13 +385,17 @@ def main():
     if not args.no_fp64:
         W64 = torch.as_tensor(W_host, dtype=torch.complex128, device=dev)
         y64 = torch.empty((nrows, nrhs), dtype=torch.complex128, device=dev)
-        timed(1, td.FP64, W64, y64, use_model=False)
+        if "level" in cfg:
+            timed(1, td.FP64, W64, y64, use_model=False)  # warm-up where a step is short
         r64 = timed(1, td.FP64, W64, y64, use_model=False)
         s64 = r64[0][2]
         X64 = r64[0][3]
         fp64 = {"step_ms": r64[0][0], "time_to_tensor_s": s64["ms_total"] / 1e3,
                 "apply_ms": r64[0][1], "apply_gflops": apply_flops(X64, X64.partition(), NQ, nrhs) / (r64[0][1] / 1e3) / 1e9,
-                "entries_per_s": represented / (r64[0][0] / 1e3),
+                "entries_per_s": (s64["entries_regular"] + s64["entries_tube"]) / (r64[0][0] / 1e3),
+                "dense_equivalent_entries_per_s": represented / (r64[0][0] / 1e3),
+                "roofline": roofline_fp64(s64, cfg, X64.partition(), pipe_peaks),
+                "apply_roofline": apply_roofline(s64, cfg, NQ, ncols, nrows, nrhs, r64[0][1], 16),
                 "phase_ms": {k: s64[k] for k in ("ms_plan", "ms_singular", "ms_near", "ms_far")},
                 "sum_rank": s64["sum_rank"], "stored_complex": s64["stored_complex"]}
         del X64, W64, y64, r64
@@ -367,16 +417,12 @@ def main():
             e2e_ms.append(dt)
         del X2, tr2, m2
     e2e_med = statistics.median(e2e_ms)
-    e2e = {"value": world * represented / (e2e_med / 1e3), "unit": "entries/s",
+    e2e = {"value": world * evaluated / (e2e_med / 1e3), "unit": "entries/s",
            "h2d_bytes_per_step": int(V.nbytes + T.nbytes + Wh.numel() * 8),
            "d2h_bytes_per_step": int(yh.numel() * 8), "ms_per_step": e2e_med}
 
     peaks, peak_kind = load_peaks()
-    apply_bytes = 8.0 * (st["stored_complex"] + float(NQ) * ncols * nrhs + float(nrows) * nrhs)
-    apply_gbs = apply_bytes / (apply_ms / 1e3) / 1e9
-    apply_roof = {"bound": "hbm", "unit": "GB/s", "achieved": apply_gbs, "peak": peaks.get("hbm_gbs"),
-                  "frac": apply_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-                  "algorithmic_bytes": apply_bytes, "peak_source": peak_kind}
+    apply_roof = apply_roofline(st, cfg, NQ, ncols, nrows, nrhs, apply_ms, 8)
     clocks = clk.summary()
     roof = roofline(st, cfg, blocks, peaks, peak_kind, clocks, args.workload, pipe_peaks)
     if rank == 0:
@@ -391,12 +437,13 @@ def main():
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_tensor_s": st["ms_total"] / 1e3,
+            "entries_evaluated_per_step": evaluated,
+            "dense_equivalent_entries_per_s": world * represented * args.steps / (total_ms / 1e3),
             "phase_ms": {k: st[k] for k in ("ms_plan", "ms_singular", "ms_near", "ms_far")},
             "apply_ms": apply_ms, "apply_gflops": apply_gflops,
             # the apply against HBM: algorithmic bytes = the compressed tensor read once
             # (faces and fibres) + W read once + y written once
             "apply_roofline": apply_roof,
-            "entries_evaluated_per_s": (st["entries_regular"] + st["entries_tube"]) / (st["ms_total"] / 1e3),
             # entries the compression evaluated, by kind: regular FP32 entries (near tensor
             # and far fibres), frequency tubes at the pivots, touching pairs (FP64 geometry)
             # integrated per unique frequency
@@ -460,6 +507,36 @@ def train_predictor(td, ctx, cfg, dev):
                    "under_predicted": float(np.mean(pw < yw)),
                    "note": "under_predicted = share of (far block, frequency) faces whose ACA continues "
                            "adaptively past the predicted first trip count"}
+
+
+def apply_roofline(st, cfg, NQ, ncols, nrows, nrhs, apply_ms, es):
+    """The weighted apply against HBM: algorithmic bytes = the compressed
+    tensor read once (faces and fibres) + W read once + y written once, es
+    bytes per complex value."""
+    peaks, kind = load_peaks()
+    nbytes = float(es) * (st["stored_complex"] + float(NQ) * ncols * nrhs + float(nrows) * nrhs)
+    gbs = nbytes / (apply_ms / 1e3) / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
+            "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None, "algorithmic_bytes": nbytes,
+            "peak_source": kind + (" (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "")}
+
+
+def roofline_fp64(st, cfg, blocks, pipe_peaks):
+    """Far phase of the plain FP64 form against the FP64 point-pair rate
+    measured on this GPU (tdbem_measure_peak, the same operation on
+    independent chains on every SM): its entries are 49 point pairs each
+    (SLP; 6 x 49 per P1 column of the double layer)."""
+    nI = (blocks[:, 1] - blocks[:, 0]).astype(np.int64)
+    nJ = (blocks[:, 3] - blocks[:, 2]).astype(np.int64)
+    near_entries = int(np.sum((nI * nJ)[blocks[:, 4] == 0])) * int(cfg["Nu"])
+    ppe = 49 if cfg["op"] == "SLP" else 49 * 6
+    pairs = (st["entries_regular"] - near_entries + st["entries_tube"]) * ppe
+    ach = pairs / (st["ms_far"] / 1e3)
+    peak = pipe_peaks.get("pair64") if pipe_peaks else None
+    return {"bound": "alu", "kernel": "far 3D-ACA (k_far_aca, FP64)", "unit": "point pairs/s", "achieved": ach,
+            "peak": peak, "frac": ach / peak if peak else None,
+            "work": "%.3e point pairs in %.1f ms" % (pairs, st["ms_far"]),
+            "peak_source": "measured: tdbem_measure_peak FP64 point-pair microbenchmark"}
 
 
 def apply_flops(X, blocks, NQ, nrhs):

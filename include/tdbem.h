@@ -147,11 +147,16 @@ int64_t tdbem_mesh_ndof(tdbem_mesh_t mesh, int32_t basis);
  * (1e-8)^(1/(2N)).  Computed in FP64 on the device. */
 int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double lambda, tdbem_freqs_t *out);
 /* gCQ contour of App. A: s_l = gamma(sigma_l), weights w_l (positively
- * oriented Cauchy quadrature), l = 1..NQ, for steps in [dt_min, dt_max] and
- * the RK method rk.  Computed in FP64 on the device (Jacobi elliptic
- * functions by the AGM).  q = 1 is lifted to 1.01 (App. A, last paragraph). */
-int tdbem_freqs_gcq(tdbem_ctx_t ctx, double dt_min, double dt_max, int32_t rk, int32_t NQ,
-                    tdbem_freqs_t *out);
+ * oriented Cauchy quadrature), l = 1..NQ, for the N time steps dts (host
+ * FP64 [N], every step > 0) and the RK method rk.  The contour depends on
+ * the steps through dt_min = min(dts) and dt_max = max(dts) (App. A); the
+ * steps are kept with the set (tdbem_freqs_steps).  Computed in FP64 on the
+ * device (Jacobi elliptic functions by the AGM).  q = 1 is lifted to 1.01
+ * (App. A, last paragraph). */
+int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ, tdbem_freqs_t *out);
+/* The time steps of a gCQ set (host [N], nullable) and their count *N
+ * (nullable); a BDF2 set returns N = 0. */
+int tdbem_freqs_steps(tdbem_freqs_t f, double *dts, int32_t *N);
 /* Copies the NQ points (and weights, nullable; BDF2 sets have none and
  * return zeros) to host arrays [2*NQ]; *NQ and *Nu (number of frequencies up
  * to conjugation, App. A last paragraph) are returned when non-NULL.
@@ -188,20 +193,41 @@ int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const 
                   int64_t nr, const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf,
                   void *out);
 
+/* The same entries through one of the kernels that tdbem_compress runs, so
+ * that each can be checked on its own against an independent evaluation:
+ *   path = TDBEM_PATH_GENERIC: tdbem_entries itself;
+ *   path = TDBEM_PATH_NEAR: the near-field phases of the compression on the
+ *     single block rows x cols: the touching-pair table of the mesh
+ *     (Sauter-Schwab, Sec. 3), then the dense near-field tensor kernel
+ *     (regular pairs by the 7-point rule with the point geometry shared
+ *     across frequencies, touching pairs read from the table); at most 256
+ *     frequencies and 2^31 - 1 entries per frequency;
+ *   path = TDBEM_PATH_FIBRE: the far-field engine's entry evaluation (the
+ *     8-lane point-pair groups with which Algorithm 1's fibres and frequency
+ *     tubes are formed in tdbem_compress), which applies the regular 7 x 7
+ *     rule to every pair: admissible blocks hold no touching pairs, and on a
+ *     touching pair this path does not give the operator's entry.
+ * Arguments and layout as tdbem_entries.  The index arrays are copied to the
+ * host and checked (TDBEM_ERR_ARG on an index out of range).  Allocates
+ * transient device buffers and synchronises the context's stream. */
+enum { TDBEM_PATH_GENERIC = 0, TDBEM_PATH_NEAR = 1, TDBEM_PATH_FIBRE = 2 };
+int tdbem_entries_path(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const int32_t *rows, int64_t nr,
+                       const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf, int32_t path, void *out);
+
 /* Allocation-free variant of tdbem_entries (the paper has no counterpart; it
- * exists for callers that cannot allocate device memory at call time: code
- * running while a stream is captured into a CUDA graph, where cudaMalloc and
- * cudaFree are not allowed, and applications whose device memory is reserved
- * up front by their own allocator).  Same arguments, kernel and results as
+ * exists for callers that cannot allocate device memory at call time:
+ * applications whose device memory is reserved up front by their own pool
+ * allocator, and host loops that must not pay the device-wide
+ * synchronisation of cudaFree).  Same arguments, kernel and results as
  * tdbem_entries; the few scratch values of a call (quadrature nodes, scaled
  * frequencies) live in one fixed device array of the library instead of
- * buffers allocated per call.
+ * buffers allocated per call, and are written there by a small kernel on the
+ * context's stream (no host-to-device copy).
  *   - No cudaMalloc, cudaFree or other allocating call is made.
  *   - The frequency set may have at most TDBEM_NOALLOC_MAX_NQ points;
  *     larger sets return TDBEM_ERR_ARG with a message.
- *   - The first call on a device looks up the device address of the fixed
- *     array (once per device); make that first call before any stream
- *     capture.  The array (about 132 KB) stays allocated on every device
+ *   - tdbem_ctx_create looks up the device address of the fixed array (once
+ *     per device).  The array (about 132 KB) stays allocated on every device
  *     that loaded the library until the process exits.
  *   - All calls share the array and it keeps the last call's contents; calls
  *     ordered on one stream are safe, calls that overlap on the GPU (other
@@ -280,7 +306,9 @@ int tdbem_zgemm(tdbem_ctx_t ctx, int32_t M, int32_t N, int32_t K, const void *A,
  * multiply-adds per second; 1: special-function operations per second
  * (reciprocal square root, base-2 exponential, sine, cosine in equal
  * parts: the four operations of a far-field point pair); 2: FP64 fused
- * multiply-adds per second.  Independent dependency chains on every SM, one
+ * multiply-adds per second; 3: FP64 single-layer point pairs per second
+ * (distance, exp, sin and cos, weight, complex accumulate: the inner
+ * operation of the FP64 form's entries).  Independent dependency chains on every SM, one
  * warm-up launch, then one launch timed with CUDA events (a few to tens of
  * milliseconds).  Synchronous.  TDBEM_ERR_ARG for another `what`. */
 int tdbem_measure_peak(tdbem_ctx_t ctx, int32_t what, double *ops_per_s);

@@ -54,7 +54,7 @@ def lib():
             "orc_aca_dense": (i32, [vp, i32, i32, d, i32, vp, vp]),
             "orc_aca3d_dense": (i32, [vp, i32, i32, i32, d, i32, vp, vp, vp]),
             "orc_aca3d_dense_acaface": (i32, [vp, i32, i32, i32, d, d, i32, vp, vp, vp, vp]),
-            "orc_compress": (vp, [vp, i32, d, i32, vp, i32, vp, d, d, i32, i32]),
+            "orc_compress": (vp, [vp, i32, d, i32, vp, i32, vp, d, d, i32, i32, vp]),
             "orc_tensor_free": (None, [vp]),
             "orc_tensor_stats": (None, [vp, vp]),
             "orc_tensor_block_ranks": (None, [vp, vp, vp]),
@@ -243,15 +243,19 @@ def aca3d_dense(t, eps, eps_aca=None):
 class Tensor:
     """Block-compressed operator tensor from the oracle's 3D-ACA."""
 
-    def __init__(self, mesh, op, s, tree, eps, eps_aca, c=1.0, ng=6, nthreads=0, block_stride=1):
+    def __init__(self, mesh, op, s, tree, eps, eps_aca, c=1.0, ng=6, nthreads=0, block_stride=1, block_mask=None):
+        """block_stride / block_mask: compress only every block_stride-th
+        block, or only the blocks where block_mask (bool [nblocks]) is set."""
         self.s = _c128(s)
         self.mesh, self.tree = mesh, tree
+        mask = None if block_mask is None else np.ascontiguousarray(block_mask, dtype=np.uint8)
+        self._mask = mask
         self.h = lib().orc_compress(mesh.h, op, c, ng, _p(self.s), len(self.s), tree.h, eps, eps_aca,
-                                    nthreads, block_stride)
-        st = np.zeros(8)
+                                    nthreads, block_stride, None if mask is None else _p(mask))
+        st = np.zeros(9)
         lib().orc_tensor_stats(self.h, _p(st))
         self.stats = dict(nblocks=int(st[0]), nfar=int(st[1]), sum_rank=int(st[2]), max_rank=int(st[3]),
-                          stored=st[4], dense=st[5], evals=st[6], sum_face_rank=int(st[7]))
+                          stored=st[4], dense=st[5], evals=st[6], sum_face_rank=int(st[7]), block_seconds=st[8])
         self.nrows = mesh.ndof(P0)
         self.ncols = mesh.ndof(P1 if op == DLP else P0)
 

@@ -123,15 +123,17 @@ int orc_aca3d_dense_acaface(const double *t, int nI, int nJ, int nK, double eps,
                             int rmax, int32_t *kpiv, double *H, double *f, int32_t *face_rank);
 
 /* Compressed operator tensor of a BEM operator over a frequency list.
- * block_stride > 1 compresses only every block_stride-th block (a bounded
- * sample for timing; the others are left empty). */
+ * block_stride > 1 compresses only every block_stride-th block, and a
+ * non-NULL block_mask [nblocks] only the blocks with a non-zero mask byte
+ * (bounded samples for timing; the others are left empty). */
 typedef struct orc_tensor orc_tensor;
 orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const double *s, int nf,
                          const orc_tree *t, double eps, double eps_aca, int nthreads,
-                         int block_stride);
+                         int block_stride, const uint8_t *block_mask);
 void orc_tensor_free(orc_tensor *x);
-/* stats[8]: nblocks, nfar, sum ranks, max rank, stored complex entries,
- * dense complex entries (nrows*ncols*nf), entries evaluated, sum face ranks */
+/* stats[9]: nblocks, nfar, sum ranks, max rank, stored complex entries,
+ * dense complex entries (nrows*ncols*nf), entries evaluated, sum face ranks,
+ * summed wall-clock seconds of the blocks' compressions (timing only) */
 void orc_tensor_stats(const orc_tensor *x, double *stats);
 /* per block: rank r_b and for far blocks the sum of face ranks. */
 void orc_tensor_block_ranks(const orc_tensor *x, int32_t *r, int32_t *kface);

@@ -31,6 +31,8 @@
  * by the matrix analogue of eq. norm) or at rank min(|I|, |J|); Algorithm 1
  * also stops when a residual face is exactly zero.
  */
+#define _POSIX_C_SOURCE 200809L /* clock_gettime */
+#include <time.h>
 #include "orc.h"
 
 #include <complex.h>
@@ -362,6 +364,7 @@ typedef struct {
     face *faces;
     cplx *f; /* [r][nf] */
     int64_t evals;
+    double secs; /* wall time of this block's compression (instrumentation only) */
 } blockc;
 
 struct orc_tensor {
@@ -372,9 +375,16 @@ struct orc_tensor {
     int32_t *perm_r, *perm_c, *inv_r, *inv_c;
 };
 
+/* wall-clock seconds (timing of the blocks only; no part of the method) */
+static double orc_wtime(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
 orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const double *s, int nf,
                          const orc_tree *t, double eps, double eps_aca, int nthreads,
-                         int block_stride) {
+                         int block_stride, const uint8_t *block_mask) {
     orc_tensor *x = calloc(1, sizeof *x);
     x->nrows = orc_mesh_ndof(m, ORC_P0);
     x->ncols = orc_mesh_ndof(m, op == ORC_DLP ? ORC_P1 : ORC_P0);
@@ -403,10 +413,11 @@ orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const doub
         B->j0 = bl[5 * b + 2];
         B->j1 = bl[5 * b + 3];
         B->far = bl[5 * b + 4];
-        if (block_stride > 1 && b % block_stride != 0) {
+        if ((block_stride > 1 && b % block_stride != 0) || (block_mask && !block_mask[b])) {
             B->r = 0;
             continue;
         }
+        const double t_start = orc_wtime();
         src3 S = {0};
         S.nI = B->i1 - B->i0;
         S.nJ = B->j1 - B->j0;
@@ -425,6 +436,7 @@ orc_tensor *orc_compress(const orc_mesh *m, int op, double c, int ng, const doub
         B->faces = faces;
         B->f = fib;
         B->evals = S.evals;
+        B->secs = orc_wtime() - t_start;
         free(kp);
     }
     return x;
@@ -446,7 +458,7 @@ void orc_tensor_free(orc_tensor *x) {
 }
 
 void orc_tensor_stats(const orc_tensor *x, double *st) {
-    double nfar = 0, sumr = 0, maxr = 0, stored = 0, evals = 0, sumk = 0;
+    double nfar = 0, sumr = 0, maxr = 0, stored = 0, evals = 0, sumk = 0, secs = 0;
     for (int64_t b = 0; b < x->nb; ++b) {
         const blockc *B = &x->b[b];
         int nI = B->i1 - B->i0, nJ = B->j1 - B->j0;
@@ -454,6 +466,7 @@ void orc_tensor_stats(const orc_tensor *x, double *st) {
         sumr += B->r;
         if (B->r > maxr) maxr = B->r;
         evals += (double)B->evals;
+        secs += B->secs;
         for (int d = 0; d < B->r; ++d) {
             stored += x->nf;
             if (B->faces[d].rank < 0)
@@ -472,6 +485,7 @@ void orc_tensor_stats(const orc_tensor *x, double *st) {
     st[5] = (double)x->nrows * (double)x->ncols * x->nf;
     st[6] = evals;
     st[7] = sumk;
+    st[8] = secs;
 }
 
 void orc_tensor_block_ranks(const orc_tensor *x, int32_t *r, int32_t *kface) {

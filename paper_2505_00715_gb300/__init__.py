@@ -17,7 +17,8 @@ import numpy as np
 from . import _lib
 from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
 
-__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "compress", "harvest", "rank_bin", "autotune",
+__all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "PATH_GENERIC", "PATH_NEAR",
+           "PATH_FIBRE", "compress", "harvest", "rank_bin", "autotune",
            "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError"]
 NPARAMS = 5648
 
@@ -61,8 +62,9 @@ class Context:
         self.check(self.L.tdbem_ctx_sync(self.h), "tdbem_ctx_sync")
 
     def measure_peak(self, what):
-        """Measured operations per second: "fma32", "sfu" or "fma64"."""
-        code = {"fma32": 0, "sfu": 1, "fma64": 2}[what]
+        """Measured operations per second: "fma32", "sfu", "fma64" or "pair64"
+        (FP64 single-layer point pairs)."""
+        code = {"fma32": 0, "sfu": 1, "fma64": 2, "pair64": 3}[what]
         v = C.c_double()
         self.check(self.L.tdbem_measure_peak(self.h, code, C.byref(v)), "tdbem_measure_peak")
         return v.value
@@ -123,10 +125,22 @@ class Freqs:
         return cls(ctx, h)
 
     @classmethod
-    def gcq(cls, ctx, dt_min, dt_max, rk, NQ):
+    def gcq(cls, ctx, dts, rk, NQ):
+        """gCQ contour of App. A for the time steps dts (host array) and the
+        Runge-Kutta method rk (EULER or RADAU2), NQ contour points."""
         h = C.c_void_p()
-        ctx.check(ctx.L.tdbem_freqs_gcq(ctx.h, dt_min, dt_max, rk, NQ, C.byref(h)), "tdbem_freqs_gcq")
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        ctx.check(ctx.L.tdbem_freqs_gcq(ctx.h, _np_ptr(d), len(d), rk, NQ, C.byref(h)), "tdbem_freqs_gcq")
         return cls(ctx, h)
+
+    def steps(self):
+        """Time steps of a gCQ set (empty for BDF2)."""
+        n = C.c_int32()
+        self.ctx.check(self.ctx.L.tdbem_freqs_steps(self.h, None, C.byref(n)), "tdbem_freqs_steps")
+        d = np.zeros(n.value)
+        if n.value:
+            self.ctx.check(self.ctx.L.tdbem_freqs_steps(self.h, _np_ptr(d), C.byref(n)), "tdbem_freqs_steps")
+        return d
 
     def __del__(self):
         if getattr(self, "h", None) and _lib._lib is not None:
@@ -164,8 +178,15 @@ def _cdtype(prec):
     return torch.complex128 if prec == FP64 else torch.complex64
 
 
-def entries(mesh, op, freqs, rows, cols, fidx, prec=MIXED, c=1.0, ng=5):
-    """A[rows, cols](s_fidx) as a device tensor [nf, nr, nc] (complex64 MIXED, complex128 FP64)."""
+PATH_GENERIC, PATH_NEAR, PATH_FIBRE = 0, 1, 2
+
+
+def entries(mesh, op, freqs, rows, cols, fidx, prec=MIXED, c=1.0, ng=5, path=PATH_GENERIC):
+    """A[rows, cols](s_fidx) as a device tensor [nf, nr, nc] (complex64 MIXED, complex128 FP64).
+    path selects the kernel: PATH_GENERIC (tdbem_entries), PATH_NEAR (the
+    compression's touching-pair table and near-field tensor kernels on the
+    block rows x cols) or PATH_FIBRE (the far-field engine's point-pair groups;
+    regular rule on every pair)."""
     torch = _torch()
     ctx = mesh.ctx
     dev = torch.device("cuda", ctx.device)
@@ -174,8 +195,12 @@ def entries(mesh, op, freqs, rows, cols, fidx, prec=MIXED, c=1.0, ng=5):
     f = torch.as_tensor(np.asarray(fidx, dtype=np.int32), device=dev)
     out = torch.empty((len(f), len(r), len(q)), dtype=_cdtype(prec), device=dev)
     o = _op(op, prec, c, ng)
-    ctx.check(ctx.L.tdbem_entries(mesh.h, C.byref(o), freqs.h, _ptr(r), len(r), _ptr(q), len(q), _ptr(f), len(f),
-                                  _ptr(out)), "tdbem_entries")
+    if path == PATH_GENERIC:
+        ctx.check(ctx.L.tdbem_entries(mesh.h, C.byref(o), freqs.h, _ptr(r), len(r), _ptr(q), len(q), _ptr(f), len(f),
+                                      _ptr(out)), "tdbem_entries")
+    else:
+        ctx.check(ctx.L.tdbem_entries_path(mesh.h, C.byref(o), freqs.h, _ptr(r), len(r), _ptr(q), len(q), _ptr(f),
+                                           len(f), int(path), _ptr(out)), "tdbem_entries_path")
     return out
 
 

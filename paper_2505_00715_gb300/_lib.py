@@ -60,8 +60,9 @@ EXPORTS = {
     "tdbem_mesh_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_mesh_ndof": (C.c_int64, [C.c_void_p, C.c_int32]),
     "tdbem_freqs_cq_bdf2": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_void_p)]),
-    "tdbem_freqs_gcq": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
+    "tdbem_freqs_gcq": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                   C.POINTER(C.c_void_p)]),
+    "tdbem_freqs_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "tdbem_freqs_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), C.c_void_p]),
     "tdbem_freqs_destroy": (C.c_int, [C.c_void_p]),
@@ -71,6 +72,8 @@ EXPORTS = {
     "tdbem_tree_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_entries": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                 C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
+    "tdbem_entries_path": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                     C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "tdbem_entries_noalloc": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                         C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
     "tdbem_compress": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p,

@@ -69,8 +69,9 @@ struct Guard {
     ~Guard() { release(); }
 };
 
-MeshDev mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw,
-                 const int *tp_slot) {
+}  // namespace
+
+MeshDev td_mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw, const int *tp_slot) {
     MeshDev d{};
     d.nt = (int)m->nt;
     d.nv = (int)m->nv;
@@ -104,7 +105,7 @@ MeshDev mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw
     return d;
 }
 
-int check_op(tdbem_ctx *ctx, const tdbem_op *op) {
+int td_check_op(tdbem_ctx *ctx, const tdbem_op *op) {
     if (!op) return td_fail(ctx, TDBEM_ERR_ARG, "op is NULL");
     if (op->op != TDBEM_SLP && op->op != TDBEM_DLP) return td_fail(ctx, TDBEM_ERR_ARG, "unknown operator %d", op->op);
     if (op->prec != TDBEM_FP64 && op->prec != TDBEM_MIXED) return td_fail(ctx, TDBEM_ERR_ARG, "unknown precision %d", op->prec);
@@ -112,6 +113,8 @@ int check_op(tdbem_ctx *ctx, const tdbem_op *op) {
     if (op->ng < 1 || op->ng > 16) return td_fail(ctx, TDBEM_ERR_ARG, "ng must be in 1..16");
     return TDBEM_OK;
 }
+
+namespace {
 
 // Gauss nodes and touching-pair slots for one operator (device, owned by caller)
 int prepare_sing(tdbem_ctx *ctx, const tdbem_mesh *m, int op, int ng, std::vector<void *> &owned,
@@ -179,7 +182,8 @@ extern "C" int tdbem_ctx_create(int device, void *stream, tdbem_ctx_t *out) {
         delete c;
         return TDBEM_ERR_CUDA;
     }
-    if (cudaMalloc(&c->dflags, sizeof(int)) != cudaSuccess || cudaMemset(c->dflags, 0, sizeof(int)) != cudaSuccess) {
+    if (td_noalloc_setup(device) != TDBEM_OK || cudaMalloc(&c->dflags, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->dflags, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamDestroy(c->capture);
         delete c;
@@ -206,9 +210,9 @@ extern "C" int tdbem_ctx_set_near_batch(tdbem_ctx_t ctx, int64_t bytes) {
 }
 
 extern "C" int tdbem_measure_peak(tdbem_ctx_t ctx, int32_t what, double *ops_per_s) {
-    if (!ctx || !ops_per_s || what < 0 || what > 2) return TDBEM_ERR_ARG;
+    if (!ctx || !ops_per_s || what < 0 || what > 3) return TDBEM_ERR_ARG;
     const int grid = ctx->num_sms * 8;
-    const int iters = what == 2 ? 64 : 2048;
+    const int iters = what == 3 ? 128 : what == 2 ? 64 : 2048;
     double *out = nullptr;
     int rc = dalloc(ctx, &out, (size_t)grid);
     if (rc) return rc;
@@ -453,13 +457,19 @@ extern "C" int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double
     return TDBEM_OK;
 }
 
-extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, double dt_min, double dt_max, int32_t rk, int32_t NQ,
+extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ,
                                tdbem_freqs_t *out) {
     cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
-    if (!ctx || !out || !(dt_min > 0.0) || !(dt_max >= dt_min) || !std::isfinite(dt_max) || NQ < 2 ||
-        NQ % 2 || NQ > 65536 || (rk != TDBEM_EULER && rk != TDBEM_RADAU2))
-        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_gcq: need 0 < dt_min <= dt_max, even NQ >= 2, rk EULER|RADAU2");
+    if (!ctx || !out || !dts || N < 1 || NQ < 2 || NQ % 2 || NQ > 65536 || (rk != TDBEM_EULER && rk != TDBEM_RADAU2))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_gcq: need N >= 1 steps, even NQ >= 2, rk EULER|RADAU2");
     *out = nullptr;
+    double dt_min = dts[0], dt_max = dts[0];
+    for (int32_t n = 0; n < N; ++n) {
+        if (!(dts[n] > 0.0) || !std::isfinite(dts[n]))
+            return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_gcq: step %d is not a finite positive number", n);
+        dt_min = std::min(dt_min, dts[n]);
+        dt_max = std::max(dt_max, dts[n]);
+    }
     double q = dt_max / dt_min;
     if (rk == TDBEM_RADAU2) q *= 5.0;  // |lambda_1(A)| = |lambda_2(A)| for 2-stage Radau IIA
     if (q < 1.01) q = 1.01;            // App. A: q = 1 gives k = 0; lift it slightly
@@ -468,6 +478,7 @@ extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, double dt_min, double dt_max, in
     f->ctx = ctx;
     f->NQ = NQ;
     f->kind = 1;
+    f->dts.assign(dts, dts + N);
     f->s.assign(2 * NQ, 0.0);
     f->w.assign(2 * NQ, 0.0);
     int rc;
@@ -492,6 +503,13 @@ extern "C" int tdbem_freqs_get(tdbem_freqs_t f, double *s, double *w, int32_t *N
     if (NQ) *NQ = f->NQ;
     if (Nu) *Nu = f->Nu;
     if (unique) std::memcpy(unique, f->unique.data(), sizeof(int32_t) * f->NQ);
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_freqs_steps(tdbem_freqs_t f, double *dts, int32_t *N) {
+    if (!f) return TDBEM_ERR_ARG;
+    if (dts && !f->dts.empty()) std::memcpy(dts, f->dts.data(), sizeof(double) * f->dts.size());
+    if (N) *N = (int32_t)f->dts.size();
     return TDBEM_OK;
 }
 
@@ -550,7 +568,7 @@ extern "C" int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_
     cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
     if (!mesh || !f) return TDBEM_ERR_ARG;
     tdbem_ctx *ctx = mesh->ctx;
-    int rc = check_op(ctx, op);
+    int rc = td_check_op(ctx, op);
     if (rc) return rc;
     if (nr < 0 || nc < 0 || nf < 0 || (nr * nc * nf > 0 && (!rows || !cols || !fidx || !out)))
         return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries: bad sizes or NULL pointers");
@@ -562,9 +580,89 @@ extern "C" int tdbem_entries(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_
     std::vector<double> hs(2 * f->NQ);
     for (int k = 0; k < 2 * f->NQ; ++k) hs[k] = f->s[k] / op->c;
     if ((rc = dalloc(ctx, &sig, hs.size(), &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size()))) return rc;
-    MeshDev md = mesh_dev(mesh, op->ng, gx, gw, tp_slot);
+    MeshDev md = td_mesh_dev(mesh, op->ng, gx, gw, tp_slot);
     if (td_launch_entries(ctx->stream, md, op->op, op->prec, sig, f->NQ, rows, nr, cols, nc, fidx, nf, out))
         return td_fail(ctx, TDBEM_ERR_CUDA, "entry kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // transient buffers are freed on return
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_entries_path(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, const int32_t *rows,
+                                  int64_t nr, const int32_t *cols, int64_t nc, const int32_t *fidx, int64_t nf,
+                                  int32_t path, void *out) {
+    if (path == TDBEM_PATH_GENERIC) return tdbem_entries(mesh, op, f, rows, nr, cols, nc, fidx, nf, out);
+    cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
+    if (!mesh || !f) return TDBEM_ERR_ARG;
+    tdbem_ctx *ctx = mesh->ctx;
+    int rc = td_check_op(ctx, op);
+    if (rc) return rc;
+    if (path != TDBEM_PATH_NEAR && path != TDBEM_PATH_FIBRE)
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: unknown path %d", path);
+    if (nr < 0 || nc < 0 || nf < 0 || (nr * nc * nf > 0 && (!rows || !cols || !fidx || !out)))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: bad sizes or NULL pointers");
+    if (nr * nc * nf == 0) return TDBEM_OK;
+    if (path == TDBEM_PATH_NEAR && (nf > 256 || nr * nc > INT32_MAX))
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: the near-field path takes at most 256 frequencies "
+                                           "and 2^31 - 1 entries per frequency");
+    // the index arrays are checked on the host (the near-field kernels read
+    // the tables at them without bounds checks, as inside tdbem_compress)
+    std::vector<int32_t> hr(nr), hc(nc), hf(nf);
+    TD_CUDA(ctx, cudaMemcpyAsync(hr.data(), rows, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaMemcpyAsync(hc.data(), cols, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaMemcpyAsync(hf.data(), fidx, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost, ctx->stream));
+    TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t ncol_max = op->op == TDBEM_SLP ? mesh->nt : mesh->nv;
+    for (int32_t v : hr)
+        if (v < 0 || v >= mesh->nt) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: row %d out of range", v);
+    for (int32_t v : hc)
+        if (v < 0 || v >= ncol_max) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: column %d out of range", v);
+    for (int32_t v : hf)
+        if (v < 0 || v >= f->NQ) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: frequency %d out of range", v);
+    std::vector<double> hs(2 * nf);
+    for (int64_t q = 0; q < nf; ++q) {
+        hs[2 * q] = f->s[2 * hf[q]] / op->c;
+        hs[2 * q + 1] = f->s[2 * hf[q] + 1] / op->c;
+    }
+    Guard g;
+    double *sig;
+    if ((rc = dalloc(ctx, &sig, hs.size(), &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size()))) return rc;
+    int lrc = 0;
+    if (path == TDBEM_PATH_FIBRE) {
+        MeshDev md = td_mesh_dev(mesh, op->ng, nullptr, nullptr, nullptr);  // regular rule only
+        lrc = td_launch_fibre_entries(ctx->stream, md, op->op, op->prec, sig, rows, nr, cols, nc, nf, out, ctx->num_sms);
+    } else {
+        // the compression's near-field phases on one block rows x cols: the
+        // touching-pair table of the mesh, then the dense near tensor
+        // [nf][nr][nc] written straight into out
+        double *gx, *gw;
+        int *tp_slot, *pti, *ptj, np;
+        if ((rc = prepare_sing(ctx, mesh, op->op, op->ng, g.p, &gx, &gw, &tp_slot, &pti, &ptj, &np))) return rc;
+        c64 *table;
+        int32_t *blk;
+        int64_t *pre;
+        if ((rc = dalloc(ctx, &table, (size_t)std::max(np, 1) * nf * 3, &g.p)) || (rc = dalloc(ctx, &blk, 8, &g.p)) ||
+            (rc = dalloc(ctx, &pre, 2, &g.p)))
+            return rc;
+        const int32_t hb[8] = {0, (int32_t)nr, 0, (int32_t)nc, 0, 0, 0, 0};  // block, then near_ids = {0}
+        const int64_t hp[2] = {0, 0};                                        // eprefix, noff
+        if ((rc = upload(ctx, blk, hb, 8)) || (rc = upload(ctx, pre, hp, 2))) return rc;
+        MeshDev md = td_mesh_dev(mesh, op->ng, gx, gw, tp_slot);
+        lrc = td_launch_sing_table(ctx->stream, md, op->op, op->prec, pti, ptj, np, sig, (int)nf, table, ctx->num_sms);
+        NearArgs na{};
+        na.nf = (int)nf;
+        na.sig = sig;
+        na.nnear = 1;
+        na.near_ids = blk + 5;
+        na.eprefix = pre;
+        na.noff = pre + 1;
+        na.blocks = blk;
+        na.perm_r = rows;
+        na.perm_c = cols;
+        na.nentries = nr * nc;
+        na.near = out;
+        if (!lrc) lrc = td_launch_near_entries(ctx->stream, md, op->op, op->prec, na, table, ctx->num_sms);
+    }
+    if (lrc) return td_fail(ctx, TDBEM_ERR_CUDA, "entry kernel launch failed: %s", cudaGetErrorString((cudaError_t)lrc));
     TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // transient buffers are freed on return
     return TDBEM_OK;
 }
@@ -604,7 +702,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
     if (!ctx || !mesh || !f || !tree || !cfg || !out) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_compress: NULL argument");
     *out = nullptr;
-    int rc = check_op(ctx, op);
+    int rc = td_check_op(ctx, op);
     if (rc) return rc;
     if (tree->mesh != mesh) return td_fail(ctx, TDBEM_ERR_ARG, "tree was built on another mesh");
     if (tree->side[0].basis != TDBEM_P0 || tree->side[1].basis != (op->op == TDBEM_DLP ? TDBEM_P1 : TDBEM_P0))
@@ -795,7 +893,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         (rc = upload(ctx, dfar_ids, far_ids.data(), far_ids.size())) ||
         (rc = upload(ctx, deprefix, eprefix.data(), eprefix.size())) || (rc = upload(ctx, dnoff, noff.data(), noff.size())))
         return fail(rc);
-    MeshDev md = mesh_dev(mesh, op->ng, gx, gw, tp_slot);
+    MeshDev md = td_mesh_dev(mesh, op->ng, gx, gw, tp_slot);
     NearArgs na{};
     na.nf = Nu;
     na.sig = sig;
@@ -1370,7 +1468,7 @@ extern "C" int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op 
                              const tdbem_aca_cfg *cfg, float *feats, int32_t *ranks, int64_t capacity, int64_t *count) {
     if (!ctx || !mesh || !f || !tree || !cfg || !count) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_harvest: NULL argument");
     cudaGetLastError();
-    int rc = check_op(ctx, op);
+    int rc = td_check_op(ctx, op);
     if (rc) return rc;
     if (tree->mesh != mesh || tree->side[0].basis != TDBEM_P0 ||
         tree->side[1].basis != (op->op == TDBEM_DLP ? TDBEM_P1 : TDBEM_P0))
@@ -1420,7 +1518,7 @@ extern "C" int tdbem_harvest(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op 
         return rc;
     cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, ctx->stream);
     cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ctx->stream);
-    MeshDev md = mesh_dev(mesh, op->ng, nullptr, nullptr, nullptr);  // far blocks have no touching pairs
+    MeshDev md = td_mesh_dev(mesh, op->ng, nullptr, nullptr, nullptr);  // far blocks have no touching pairs
     FarArgs fa{};
     fa.nfar = (int)far_ids.size();
     fa.far_ids = dfar;

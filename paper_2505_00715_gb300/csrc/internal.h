@@ -74,6 +74,7 @@ struct tdbem_freqs {
     double *ds = nullptr;         // device [2*NQ]
     double *dw = nullptr;
     int kind = 0;                 // 0 BDF2, 1 gCQ
+    std::vector<double> dts;      // gCQ: the time steps the contour was built for
 };
 
 // Compressed tensor (device pools + host copies of the small metadata).
@@ -126,6 +127,15 @@ int td_fail(tdbem_ctx *ctx, int code, const char *fmt, ...);
             return td_fail((ctx), TDBEM_ERR_CUDA, "%s: %s (%s:%d)", #call,                   \
                            cudaGetErrorString(e_), __FILE__, __LINE__);                      \
     } while (0)
+
+// api.cu: argument check of an operator description, and the device view of
+// a mesh's tables (Gauss-Legendre rule gx/gw and touching-pair slots as given)
+struct MeshDev;
+int td_check_op(tdbem_ctx *ctx, const tdbem_op *op);
+MeshDev td_mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double *gw, const int *tp_slot);
+// noalloc.cu: device address of the allocation-free entry point's scratch on
+// the current device `device` (once per device, cached)
+int td_noalloc_setup(int device);
 
 // planner.cpp
 void td_plan_tree(const tdbem_mesh *m, int basis, int leaf, HostTree &t);

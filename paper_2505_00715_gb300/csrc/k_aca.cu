@@ -16,6 +16,7 @@
 // (Sec. 4); the frequency tube at the pivot is evaluated with one warp per
 // frequency.  Persistent CTAs take far blocks from an atomic work queue
 // ordered by decreasing size.
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
@@ -1187,6 +1188,47 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
 }
 
 }  // namespace
+
+namespace {
+// The far-field engine's entry evaluation on its own: out[f][r][c] =
+// A[rows[r], cols[c]](sig_f) by group_entry, the 8-lane point-pair groups
+// with which k_far_aca forms its row and column fibres and its frequency
+// tubes (regular 7 x 7 rule, every pair; admissible blocks hold no touching
+// pairs).  Four entries per warp; every lane of a warp takes the same number
+// of trips, as group_entry's shuffles require.  An index out of range gives
+// NaN without any table access.
+template <class T, int OP>
+__global__ void __launch_bounds__(128) k_fibre_entries(MeshDev m, const double *sig, const int *rows, int64_t nr,
+                                                       const int *cols, int64_t nc, int64_t nf, cx<T> *out) {
+    const int64_t n = nr * nc * nf;
+    const int ncol_max = OP == TD_SLP ? m.nt : m.nv;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; base < n; base += stride) {
+        const int64_t t = base + ((threadIdx.x & 31) >> 3);
+        const int64_t tt = t < n ? t : 0;
+        const int64_t c = tt % nc, r = (tt / nc) % nr, f = tt / (nc * nr);
+        const int row = rows[r], col = cols[c];
+        const bool ok = t < n && row >= 0 && row < m.nt && col >= 0 && col < ncol_max;
+        const cx<T> v = group_entry<T, OP>(m, ok ? row : 0, ok ? col : 0, (T)sig[2 * f], (T)sig[2 * f + 1], ok);
+        if (t < n && (threadIdx.x & 7) == 0) out[t] = ok ? v : cx<T>{(T)NAN, (T)NAN};
+    }
+}
+}  // namespace
+
+int td_launch_fibre_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, const int *rows,
+                            int64_t nr, const int *cols, int64_t nc, int64_t nf, void *out, int num_sms) {
+    const int64_t n = nr * nc * nf;
+    if (n == 0) return 0;
+    const int grid = (int)std::min<int64_t>((n + 15) / 16, (int64_t)num_sms * 16);
+    if (prec == TDBEM_FP64) {
+        if (op == TD_SLP) k_fibre_entries<double, TD_SLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c64 *)out);
+        else k_fibre_entries<double, TD_DLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c64 *)out);
+    } else {
+        if (op == TD_SLP) k_fibre_entries<float, TD_SLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c32 *)out);
+        else k_fibre_entries<float, TD_DLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c32 *)out);
+    }
+    return (int)cudaGetLastError();
+}
 
 int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const TensorOut &o,
                        const AcaParams &p, void *scratch, int64_t sper, int nctas) {

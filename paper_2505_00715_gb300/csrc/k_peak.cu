@@ -78,14 +78,52 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_fma64(double *out, int it
     if (r == 12345.678) out[blockIdx.x] = r;
 }
 
+// FP64 point pairs of the far field (single layer), the inner operation of
+// the plain FP64 form: r = |y - x|, exp(-Re(sigma) r), sin and cos of
+// Im(sigma) r, weight / r, complex accumulate.  4 independent chains per
+// thread, the distance of each chain moving every step so that nothing is
+// loop invariant: 4 * kPeakPairUnroll pairs per iteration.
+constexpr int kPeakPairUnroll = 2;
+__global__ void __launch_bounds__(kPeakThreads) k_peak_pair64(double *out, int iters) {
+    double x[4], are[4], aim[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        x[c] = 0.05 + 1e-4 * (threadIdx.x + 64 * c);
+        are[c] = aim[c] = 0.0;
+    }
+    const double sr = 3.7, si = 21.3, y = 0.3, z = 0.2, w = 1e-3;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kPeakPairUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const double r = sqrt(x[c] * x[c] + y * y + z * z);
+                const double ea = exp(-sr * r);
+                double sn, cs;
+                sincos(si * r, &sn, &cs);
+                const double wr = w / r;
+                are[c] += wr * ea * cs;
+                aim[c] -= wr * ea * sn;
+                x[c] += 1e-7;
+            }
+    }
+    double r = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r += are[c] + aim[c];
+    if (r == 12345.678) out[blockIdx.x] = r;
+}
+
 }  // namespace
 
-// Launches one microbenchmark (what: 0 FP32 FMA, 1 SFU, 2 FP64 FMA) on
-// `grid` CTAs; returns the operations it performs (an FMA counts as one).
+// Launches one microbenchmark (what: 0 FP32 FMA, 1 SFU, 2 FP64 FMA, 3 FP64
+// point pairs) on `grid` CTAs; returns the operations it performs (an FMA
+// counts as one, a point pair as one).
 int td_launch_peak(cudaStream_t st, int what, int grid, int iters, void *out, double *ops) {
-    const double per_thread = (double)iters * kPeakUnroll * 8;
+    const double per_thread = what == 3 ? (double)iters * kPeakPairUnroll * 4 : (double)iters * kPeakUnroll * 8;
     *ops = per_thread * kPeakThreads * grid;
-    if (what == 0)
+    if (what == 3)
+        k_peak_pair64<<<grid, kPeakThreads, 0, st>>>((double *)out, iters);
+    else if (what == 0)
         k_peak_fma32<<<grid, kPeakThreads, 0, st>>>((float *)out, iters);
     else if (what == 1)
         k_peak_sfu<<<grid, kPeakThreads, 0, st>>>((float *)out, iters);

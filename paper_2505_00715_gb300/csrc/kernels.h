@@ -75,6 +75,9 @@ int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const Tenso
                        const AcaParams &p, void *scratch, int64_t scratch_per_cta, int nctas);
 int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
                       const TensorOut &o, const AcaParams &p, int nctas, int nt);
+// k_aca.cu: entries by the far-field engine's point-pair groups (fibres, tubes)
+int td_launch_fibre_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, const int *rows,
+                            int64_t nr, const int *cols, int64_t nc, int64_t nf, void *out, int num_sms);
 int td_launch_bdf2(cudaStream_t st, int N, double dt, double lam, double *ds);
 int td_launch_gcq(cudaStream_t st, int NQ, double dt_min, double q, double *ds, double *dw);
 

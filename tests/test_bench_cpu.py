@@ -37,3 +37,24 @@ def test_roofline_arithmetic():
     assert r["peak"] == 4.0 and abs(r["frac"] - r["achieved"] / 4.0) < 1e-15
     r2 = bench.roofline(st, cfg, blocks, peaks, "measured", {"sm_mhz": 2000.0}, "x", None)
     assert abs(r2["peak"] - 16 * 152 * 2000e6 / 1e12) < 1e-12
+
+
+def test_oracle_samples_are_stratified_and_disjoint():
+    rng = np.random.default_rng(0)
+    nb = 1000
+    i0 = rng.integers(0, 100, nb)
+    blocks = np.stack([i0, i0 + rng.integers(1, 300, nb), i0, i0 + rng.integers(1, 300, nb),
+                       rng.integers(0, 2, nb)], axis=1).astype(np.int32)
+    masks = []
+    for off in range(5):
+        m, k = bench.oracle_sample_mask(blocks, 24, off)
+        assert k == -(-nb // 24) and m.sum() == -(-nb // k)
+        masks.append(m)
+        # one block from each stratum of k blocks in decreasing size order
+        sz = (blocks[:, 1] - blocks[:, 0]).astype(np.int64) * (blocks[:, 3] - blocks[:, 2])
+        order = np.lexsort((np.arange(nb), -sz))
+        for a in range(0, nb, k):
+            assert m[order[a:a + k]].sum() == 1
+    assert not np.any(np.sum(masks, axis=0) > 1)  # disjoint samples
+    m2, _ = bench.oracle_sample_mask(blocks, 24, 3)
+    assert np.array_equal(m2, masks[3])  # deterministic

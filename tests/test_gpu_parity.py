@@ -64,7 +64,7 @@ def test_freqs_bdf2(td, ctx, orc, N, dt):
 @pytest.mark.parametrize("rk,NQ", [(1, 256), (0, 64)])
 def test_freqs_gcq(td, ctx, orc, rk, NQ):
     dts = graded_steps(256, 1.01, 0.015)
-    f = td.Freqs.gcq(ctx, dts.min(), dts.max(), rk, NQ)
+    f = td.Freqs.gcq(ctx, dts, rk, NQ)
     s, w, _ = orc.freqs_gcq(dts.min(), dts.max(), rk, NQ)
     assert np.max(np.abs(f.s - s)) <= 1e-12 * np.max(np.abs(s))
     assert np.max(np.abs(f.w - w)) <= 1e-12 * np.max(np.abs(w))
