@@ -54,6 +54,9 @@ WORKLOADS = {
     # finned machine housings (c = 343 m/s) with the gCQ contour of 2-stage Radau
     # IIA over geometrically graded steps (T = 0.015 s); 512 steps are graded so
     # that dt_max / dt_min equals that of 256 steps of ratio 1.01
+    # a smaller housing of the same recipe (9024 triangles): one-launch profiling captures
+    "housing9k_slp_gcq256": dict(housing=10000, op="SLP", gcq=(256, 1.01, 0.015), leaf=64, eta=2.0, eps=1e-4,
+                                 eps_aca=1e-6, ng=5, nrhs=16, c=343.0),
     "housing30k_slp_gcq256": dict(housing=30000, op="SLP", gcq=(256, 1.01, 0.015), leaf=64, eta=2.0, eps=1e-4,
                                   eps_aca=1e-6, ng=5, nrhs=16, c=343.0),
     "housing60k_slp_gcq256": dict(housing=60000, op="SLP", gcq=(256, 1.01, 0.015), leaf=64, eta=2.0, eps=1e-4,

@@ -119,6 +119,16 @@ const char *tdbem_last_error(tdbem_ctx_t ctx);
 /* Block until all work of the context's stream has finished; TDBEM_ERR_CUDA
  * if a tensor-core wait of an earlier asynchronous call gave up. */
 int tdbem_ctx_sync(tdbem_ctx_t ctx);
+/* Poll limit of every wait of the tensor-core kernels (tdbem_zgemm and the
+ * mixed-form weighted apply) on their MMA completion barrier; 0 restores the
+ * default (2^24 polls, far above any MMA group's latency).  A wait that
+ * reaches the limit gives up: the kernel records the failure, waits (with
+ * the default limit) for the MMAs it has issued, frees its tensor memory and
+ * returns; the call's result is then invalid and tdbem_ctx_sync (or
+ * tdbem_zgemm itself) returns TDBEM_ERR_CUDA.  The context stays usable.
+ * A small limit exists to exercise that path.  TDBEM_ERR_ARG if polls < 0
+ * or polls >= 2^31. */
+int tdbem_ctx_set_wait_limit(tdbem_ctx_t ctx, int64_t polls);
 /* Size in bytes of the buffer in which tdbem_compress forms and compresses
  * the near-field tensor, batch by batch of near blocks (default 16 GiB; a
  * block larger than the buffer forms a batch of its own).  TDBEM_ERR_ARG if

@@ -40,6 +40,7 @@ def lib():
             "orc_pair_regular": (None, [vp, i32, i64, i64, d, d, d, vp]),
             "orc_entry": (None, [vp, i32, i64, i64, d, d, d, i32, vp]),
             "orc_entries": (None, [vp, i32, vp, i64, vp, i64, vp, i64, d, i32, vp]),
+            "orc_entries_mag": (None, [vp, i32, vp, i64, vp, i64, vp, i64, d, i32, vp]),
             "orc_freqs_bdf2": (i32, [i32, d, d, vp]),
             "orc_ellipk": (d, [d]),
             "orc_ellipj": (None, [d, d, vp, vp, vp]),
@@ -122,6 +123,17 @@ class Mesh:
         out = np.zeros((len(s), len(rows), len(cols)), dtype=np.complex128)
         lib().orc_entries(self.h, op, _p(rows), len(rows), _p(cols), len(cols), _p(s), len(s), c, ng,
                           _p(out))
+        return out
+
+    def entries_mag(self, op, rows, cols, s, c=1.0, ng=6):
+        """Magnitude sums [nf, nr, nc] (real) of the entries: the same
+        quadrature with every term replaced by a bound of its modulus."""
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        s = _c128(np.atleast_1d(s))
+        out = np.zeros((len(s), len(rows), len(cols)))
+        lib().orc_entries_mag(self.h, op, _p(rows), len(rows), _p(cols), len(cols), _p(s), len(s), c, ng,
+                              _p(out))
         return out
 
     def dense_apply_rows(self, op, s, rows, W, c=1.0, ng=6, nthreads=0):

@@ -76,6 +76,17 @@ void orc_entries(const orc_mesh *m, int op, const int32_t *rows, int64_t nr,
                  const int32_t *cols, int64_t nc, const double *s /*[2*nf]*/, int64_t nf,
                  double c, int ng, double *out);
 
+/* Magnitude sums out[f][r][c] (real): the quadrature of orc_entries with
+ * every term replaced by a bound of its modulus, |exp(-s r/c)|/(4 pi r) for
+ * the single layer and |exp(-s r/c)(1 + s r/c)|/(4 pi r^2) for the double
+ * layer (|(x - y).n_y| <= |x - y|).  A floating-point evaluation of an entry
+ * can only be accurate relative to this sum: rounding in each term is
+ * relative to its bound, and the terms may cancel.  For the single layer at
+ * real s every term is positive and the sum equals |entry|. */
+void orc_entries_mag(const orc_mesh *m, int op, const int32_t *rows, int64_t nr,
+                     const int32_t *cols, int64_t nc, const double *s /*[2*nf]*/, int64_t nf,
+                     double c, int ng, double *out);
+
 /* ---- frequency sets (App. A; BDF2 CQ) ---- */
 /* BDF2 convolution quadrature: s_k = delta(lambda e^{2 pi i k/N})/dt,
  * delta(z) = (1-z) + (1-z)^2/2, k = 0..N-1.  lambda <= 0 picks

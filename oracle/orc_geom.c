@@ -183,6 +183,17 @@ static cplx k_dlp(const double *d, const double *ny, cplx sc) {
     double r = sqrt(dot3(d, d));
     return cexp(-sc * r) * (1.0 + sc * r) * (-dot3(d, ny)) / (FOUR_PI * r * r * r);
 }
+/* Modulus bounds of the kernels (for the magnitude sums, see orc_entries_mag):
+ * |exp(-s r/c)| / (4 pi r), and |exp(-s r/c)(1 + s r/c)| r / (4 pi r^3), the
+ * double layer with |(x-y).n_y| replaced by its bound |x - y|. */
+static double k_slp_mag(const double *d, cplx sc) {
+    double r = sqrt(dot3(d, d));
+    return exp(-creal(sc) * r) / (FOUR_PI * r);
+}
+static double k_dlp_mag(const double *d, cplx sc) {
+    double r = sqrt(dot3(d, d));
+    return cabs(cexp(-sc * r) * (1.0 + sc * r)) / (FOUR_PI * r * r);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Pair classification and parametrisation                                   */
@@ -253,12 +264,12 @@ static void chi(const param_tri *p, double x1, double x2, double *o) {
 
 /* Accumulate weight * kernel * basis into out[3] (mesh-local trial vertex).
  * For SLP only out[0] is used. */
-static void accum(int op, const double *d, const double *ny, cplx sc, double wgt,
+static void accum(int op, int mag, const double *d, const double *ny, cplx sc, double wgt,
                   const param_tri *pb, double y1, double y2, cplx *out) {
     if (op == ORC_SLP) {
-        out[0] += wgt * k_slp(d, sc);
+        out[0] += mag ? wgt * k_slp_mag(d, sc) : wgt * k_slp(d, sc);
     } else {
-        cplx k = wgt * k_dlp(d, ny, sc);
+        cplx k = mag ? wgt * k_dlp_mag(d, sc) : wgt * k_dlp(d, ny, sc);
         double lam[3] = {1.0 - y1, y1 - y2, y2};
         for (int q = 0; q < 3; ++q) out[pb->loc[q]] += k * lam[q];
     }
@@ -275,7 +286,7 @@ static const double SECT[6][2][2] = {{{1, 0}, {1, 1}},   {{1, 1}, {0, 1}},
                                      {{0, 1}, {-1, 0}},  {{-1, 0}, {-1, -1}},
                                      {{-1, -1}, {0, -1}}, {{0, -1}, {1, 0}}};
 
-static void pair_identical(const orc_mesh *m, int op, int64_t ti, const param_tri *pa,
+static void pair_identical(const orc_mesh *m, int op, int mag, int64_t ti, const param_tri *pa,
                            cplx sc, int ng, const double *gx, const double *gw, cplx *out) {
     (void)op;
     double g = 2.0 * m->area[ti];
@@ -292,7 +303,7 @@ static void pair_identical(const orc_mesh *m, int op, int64_t ti, const param_tr
                 double d[3];
                 for (int k = 0; k < 3; ++k) d[k] = xi * (z1 * e1[k] + z2 * e2[k]);
                 double wgt = gw[a] * gw[b] * xi * (1.0 - xi) * (1.0 - xi) * 0.5;
-                acc += wgt * k_slp(d, sc);
+                acc += mag ? wgt * k_slp_mag(d, sc) : wgt * k_slp(d, sc);
             }
     out[0] += g * g * acc;
 }
@@ -314,7 +325,7 @@ static double det3(const double a[3], const double b[3], const double c[3]) {
            a[2] * (b[0] * c[1] - b[1] * c[0]);
 }
 
-static void pair_edge(const orc_mesh *m, int op, int64_t ti, int64_t tj, const param_tri *pa,
+static void pair_edge(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj, const param_tri *pa,
                       const param_tri *pb, cplx sc, int ng, const double *gx, const double *gw,
                       cplx *out) {
     double g = 4.0 * m->area[ti] * m->area[tj];
@@ -342,7 +353,7 @@ static void pair_edge(const orc_mesh *m, int op, int64_t ti, int64_t tj, const p
                     double tlo = p > q - u ? p : q - u;
                     double thi = u > 0.0 ? 1.0 - u : 1.0;
                     double tm = 0.5 * (tlo + thi);
-                    accum(op, d, ny, sc, wgt, pb, tm + u, q, acc);
+                    accum(op, mag, d, ny, sc, wgt, pb, tm + u, q, acc);
                 }
     }
     for (int k = 0; k < 3; ++k) out[k] += g * acc[k];
@@ -352,7 +363,7 @@ static void pair_edge(const orc_mesh *m, int op, int64_t ti, int64_t tj, const p
 /* Shared vertex P0.  Split on which of xh1, yh1 is larger; the larger one is
  * xi and the other triangle is the Duffy image of the unit square scaled by
  * xi: xh = xi (1, w), yh = xi (e1, e1 e2) (and swapped), weight xi^3 e1. */
-static void pair_vertex(const orc_mesh *m, int op, int64_t ti, int64_t tj, const param_tri *pa,
+static void pair_vertex(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj, const param_tri *pa,
                         const param_tri *pb, cplx sc, int ng, const double *gx, const double *gw,
                         cplx *out) {
     double g = 4.0 * m->area[ti] * m->area[tj];
@@ -381,13 +392,13 @@ static void pair_vertex(const orc_mesh *m, int op, int64_t ti, int64_t tj, const
                         chi(pb, y1, y2, y);
                         sub3(y, x, d);
                         double wgt = gw[a] * gw[b] * gw[cidx] * gw[dd] * xi * xi * xi * e1;
-                        accum(op, d, ny, sc, wgt, pb, y1, y2, acc);
+                        accum(op, mag, d, ny, sc, wgt, pb, y1, y2, acc);
                     }
     for (int k = 0; k < 3; ++k) out[k] += g * acc[k];
 }
 
 /* ---- regular pairs: 7 x 7 rule --------------------------------------------- */
-static void pair_regular(const orc_mesh *m, int op, int64_t ti, int64_t tj, cplx sc, cplx *out) {
+static void pair_regular(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj, cplx sc, cplx *out) {
     double bary[7][3], w[7];
     orc_rule7(&bary[0][0], w);
     const double *ny = m->nrm + 3 * tj;
@@ -404,9 +415,9 @@ static void pair_regular(const orc_mesh *m, int op, int64_t ti, int64_t tj, cplx
             sub3(y, x, d);
             double wgt = w[a] * w[b] * scale;
             if (op == ORC_SLP) {
-                out[0] += wgt * k_slp(d, sc);
+                out[0] += mag ? wgt * k_slp_mag(d, sc) : wgt * k_slp(d, sc);
             } else {
-                cplx k = wgt * k_dlp(d, ny, sc);
+                cplx k = mag ? wgt * k_dlp_mag(d, sc) : wgt * k_dlp(d, ny, sc);
                 for (int q = 0; q < 3; ++q) out[q] += k * bary[b][q];
             }
         }
@@ -416,16 +427,15 @@ static void pair_regular(const orc_mesh *m, int op, int64_t ti, int64_t tj, cplx
 void orc_pair_regular(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re,
                       double s_im, double c, double *o) {
     cplx out[3] = {0, 0, 0};
-    pair_regular(m, op, ti, tj, (s_re + I * s_im) / c, out);
+    pair_regular(m, op, 0, ti, tj, (s_re + I * s_im) / c, out);
     for (int k = 0; k < 3; ++k) {
         o[2 * k] = creal(out[k]);
         o[2 * k + 1] = cimag(out[k]);
     }
 }
 
-int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, double s_im,
-             double c, int ng, double *o) {
-    cplx sc = (s_re + I * s_im) / c;
+/* Pair integral (mag = 0) or its magnitude sum (mag = 1) into out[3]. */
+static int pair_any(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj, cplx sc, int ng, cplx *out) {
     /* the Galerkin single layer is symmetric: integrate each unordered pair
      * once, in the order (lower index, higher index) */
     if (op == ORC_SLP && ti > tj) {
@@ -433,7 +443,6 @@ int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, dou
         ti = tj;
         tj = t;
     }
-    cplx out[3] = {0, 0, 0};
     param_tri pa, pb;
     int cls = classify(m, ti, tj, &pa, &pb);
     double gx[64], gw[64];
@@ -441,12 +450,19 @@ int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, dou
     switch (cls) {
     case 3:
         /* flat panel: (x - y).n_y = 0, the double layer vanishes identically */
-        if (op == ORC_SLP) pair_identical(m, op, ti, &pa, sc, ng, gx, gw, out);
+        if (op == ORC_SLP) pair_identical(m, op, mag, ti, &pa, sc, ng, gx, gw, out);
         break;
-    case 2: pair_edge(m, op, ti, tj, &pa, &pb, sc, ng, gx, gw, out); break;
-    case 1: pair_vertex(m, op, ti, tj, &pa, &pb, sc, ng, gx, gw, out); break;
-    default: pair_regular(m, op, ti, tj, sc, out); break;
+    case 2: pair_edge(m, op, mag, ti, tj, &pa, &pb, sc, ng, gx, gw, out); break;
+    case 1: pair_vertex(m, op, mag, ti, tj, &pa, &pb, sc, ng, gx, gw, out); break;
+    default: pair_regular(m, op, mag, ti, tj, sc, out); break;
     }
+    return cls;
+}
+
+int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, double s_im,
+             double c, int ng, double *o) {
+    cplx out[3] = {0, 0, 0};
+    int cls = pair_any(m, op, 0, ti, tj, (s_re + I * s_im) / c, ng, out);
     for (int k = 0; k < 3; ++k) {
         o[2 * k] = creal(out[k]);
         o[2 * k + 1] = cimag(out[k]);
@@ -482,4 +498,33 @@ void orc_entries(const orc_mesh *m, int op, const int32_t *rows, int64_t nr, con
             for (int64_t q = 0; q < nc; ++q)
                 orc_entry(m, op, rows[r], cols[q], s[2 * f], s[2 * f + 1], c, ng,
                           out + 2 * ((f * nr + r) * nc + q));
+}
+
+/* Magnitude sum of an entry: the same quadrature (7 x 7 rule or
+ * Sauter-Schwab points, same weights and P1 hat weights) with every term
+ * replaced by a bound of its modulus, |exp(-s r/c)| / (4 pi r) for the single
+ * layer and |exp(-s r/c)(1 + s r/c)| / (4 pi r^2) for the double layer (the
+ * factor |(x - y).n_y| bounded by |x - y|). */
+static double entry_mag(const orc_mesh *m, int op, int64_t row, int64_t col, cplx sc, int ng) {
+    if (op == ORC_SLP) {
+        cplx out[3] = {0, 0, 0};
+        pair_any(m, op, 1, row, col, sc, ng, out);
+        return creal(out[0]);
+    }
+    double acc = 0.0;
+    for (int64_t p = m->v2t_ptr[col]; p < m->v2t_ptr[col + 1]; ++p) {
+        cplx out[3] = {0, 0, 0};
+        pair_any(m, op, 1, row, m->v2t[p], sc, ng, out);
+        acc += creal(out[m->v2t_loc[p]]);
+    }
+    return acc;
+}
+
+void orc_entries_mag(const orc_mesh *m, int op, const int32_t *rows, int64_t nr, const int32_t *cols,
+                     int64_t nc, const double *s, int64_t nf, double c, int ng, double *out) {
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+    for (int64_t f = 0; f < nf; ++f)
+        for (int64_t r = 0; r < nr; ++r)
+            for (int64_t q = 0; q < nc; ++q)
+                out[(f * nr + r) * nc + q] = entry_mag(m, op, rows[r], cols[q], (s[2 * f] + I * s[2 * f + 1]) / c, ng);
 }

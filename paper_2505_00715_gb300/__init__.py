@@ -73,6 +73,10 @@ class Context:
         """Scale of the far part of the first face-pool size in compress."""
         self.check(self.L.tdbem_ctx_set_pool_scale(self.h, float(scale)), "tdbem_ctx_set_pool_scale")
 
+    def set_wait_limit(self, polls):
+        """Poll limit of the tensor-core waits (0: default); see tdbem_ctx_set_wait_limit."""
+        self.check(self.L.tdbem_ctx_set_wait_limit(self.h, int(polls)), "tdbem_ctx_set_wait_limit")
+
     def set_near_batch(self, nbytes):
         """Buffer size (bytes) of the batched near-field tensor in compress."""
         self.check(self.L.tdbem_ctx_set_near_batch(self.h, int(nbytes)), "tdbem_ctx_set_near_batch")

@@ -53,6 +53,7 @@ EXPORTS = {
     "tdbem_last_error": (C.c_char_p, [C.c_void_p]),
     "tdbem_ctx_sync": (C.c_int, [C.c_void_p]),
     "tdbem_ctx_set_near_batch": (C.c_int, [C.c_void_p, C.c_int64]),
+    "tdbem_ctx_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "tdbem_ctx_set_pool_scale": (C.c_int, [C.c_void_p, C.c_double]),
     "tdbem_measure_peak": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "tdbem_mesh_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,

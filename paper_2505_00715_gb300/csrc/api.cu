@@ -235,6 +235,13 @@ extern "C" int tdbem_measure_peak(tdbem_ctx_t ctx, int32_t what, double *ops_per
     return TDBEM_OK;
 }
 
+extern "C" int tdbem_ctx_set_wait_limit(tdbem_ctx_t ctx, int64_t polls) {
+    if (!ctx) return TDBEM_ERR_ARG;
+    if (polls < 0 || polls > INT32_MAX) return td_fail(ctx, TDBEM_ERR_ARG, "wait limit must be in 0..2^31-1");
+    ctx->wait_polls = (uint32_t)polls;
+    return TDBEM_OK;
+}
+
 extern "C" int tdbem_ctx_set_pool_scale(tdbem_ctx_t ctx, double scale) {
     if (!ctx) return TDBEM_ERR_ARG;
     if (!(scale > 0.0)) return td_fail(ctx, TDBEM_ERR_ARG, "pool scale must be > 0");
@@ -1376,7 +1383,7 @@ int apply_tc(tdbem_tensor *t, const void *W, int nrhs, void *y) {
     const int64_t *zbase = (const int64_t *)(mem + t->plan_off[3]);
     int e = td_launch_zgemm_apply(ctx->stream, groups, rowtab, t->dpartner, (const c32 *)t->dfib, (const c32 *)W,
                                   t->dperm_c, (c32 *)t->plan_Z, t->Nu, nrhs, t->ncols, t->NQ, jobs, t->plan_njobs,
-                                  ctx->dflags, ctx->num_sms);
+                                  ctx->dflags, ctx->wait_polls, ctx->num_sms);
     if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "tensor-core contraction failed: %s", cudaGetErrorString((cudaError_t)e));
     ApplyZArgs a{};
     a.nb = (int)t->nblocks;
@@ -1617,7 +1624,7 @@ extern "C" int tdbem_zgemm(tdbem_ctx_t ctx, int32_t M, int32_t N, int32_t K, con
         rc = td_fail(ctx, TDBEM_ERR_CUDA, "tdbem_zgemm: upload failed");
     if (!rc) {
         int e = td_launch_zgemm_dense(ctx->stream, (const c32 *)A, lda, (const c32 *)B, ldb, (c32 *)D, ldd, M, N, K,
-                                      dj, (int)jobs.size(), ctx->dflags, ctx->num_sms);
+                                      dj, (int)jobs.size(), ctx->dflags, ctx->wait_polls, ctx->num_sms);
         if (e) rc = td_fail(ctx, TDBEM_ERR_CUDA, "tdbem_zgemm: launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
     if (!rc) rc = tdbem_ctx_sync(ctx);

@@ -21,6 +21,7 @@ struct tdbem_ctx {
     std::string err;
     int num_sms = 0;
     int *dflags = nullptr;  // device status word of asynchronous kernels (TD_DEV_* bits)
+    uint32_t wait_polls = 0;  // poll limit of the tensor-core waits (0: the kernels' default)
 };
 
 // Host-side planner output for the cluster trees and the block list.

@@ -38,7 +38,7 @@ constexpr int kABytes = kTM * 2 * kTK * 2;     // one split part of A: 32 KB
 constexpr int kBBytes = 2 * kTN * 2 * kTK * 2; // one split part of B: 64 KB
 constexpr int kSmemBytes = 2 * kABytes + 2 * kBBytes + 1024 + 64;
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kMaxPolls = 1u << 24;
+constexpr uint32_t kMaxPolls = 1u << 24;  // default poll limit of a tensor-core wait
 
 struct SplitPack {
     uint4 hi, lo;
@@ -124,7 +124,8 @@ struct ApplyOps {
 };
 
 template <class Ops>
-__global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs, int njobs, int K, int *err) {
+__global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs, int njobs, int K, int *err,
+                                                        uint32_t max_polls) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // 1024-byte aligned operand region
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                 }
                 tc_commit(bar);
             }
-            const bool ok = mbar_wait(bar, phase, kMaxPolls);
+            const bool ok = mbar_wait(bar, phase, max_polls);
             phase ^= 1u;
             failed = __syncthreads_or(!ok) != 0;
             tc_fence_after();
@@ -262,28 +263,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
 }
 
 template <class Ops>
-int launch_zgemm(cudaStream_t st, const Ops &ops, const ZJob *jobs, int njobs, int K, int *err, int num_sms) {
+int launch_zgemm(cudaStream_t st, const Ops &ops, const ZJob *jobs, int njobs, int K, int *err, uint32_t max_polls,
+                 int num_sms) {
     if (njobs == 0) return 0;
     cudaError_t e = cudaFuncSetAttribute(k_zgemm<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int grid = std::min(njobs, num_sms);
-    k_zgemm<Ops><<<grid, kThreads, kSmemBytes, st>>>(ops, jobs, njobs, K, err);
+    k_zgemm<Ops><<<grid, kThreads, kSmemBytes, st>>>(ops, jobs, njobs, K, err, max_polls ? max_polls : kMaxPolls);
     return (int)cudaGetLastError();
 }
 
 }  // namespace
 
 int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 *B, int64_t ldb, c32 *D, int64_t ldd,
-                          int M, int N, int K, const ZJob *jobs, int njobs, int *err, int num_sms) {
+                          int M, int N, int K, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
+                          int num_sms) {
     DenseOps ops{A, B, D, lda, ldb, ldd, M, N};
-    return launch_zgemm(st, ops, jobs, njobs, K, err, num_sms);
+    return launch_zgemm(st, ops, jobs, njobs, K, err, max_polls, num_sms);
 }
 
 int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap, const c32 *fib,
                           const c32 *W, const int *perm_c, c32 *Z, int Nu, int nrhs, int64_t ncols, int NQ,
-                          const ZJob *jobs, int njobs, int *err, int num_sms) {
+                          const ZJob *jobs, int njobs, int *err, uint32_t max_polls, int num_sms) {
     ApplyOps ops{groups, rowtab, qmap, fib, W, perm_c, Z, Nu, nrhs, ncols};
-    return launch_zgemm(st, ops, jobs, njobs, NQ, err, num_sms);
+    return launch_zgemm(st, ops, jobs, njobs, NQ, err, max_polls, num_sms);
 }
 
 int td_zgemm_tile_rows() { return kTM; }

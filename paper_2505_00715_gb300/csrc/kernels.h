@@ -99,6 +99,8 @@ struct ApplyArgs {
 int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorOut &o, int num_sms);
 
 // ---- tensor-core complex GEMM (k_zgemm.cu) and the apply built on it ----
+// max_polls: poll limit of each tensor-core wait (0: the default); a wait that
+// gives up sets TD_DEV_TIMEOUT in *err, lets its MMAs finish and returns
 struct ZJob {               // one output tile
     int g, m0, n0, pad;     // group, first row, first complex column
 };
@@ -109,10 +111,11 @@ struct ZGroup {             // rows (block, term, half) that share a column clus
     int L, pad;             // Z row length = nJ * nrhs
 };
 int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 *B, int64_t ldb, c32 *D, int64_t ldd,
-                          int M, int N, int K, const ZJob *jobs, int njobs, int *err, int num_sms);
+                          int M, int N, int K, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
+                          int num_sms);
 int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap, const c32 *fib,
                           const c32 *W, const int *perm_c, c32 *Z, int Nu, int nrhs, int64_t ncols, int NQ,
-                          const ZJob *jobs, int njobs, int *err, int num_sms);
+                          const ZJob *jobs, int njobs, int *err, uint32_t max_polls, int num_sms);
 int td_zgemm_tile_rows();
 int td_zgemm_tile_cols();
 

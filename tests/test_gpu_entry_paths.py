@@ -12,9 +12,15 @@ oracle at 1e-5 (mixed form) and 1e-12 (FP64 form), on the 320-triangle sphere
 of 2-stage Radau IIA over 256 graded steps), where the phases s r / c reach
 tens of radians.
 
-Relative error of an entry: |g - o| / max(|o|, 1e-6 * scale_k), scale_k the
-largest entry of the operator's frequency slice A(s_k) (a self-interaction
-entry; FP32 underflows exp(-Re(s) r / c) for the largest Re(s) r / c).
+Relative error of an entry: |g - o| / max(M, 1e-6 * scale_k), M the oracle's
+magnitude sum of the entry (the same quadrature with every term replaced by a
+bound of its modulus; |(x - y).n_y| bounded by |x - y| for the double layer)
+and scale_k the largest magnitude sum of a self-interaction entry of the
+sampled rows at s_k.  For the single layer at real s, M = |o|.  An entry's
+terms may cancel (oscillating phases; the double-layer factor (x - y).n_y on
+nearly flat neighbourhoods), and floating-point evaluation in either
+precision is accurate only relative to M; the floor covers FP32 underflow of
+exp(-Re(s) r / c).
 """
 import numpy as np
 import pytest
@@ -75,16 +81,22 @@ def _own_dof(k, op, rows):
 
 
 def _scale(k, orc, op, rows, fidx):
-    """Largest |A(s_k)| over the self-interaction entries of the given rows."""
+    """Largest magnitude sum over the self-interaction entries of the rows."""
     own = _own_dof(k, op, rows)
-    diag = np.stack([np.abs(k.om.entries(getattr(orc, op), [r], [q], k.f.s[fidx], c=k.c, ng=5)[:, 0, 0])
+    diag = np.stack([k.om.entries_mag(getattr(orc, op), [r], [q], k.f.s[fidx], c=k.c, ng=5)[:, 0, 0]
                      for r, q in zip(rows[:8], own[:8])], axis=1)
     return diag.max(axis=1)
 
 
-def _rel_err(g, o, scale):
-    den = np.maximum(np.abs(o), 1e-6 * scale.reshape((-1,) + (1,) * (o.ndim - 1)))
+def _rel_err(g, o, mag, scale):
+    den = np.maximum(mag, 1e-6 * scale.reshape((-1,) + (1,) * (o.ndim - 1)))
     return np.abs(g - o) / den
+
+
+def _oracle(k, orc, op, rows, cols, fidx):
+    o = k.om.entries(getattr(orc, op), rows, cols, k.f.s[fidx], c=k.c, ng=5)
+    mag = k.om.entries_mag(getattr(orc, op), rows, cols, k.f.s[fidx], c=k.c, ng=5)
+    return o, mag, _scale(k, orc, op, rows, fidx)
 
 
 def _near_strip(td, k, op):
@@ -131,8 +143,8 @@ def test_near_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     fidx = k.fidx if (mesh == "sphere" or op == "SLP") else k.fidx[::2]
     g = td.entries(k.gm, getattr(td, op), k.f, rows, cols, fidx, prec=getattr(td, prec), c=k.c, ng=5,
                    path=td.PATH_NEAR).cpu().numpy()
-    o = k.om.entries(getattr(orc, op), rows, cols, k.f.s[fidx], c=k.c, ng=5)
-    err = _rel_err(g, o, _scale(k, orc, op, rows, fidx))
+    o, mag, sc = _oracle(k, orc, op, rows, cols, fidx)
+    err = _rel_err(g, o, mag, sc)
     touch = np.broadcast_to(_touch_mask(k, rows, cols, op), err.shape)
     e_t, e_r = float(err[touch].max()), float(err[~touch].max())
     print("near path %s %s %s: %d x %d x %d entries, max rel err touching %.2e, regular %.2e"
@@ -152,8 +164,8 @@ def test_generic_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     fidx = k.fidx[::2]
     g = td.entries(k.gm, getattr(td, op), k.f, rows, cols, fidx, prec=getattr(td, prec), c=k.c,
                    ng=5).cpu().numpy()
-    o = k.om.entries(getattr(orc, op), rows, cols, k.f.s[fidx], c=k.c, ng=5)
-    err = float(_rel_err(g, o, _scale(k, orc, op, rows, fidx)).max())
+    o, mag, sc = _oracle(k, orc, op, rows, cols, fidx)
+    err = float(_rel_err(g, o, mag, sc).max())
     print("generic path %s %s %s: max rel err %.2e" % (mesh, op, prec, err))
     assert err <= TOL[prec], err
 
@@ -181,8 +193,8 @@ def test_fibre_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
         assert not _touch_mask(k, rows, cols, op).any()
         g = td.entries(k.gm, getattr(td, op), k.f, rows, cols, k.fidx, prec=getattr(td, prec), c=k.c, ng=5,
                        path=td.PATH_FIBRE).cpu().numpy()
-        o = k.om.entries(getattr(orc, op), rows, cols, k.f.s[k.fidx], c=k.c, ng=5)
-        worst = max(worst, float(_rel_err(g, o, _scale(k, orc, op, rows, k.fidx)).max()))
+        o, mag, sc = _oracle(k, orc, op, rows, cols, k.fidx)
+        worst = max(worst, float(_rel_err(g, o, mag, sc).max()))
     print("fibre path %s %s %s: max rel err %.2e over %d far blocks" % (mesh, op, prec, worst, len(pick)))
     assert worst <= TOL[prec], worst
 

@@ -54,3 +54,29 @@ def test_zgemm_scales_and_zero_k(td, ctx):
                  torch.zeros((0, 5), dtype=torch.complex64, device="cuda")).cpu().numpy()
     assert np.all(Z == 0)
     ctx.sync()
+
+
+def test_tensor_core_wait_gives_up_and_context_stays_usable(td, ctx):
+    """Failure detection of the bounded tensor-core waits: with a poll limit
+    of 1 every wait on the MMA completion barrier gives up before the MMAs
+    finish; the kernel records the failure, lets its own MMAs finish, frees
+    its tensor memory and returns, and the call reports TDBEM_ERR_CUDA.  With
+    the default limit restored the same context computes correctly again."""
+    import torch
+    rng = np.random.default_rng(4)
+    A, B = _rand(rng, (256, 192)), _rand(rng, (192, 256))
+    At, Bt = torch.as_tensor(A, device="cuda"), torch.as_tensor(B, device="cuda")
+    ctx.set_wait_limit(1)
+    try:
+        with pytest.raises(td.TdbemError) as ei:
+            td.zgemm(ctx, At, Bt)
+        assert "gave up" in str(ei.value)
+    finally:
+        ctx.set_wait_limit(0)
+    ctx.sync()  # the status word was cleared by the failing call
+    D = td.zgemm(ctx, At, Bt).cpu().numpy()
+    ref = A.astype(np.complex128) @ B.astype(np.complex128)
+    bound = 8e-5 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64))
+    assert np.all(np.abs(D - ref) <= bound)
+    with pytest.raises(td.TdbemError):
+        ctx.set_wait_limit(-1)

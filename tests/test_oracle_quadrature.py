@@ -180,3 +180,51 @@ def test_octahedron_brute_force_dense(orc):
                     ref = pair_brute_regular(V[T[i]], V[T[j]], s, "slp", level=2, n=5)[0]
                     tol = 2e-3  # the 7x7 rule itself on touching-distance pairs
                 assert abs(A[i, j] - ref) <= tol * abs(ref), (i, j, shared)
+
+
+# ---------------------------------------------------------------- magnitude sums
+def test_magnitude_sums_equal_modulus_for_positive_terms(orc, sphere1):
+    """Single layer at real s: every quadrature term is positive, so the
+    magnitude sum equals |entry| (touching and regular pairs alike)."""
+    V, T, m = sphere1
+    rows = np.array([0, 3, 7], dtype=np.int32)
+    cols = np.arange(len(T), dtype=np.int32)
+    for s in (0.0, 2.5):
+        a = m.entries(orc.SLP, rows, cols, [s], c=1.0, ng=6)
+        g = m.entries_mag(orc.SLP, rows, cols, [s], c=1.0, ng=6)
+        assert np.max(np.abs(g - np.abs(a)) / np.abs(a)) < 1e-13
+
+
+@pytest.mark.parametrize("op", ["SLP", "DLP"])
+def test_magnitude_sums_bound_the_entries(orc, sphere1, op):
+    """Triangle inequality: the magnitude sum bounds |entry| at complex s,
+    and for the double layer the bound is strict on curved neighbours."""
+    V, T, m = sphere1
+    rows = np.array([0, 5, 11], dtype=np.int32)
+    cols = np.arange(len(T) if op == "SLP" else len(V), dtype=np.int32)
+    s = [1.5 + 7.0j, 0.3 - 2.0j]
+    a = m.entries(getattr(orc, op), rows, cols, s, c=1.0, ng=6)
+    g = m.entries_mag(getattr(orc, op), rows, cols, s, c=1.0, ng=6)
+    assert np.all(g >= np.abs(a) * (1 - 1e-12))
+    assert np.all(g > 0)
+    if op == "DLP":
+        assert np.median(g / np.maximum(np.abs(a), 1e-300)) > 1.5
+
+
+def test_dlp_magnitude_of_stacked_small_triangles(orc):
+    """Two small parallel triangles a distance R apart, one above the other:
+    |x - y| and |(x - y).n_y| agree to O((h/R)^2), so the double-layer entry
+    summed over the trial hats and its magnitude sum both approach the
+    far-field value |T0| |T1| |exp(-sR)(1 + sR)| / (4 pi R^2)."""
+    h, R = 1e-2, 1.0
+    P = np.array([[0.0, 0.0, 0.0], [h, 0.0, 0.0], [0.0, h, 0.0]])
+    V = np.vstack([P, P + [0.0, 0.0, R]])
+    T = np.array([[0, 1, 2], [3, 4, 5]], dtype=np.int32)  # both normals +z
+    m = orc.Mesh(V, T)
+    s = 3.0 + 4.0j
+    ent = m.entries(orc.DLP, [0], [3, 4, 5], [s], c=1.0, ng=6)[0, 0].sum()
+    mag = m.entries_mag(orc.DLP, [0], [3, 4, 5], [s], c=1.0, ng=6)[0, 0].sum()
+    area = 0.5 * h * h
+    far = area * area * abs(np.exp(-s * R) * (1 + s * R)) / (4 * np.pi * R * R)
+    assert abs(abs(ent) - mag) <= 1e-3 * mag
+    assert abs(mag - far) <= 1e-3 * far
