@@ -308,6 +308,16 @@ constexpr int kDenseS = 1600;
 template <class T>
 using AccT = T;
 
+// Terms of Algorithm 1 whose Gram matrix <H_d, H_d'> a far-field CTA keeps
+// (the norm of the frequency slice C^(l-1)(k_l) is formed from it).
+constexpr int kGmax = 24;
+// Rounding floor of the mixed form's FP32 residual faces, relative to the
+// frequency slice they were subtracted from: the residual of term l is
+// A(k_l) - C^(l-1)(k_l) minus the face's own terms, every one stored and
+// summed in FP32 (unit roundoff 2^-24, a few hundred terms).  Face ACA steps
+// below 2^-20 ||C^(l-1)(k_l)||_F are rounding noise, not residual.
+constexpr double kFp32Floor = 9.5367431640625e-07;  // 2^-20
+
 // Fixed shared state of one far-field CTA.
 template <class T>
 struct FarShared {
@@ -322,6 +332,8 @@ struct FarShared {
     cx<T> coef[kNCoef];
     const cx<T> *base[kNCoef];
     cx<T> part[256];  // partial corrections of the thread groups (correct_fibre)
+    AccT<T> gre[kGmax][kGmax], gim[kGmax][kGmax];  // <H_d, H_d'> of the block's kept terms
+    double floor2;  // mixed form: (2^-20 ||C^(l-1)(k_l)||_F)^2, the face ACA's noise floor (0: none)
 };
 
 // Per-frequency arrays of one far-field CTA, carved from dynamic shared memory
@@ -701,7 +713,24 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             }
             __syncthreads();
             int kf = 0, istar = 0, par = 0;
-            if (tid == 0) S.normS2 = 0.0;
+            if (tid == 0) {
+                S.normS2 = 0.0;
+                // mixed form: ||C^(l-1)(k)||_F^2 = sum_{d,d'} f_d[k] conj(f_d'[k]) <H_d, H_d'>
+                double c2 = 0.0;
+                if (std::is_same<T, float>::value && l <= kGmax) {
+                    for (int d = 0; d < l; ++d) {
+                        const cx<T> fd = fib[(tb + d) * Nu + k];
+                        for (int e = 0; e < l; ++e) {
+                            const cx<T> fe = fib[(tb + e) * Nu + k];
+                            // Re(fd conj(fe) G[d][e])
+                            const double pr = (double)fd.x * fe.x + (double)fd.y * fe.y;
+                            const double pi = (double)fd.y * fe.x - (double)fd.x * fe.y;
+                            c2 += pr * S.gre[d][e] - pi * S.gim[d][e];
+                        }
+                    }
+                }
+                S.floor2 = kFp32Floor * kFp32Floor * fmax(c2, 0.0);
+            }
             int pend0 = 0;  // first ACA step whose norm terms are not yet summed
             const int kp = (a.kpred && !a.harvest) ? min(a.kpred[tb + k], p.kcap) : 0;
             bool converged = false;
@@ -803,7 +832,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                                 t1 += S.red3[par][w][1];
                                 t2 += S.red3[par][w][2];
                             }
-                            st = (double)t1 * (double)t2 <= p.eps_aca * p.eps_aca * (double)t0;  // squared test, no FP64 sqrt
+                            // squared test, no FP64 sqrt; the mixed form also stops at its rounding floor
+                            st = (double)t1 * (double)t2 <= fmax(p.eps_aca * p.eps_aca * (double)t0, S.floor2);
                         }
                         stop = __shfl_sync(0xffffffffu, st, 0) != 0;
                     }
@@ -972,7 +1002,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     for (int t = pend0; t <= kf; ++t) {
                         const double uu = S.nu[t], vv = S.nv[t];
                         n2 += 2.0 * (double)S.nrow[t] + uu * vv;
-                        if (uu * vv <= p.eps_aca * p.eps_aca * n2) {
+                        if (uu * vv <= fmax(p.eps_aca * p.eps_aca * n2, S.floor2)) {
                             kstop = t;
                             break;
                         }
@@ -1147,6 +1177,14 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             copy_cols(pool + off, Uw, a.maxI, kf, nI);
             copy_cols(pool + off + (int64_t)kf * nI, Vw, a.maxJ, kf, nJ);
             for (int kk = tid; kk < Nu; kk += blockDim.x) fib[(tb + l) * Nu + kk] = F.fl[kk];
+            if (l < kGmax)
+                for (int d = tid; d <= l; d += blockDim.x) {
+                    // <H_l, H_d> and <H_d, H_l> = conj
+                    S.gre[l][d] = F.gH[2 * d];
+                    S.gim[l][d] = F.gH[2 * d + 1];
+                    S.gre[d][l] = F.gH[2 * d];
+                    S.gim[d][l] = -F.gH[2 * d + 1];
+                }
             if (tid == 0) {
                 o.kpiv[tb + l] = k;
                 o.frank[tb + l] = kf;
