@@ -171,7 +171,7 @@ def oracle_problem(cfg):
     if "gcq" in cfg:
         nq, ratio, T_end = cfg["gcq"]
         dts = graded_steps(nq, ratio, T_end)
-        s, _, _ = orc.freqs_gcq(dts.min(), dts.max(), 1, nq)
+        s, _, _ = orc.freqs_gcq(dts.min(), dts.max(), 1, nq, len(dts))
         su = s[:nq // 2]  # points l and NQ-1-l are conjugate
     else:
         s = orc.freqs_bdf2(cfg["N"], cfg["dt"])

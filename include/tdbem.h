@@ -162,7 +162,12 @@ int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double lambda, td
  * the steps through dt_min = min(dts) and dt_max = max(dts) (App. A); the
  * steps are kept with the set (tdbem_freqs_steps).  Computed in FP64 on the
  * device (Jacobi elliptic functions by the AGM).  q = 1 is lifted to 1.01
- * (App. A, last paragraph). */
+ * (App. A, last paragraph).  The contour is the circle through 0 and
+ * 2 rho / dt_min: rho = 1 for EULER (as printed in App. A); for RADAU2 the
+ * smallest rho >= sqrt(6) (every resolvent pole 1/(dt lambda_i(A)) inside)
+ * in steps of 5 % with max |R(dt_min s)|^N <= 1e4 along the circle, R the
+ * stability function, so that the Runge-Kutta stages of the N steps
+ * (eq. gCQ_xn) stay bounded on the contour. */
 int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ, tdbem_freqs_t *out);
 /* The time steps of a gCQ set (host [N], nullable) and their count *N
  * (nullable); a BDF2 set returns N = 0. */

@@ -111,7 +111,40 @@ void orc_ellipj_complex(double u, double v, double m, double *sn, double *cn, do
     dn[1] = -m * s * c * s1 / D;
 }
 
-int orc_freqs_gcq(double dt_min, double dt_max, int rk, int NQ, double *s, double *w,
+/* Stability function of the Runge-Kutta method, R(z) = 1 + z b^T (I - z A)^{-1} 1:
+ * implicit Euler 1/(1 - z); 2-stage Radau IIA (1 + z/3)/(1 - 2z/3 + z^2/6). */
+static cplx rk_stability(int rk, cplx z) {
+    if (rk == 1) return (1.0 + z / 3.0) / (1.0 - 2.0 * z / 3.0 + z * z / 6.0);
+    return 1.0 / (1.0 - z);
+}
+
+/* Radius factor rho of the contour (the circle through 0 and 2 rho / dt_min):
+ * the gCQ steps (eq. gCQ_xn) need a contour that encloses every resolvent pole
+ * 1/(dt lambda_i(A)), which takes rho > 1 / (2 min_i Re lambda_i) and holds
+ * for rho = 1 / min_i |lambda_i|; and the Runge-Kutta stages of the N steps
+ * grow along the contour like max |R(dt_min s)|^N, which must stay bounded
+ * (<= 1e4 here) for the quadrature sums not to cancel away in FP64.  For
+ * implicit Euler |R| = 1 on the circle of rho = 1 (the printed contour);
+ * for Radau IIA rho grows from sqrt(6) in steps of 5 % until the bound holds
+ * on 4096 points of the circle. */
+double orc_gcq_radius(int rk, int nsteps) {
+    if (rk != 1) return 1.0;
+    const double pi = acos(-1.0);
+    double rho = sqrt(6.0);
+    for (int it = 0; it < 400; ++it) {
+        double mx = 0.0;
+        for (int j = 1; j < 4096; ++j) {
+            cplx z = rho * (1.0 + cexp(I * (2.0 * pi * j / 4096.0)));
+            double a = cabs(rk_stability(rk, z));
+            if (a > mx) mx = a;
+        }
+        if ((double)(nsteps > 1 ? nsteps : 1) * log(mx) <= log(1e4)) return rho;
+        rho *= 1.05;
+    }
+    return rho;
+}
+
+int orc_freqs_gcq(double dt_min, double dt_max, int rk, int nsteps, int NQ, double *s, double *w,
                   double *info) {
     if (!(dt_min > 0.0) || !(dt_max >= dt_min) || NQ < 2) return -1;
     double q = dt_max / dt_min;
@@ -121,12 +154,16 @@ int orc_freqs_gcq(double dt_min, double dt_max, int rk, int NQ, double *s, doubl
         q = 1.01;
         lifted = 1;
     }
+    const double rho = orc_gcq_radius(rk, nsteps);
     const double pi = acos(-1.0);
     double r = sqrt(2.0 * q - 1.0);
     double k = (q - r) / (q + r);
     double m = k * k;
     double K = orc_ellipk(m), Kp = orc_ellipk(1.0 - m);
-    double scale = 1.0 / (dt_min * (q - 1.0));
+    /* Reading of App. A: gamma and gamma' take dt_min / rho (orc_gcq_radius);
+     * with dt_min as printed the circle misses the Radau IIA poles
+     * (2 -/+ i sqrt(2))/dt of steps below 1.5 dt_min. */
+    double scale = rho / (dt_min * (q - 1.0));
     for (int l = 1; l <= NQ; ++l) {
         double u = -K + (l - 0.5) * 4.0 * K / NQ, v = 0.5 * Kp;
         double snr[2], cnr[2], dnr[2];
@@ -147,6 +184,7 @@ int orc_freqs_gcq(double dt_min, double dt_max, int rk, int NQ, double *s, doubl
         info[1] = k;
         info[2] = K;
         info[3] = Kp;
+        info[4] = rho;
     }
     return lifted;
 }

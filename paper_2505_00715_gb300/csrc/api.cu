@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -412,6 +413,33 @@ extern "C" int64_t tdbem_mesh_ndof(tdbem_mesh_t m, int32_t basis) {
 // ============================================================================
 // frequencies
 // ============================================================================
+// Radius factor of the gCQ contour (App. A, as read here): the gCQ steps
+// (eq. gCQ_xn) need a contour around every pole 1/(dt lambda_i(A)) of the
+// Runge-Kutta resolvents (I - dt s A)^{-1}, i.e. rho >= 1 / min_i |lambda_i|,
+// and the stages of the N steps grow along it like max|R(dt_min s)|^N, R the
+// stability function, which must stay bounded (1e4) for the quadrature sums
+// to keep their digits.  Implicit Euler: |R| = 1 on the circle of rho = 1
+// (the contour as printed).  2-stage Radau IIA, R(z) = (1 + z/3) / (1 - 2z/3 +
+// z^2/6): rho starts at sqrt(6) and grows by 5 % until the bound holds on 4096
+// points of the circle z = rho (1 + e^{i theta}).
+double td_gcq_radius(int rk, int nsteps) {
+    if (rk != TDBEM_RADAU2) return 1.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    double rho = std::sqrt(6.0);
+    for (int it = 0; it < 400; ++it) {
+        double mx = 0.0;
+        for (int j = 1; j < 4096; ++j) {
+            const double th = two_pi * j / 4096.0;
+            const std::complex<double> z = rho * std::complex<double>(1.0 + std::cos(th), std::sin(th));
+            const std::complex<double> R = (1.0 + z / 3.0) / (1.0 - 2.0 * z / 3.0 + z * z / 6.0);
+            mx = std::max(mx, std::abs(R));
+        }
+        if (std::max(nsteps, 1) * std::log(mx) <= std::log(1e4)) return rho;
+        rho *= 1.05;
+    }
+    return rho;
+}
+
 namespace {
 int finish_freqs(tdbem_ctx *ctx, tdbem_freqs *f) {
     TD_CUDA(ctx, cudaMemcpyAsync(f->s.data(), f->ds, sizeof(double) * 2 * f->NQ, cudaMemcpyDeviceToHost, ctx->stream));
@@ -494,7 +522,11 @@ extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, in
         return rc;
     }
     f->dw = f->ds + 2 * NQ;
-    if (td_launch_gcq(ctx->stream, NQ, dt_min, q, f->ds, f->dw) || (rc = finish_freqs(ctx, f))) {
+    // the contour is built for dt_min / rho (td_gcq_radius): a circle through 0
+    // and 2 rho / dt_min around every resolvent pole of the steps
+    const double rho = td_gcq_radius(rk, N);
+    f->rho = rho;
+    if (td_launch_gcq(ctx->stream, NQ, dt_min / rho, q, f->ds, f->dw) || (rc = finish_freqs(ctx, f))) {
         cudaFree(f->ds);
         delete f;
         return rc ? rc : td_fail(ctx, TDBEM_ERR_CUDA, "gCQ frequency kernel failed");

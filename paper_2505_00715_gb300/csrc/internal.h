@@ -76,6 +76,7 @@ struct tdbem_freqs {
     double *dw = nullptr;
     int kind = 0;                 // 0 BDF2, 1 gCQ
     std::vector<double> dts;      // gCQ: the time steps the contour was built for
+    double rho = 1.0;             // gCQ: radius factor of the contour (td_gcq_radius)
 };
 
 // Compressed tensor (device pools + host copies of the small metadata).
@@ -137,6 +138,9 @@ MeshDev td_mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double 
 // noalloc.cu: device address of the allocation-free entry point's scratch on
 // the current device `device` (once per device, cached)
 int td_noalloc_setup(int device);
+
+// api.cu: radius factor of the gCQ contour for nsteps steps of method rk
+double td_gcq_radius(int rk, int nsteps);
 
 // planner.cpp
 void td_plan_tree(const tdbem_mesh *m, int basis, int leaf, HostTree &t);

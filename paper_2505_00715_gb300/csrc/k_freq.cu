@@ -13,7 +13,9 @@
 //   clockwise).  K by the arithmetic-geometric mean, sn/cn/dn of real
 //   argument by the descending Landen sequence, complex argument by the
 //   addition formulas with the complementary parameter (Abramowitz-Stegun
-//   16.4, 16.21).
+//   16.4, 16.21).  The caller passes dt_min / rho (td_gcq_radius), so that
+//   the circle through 0 and 2 rho / dt_min encloses every resolvent pole
+//   1/(dt lambda_i(A)) of the steps.
 #include "common.cuh"
 #include "internal.h"
 

@@ -65,7 +65,7 @@ def test_freqs_bdf2(td, ctx, orc, N, dt):
 def test_freqs_gcq(td, ctx, orc, rk, NQ):
     dts = graded_steps(256, 1.01, 0.015)
     f = td.Freqs.gcq(ctx, dts, rk, NQ)
-    s, w, _ = orc.freqs_gcq(dts.min(), dts.max(), rk, NQ)
+    s, w, _ = orc.freqs_gcq(dts.min(), dts.max(), rk, NQ, len(dts))
     assert np.max(np.abs(f.s - s)) <= 1e-12 * np.max(np.abs(s))
     assert np.max(np.abs(f.w - w)) <= 1e-12 * np.max(np.abs(w))
     assert f.Nu == NQ // 2

@@ -78,46 +78,72 @@ def _radau_eigs():
     return np.linalg.eigvals(A)
 
 
-@pytest.mark.parametrize("rk,ratio", [(1, 12.6), (1, 1.0), (0, 12.6)])
-def test_gcq_contour_cauchy(orc, rk, ratio):
+def _stability(z, rk):
+    """R(z) = 1 + z b^T (I - z A)^{-1} 1 from the Butcher tableau."""
+    if rk == 0:
+        A, b = np.array([[1.0]]), np.array([1.0])
+    else:
+        A, b = np.array([[5 / 12, -1 / 12], [3 / 4, 1 / 4]]), np.array([3 / 4, 1 / 4])
+    m = len(b)
+    return np.array([1 + zz * b @ np.linalg.solve(np.eye(m) - zz * A, np.ones(m)) for zz in np.atleast_1d(z)])
+
+
+@pytest.mark.parametrize("rk,ratio,nsteps", [(1, 12.6, 256), (1, 1.0, 10), (1, 12.6, 1), (0, 12.6, 256)])
+def test_gcq_contour_cauchy(orc, rk, ratio, nsteps):
     """The quadrature sum w_l g(s_l) ~ (1/2 pi i) oint g ds (positive
     orientation) reproduces the Cauchy formula for g = 1/(s - z): winding
-    number 1 for the implicit-Euler resolvent poles z = 1/dt of every step
-    size in [dt_min, dt_max] and for the Radau IIA poles 1/(dt_max lambda(A)),
-    0 for points outside.  The set is symmetric under conjugation and lies in
-    the right half plane."""
+    number 1 at every resolvent pole of the steps, z = 1/dt (implicit Euler)
+    and z = 1/(dt lambda_i(A)) (Radau IIA) for dt in [dt_min, dt_max]; 0 for
+    points outside.  The set is symmetric under conjugation and lies in the
+    right half plane."""
     dt_min = 1e-3
     dt_max = dt_min * ratio
-    NQ = 128
-    s, w, info = orc.freqs_gcq(dt_min, dt_max, rk, NQ)
+    NQ = 256
+    s, w, info = orc.freqs_gcq(dt_min, dt_max, rk, NQ, nsteps)
     assert np.all(s.real > 0)
     assert np.allclose(s, np.conj(s[::-1]), rtol=1e-12)
     inside = [1.0 / dt for dt in np.geomspace(dt_min, dt_max, 5)]
-    if rk == 1 and ratio > 2:
-        # (for dt close to dt_min the Radau poles (2 -/+ 1.41i)/dt lie outside
-        # the circle of radius 1/dt_min; the formula of App. A is kept as printed)
-        inside += list(1.0 / (dt_max * _radau_eigs()))
+    if rk == 1:
+        inside += [z for dt in np.geomspace(dt_min, dt_max, 5) for z in 1.0 / (dt * _radau_eigs())]
     for z in inside:
         val = np.sum(w / (s - z))
         assert abs(val - 1.0) < 1e-6, (z, val)
-    for z in (-10.0 / dt_min, 1e3 / dt_min, 1e2 / dt_min * 1j):
+    R = info["rho"] / dt_min
+    for z in (-10.0 / dt_min, 3 * R, 2 * R * 1j):
         assert abs(np.sum(w / (s - z))) < 1e-6
     assert info["lifted"] == (rk == 0 and ratio == 1.0)
 
 
-def test_gcq_contour_is_circle_through_0_and_2_over_dtmin(orc):
-    """gamma maps Im sigma = K'/2 onto the circle |s - 1/dt_min| = 1/dt_min
-    (sn(+-K + i K'/2) = +-1/sqrt(k) gives gamma = 2/dt_min and 0); q only
-    changes how the points cluster towards 0."""
-    for rk, ratio in ((1, 12.6), (0, 3.0)):
-        dt_min = 2e-3
-        s, w, info = orc.freqs_gcq(dt_min, ratio * dt_min, rk, 64)
-        r = np.abs(s - 1.0 / dt_min)
-        assert np.max(np.abs(r - 1.0 / dt_min)) < 1e-9 / dt_min
-        # clustering: more points near 0 for larger q
-        assert np.sum(s.real < 0.25 / dt_min) > np.sum(s.real > 1.75 / dt_min)
+@pytest.mark.parametrize("rk,nsteps", [(1, 1), (1, 10), (1, 64), (1, 512), (0, 512)])
+def test_gcq_contour_radius(orc, rk, nsteps):
+    """The circle |s - R| = R, R = rho / dt_min (gamma maps Im sigma = K'/2
+    onto it: sn(+-K + i K'/2) = +-1/sqrt(k) gives gamma = 2R and 0; q only
+    clusters the points towards 0).  rho = 1 for implicit Euler (|R(dt s)| = 1
+    on the whole circle); for Radau IIA rho >= 1/min|lambda_i(A)| = sqrt(6)
+    (the poles inside) and the Runge-Kutta stages grow by at most 1e4 over the
+    nsteps steps along the contour, max |R(dt_min s_l)|^nsteps <= 1e4, with a
+    radius 5 % smaller violating that bound unless rho = sqrt(6)."""
+    dt_min = 2e-3
+    s, w, info = orc.freqs_gcq(dt_min, 12.6 * dt_min, rk, 256, nsteps)
+    rho = info["rho"]
+    R = rho / dt_min
+    assert np.max(np.abs(np.abs(s - R) - R)) < 1e-9 * R
+    assert np.sum(s.real < 0.25 * R) > np.sum(s.real > 1.75 * R)
+    if rk == 0:
+        assert rho == 1.0
+        assert np.allclose(np.abs(_stability(dt_min * s, 0)), 1.0, rtol=1e-9)
+        return
+    assert rho >= np.sqrt(6.0) - 1e-12
+    th = 2 * np.pi * np.arange(1, 4096) / 4096
+    grow = np.max(np.abs(_stability(rho * (1 + np.exp(1j * th)), 1)))
+    assert nsteps * np.log(grow) <= np.log(1e4) + 1e-9
+    assert nsteps * np.log(np.max(np.abs(_stability(dt_min * s, 1)))) <= np.log(1e4) + 1e-6
+    if rho > np.sqrt(6.0) + 1e-9:
+        smaller = np.max(np.abs(_stability(rho / 1.05 * (1 + np.exp(1j * th)), 1)))
+        assert nsteps * np.log(smaller) > np.log(1e4)
+    assert orc.gcq_radius(rk, nsteps) == rho
 
 
 def test_gcq_degenerate_q_lifted(orc):
-    s, w, info = orc.freqs_gcq(1e-3, 1e-3, 0, 32)
+    s, w, info = orc.freqs_gcq(1e-3, 1e-3, 0, 32, 4)
     assert info["lifted"] and info["q"] > 1.0 and np.all(np.isfinite(s))
