@@ -74,7 +74,7 @@ def workload_freqs(td, ctx, cfg):
     if "gcq" in cfg:
         nq, ratio, T_end = cfg["gcq"]
         dts = graded_steps(nq, ratio, T_end)
-        return td.Freqs.gcq(ctx, dts, td.RADAU2, nq)
+        return td.Freqs.gcq(ctx, dts, td.RADAU2, nq, rho=1.0)
     return td.Freqs.bdf2(ctx, cfg["N"], cfg["dt"])
 
 
@@ -171,7 +171,7 @@ def oracle_problem(cfg):
     if "gcq" in cfg:
         nq, ratio, T_end = cfg["gcq"]
         dts = graded_steps(nq, ratio, T_end)
-        s, _, _ = orc.freqs_gcq(dts.min(), dts.max(), 1, nq, len(dts))
+        s, _, _ = orc.freqs_gcq(dts.min(), dts.max(), 1, nq, len(dts), rho=1.0)
         su = s[:nq // 2]  # points l and NQ-1-l are conjugate
     else:
         s = orc.freqs_bdf2(cfg["N"], cfg["dt"])

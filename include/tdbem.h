@@ -121,7 +121,8 @@ const char *tdbem_last_error(tdbem_ctx_t ctx);
 int tdbem_ctx_sync(tdbem_ctx_t ctx);
 /* Poll limit of every wait of the tensor-core kernels (tdbem_zgemm and the
  * mixed-form weighted apply) on their MMA completion barrier; 0 restores the
- * default (2^24 polls, far above any MMA group's latency).  A wait that
+ * default (2^24 polls of a blocking try-wait, far above any MMA group's
+ * latency); a smaller limit counts non-blocking tests of the barrier.  A wait that
  * reaches the limit gives up: the kernel records the failure, waits (with
  * the default limit) for the MMAs it has issued, frees its tensor memory and
  * returns; the call's result is then invalid and tdbem_ctx_sync (or
@@ -163,12 +164,16 @@ int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double lambda, td
  * steps are kept with the set (tdbem_freqs_steps).  Computed in FP64 on the
  * device (Jacobi elliptic functions by the AGM).  q = 1 is lifted to 1.01
  * (App. A, last paragraph).  The contour is the circle through 0 and
- * 2 rho / dt_min: rho = 1 for EULER (as printed in App. A); for RADAU2 the
- * smallest rho >= sqrt(6) (every resolvent pole 1/(dt lambda_i(A)) inside)
- * in steps of 5 % with max |R(dt_min s)|^N <= 1e4 along the circle, R the
- * stability function, so that the Runge-Kutta stages of the N steps
- * (eq. gCQ_xn) stay bounded on the contour. */
-int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ, tdbem_freqs_t *out);
+ * 2 rho / dt_min:
+ *   rho > 0: that factor; rho = 1 is App. A as printed;
+ *   rho <= 0: the radius the gCQ marching needs (tdbem_march_*): 1 for
+ *     EULER; for RADAU2 the smallest rho >= sqrt(6) (every resolvent pole
+ *     1/(dt lambda_i(A)) inside) in steps of 5 % with max |R(dt_min s)|^N
+ *     <= 1e4 along the circle, R the stability function, so that the
+ *     Runge-Kutta stages of the N steps (eq. gCQ_xn) stay bounded on it.
+ * ERR_ARG for a non-finite rho. */
+int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ, double rho,
+                    tdbem_freqs_t *out);
 /* The time steps of a gCQ set (host [N], nullable) and their count *N
  * (nullable); a BDF2 set returns N = 0. */
 int tdbem_freqs_steps(tdbem_freqs_t f, double *dts, int32_t *N);
@@ -180,6 +185,11 @@ int tdbem_freqs_steps(tdbem_freqs_t f, double *dts, int32_t *N);
  * (conjugate) as  rep + 1 (same) or -(rep + 1) (conjugate). */
 int tdbem_freqs_get(tdbem_freqs_t f, double *s, double *w, int32_t *NQ, int32_t *Nu,
                     int32_t *unique);
+/* A frequency set of explicit points s (host [2 * NQ], every Re s > 0) and
+ * optional weights w (host [2 * NQ], nullable: zeros).  Points whose
+ * conjugate is also in the set are paired (the tensor is built over one of
+ * each pair).  For the step operators of the gCQ marching. */
+int tdbem_freqs_points(tdbem_ctx_t ctx, const double *s, const double *w, int32_t NQ, tdbem_freqs_t *out);
 int tdbem_freqs_destroy(tdbem_freqs_t f);
 
 /* ---- cluster tree and block cluster tree (Sec. 4, eq. admissible) ---------- */
@@ -348,6 +358,45 @@ int tdbem_measure_peak(tdbem_ctx_t ctx, int32_t what, double *ops_per_s);
  * complex values of device scratch per call and synchronises the stream. */
 int tdbem_solve(tdbem_tensor_t t, int32_t fidx, const void *b, int32_t nrhs, void *x, double tol, int32_t maxit,
                 int32_t restart, int32_t *iters, double *relres);
+
+/* ---- gCQ time marching (Sec. 3 "Temporal discretisation", eqs. gCQ_xn and
+ * gcq_formula; App. A) ----------------------------------------------------
+ * The direct Dirichlet problem of Sec. 2 in Galerkin form (P0 test):
+ *   V * q = (1/2 M + K) * g,   M[i][v] = int_{tau_i} phi_v,
+ * g the Dirichlet data (P1 nodal values), q the Neumann data (P0), marched
+ * with the Runge-Kutta based gCQ (rk = TDBEM_EULER or TDBEM_RADAU2) over the
+ * steps dts.  Step n:
+ *   x_{n-1}(s_l) = (I - dt_{n-1} s_l A)^{-1} ((b^T A^{-1} x_{n-2}(s_l)) 1 + dt_{n-1} A q_{n-1})
+ *   V((dt_n A)^{-1}) q_n = 1/2 M g_n + K((dt_n A)^{-1}) g_n
+ *                          + sum_l K(s_l) W_l[g] - sum_l V(s_l) W_l[q],
+ *   W_l = omega_l (b^T A^{-1} x_{n-1}(s_l)) (I - dt_n s_l A)^{-1} 1,
+ * omega_l = -w_l (w_l the positively oriented weights of tdbem_freqs_get).
+ * The history sums are tdbem_apply_weighted on V and K, tensors compressed
+ * over one gCQ contour (tdbem_freqs_gcq with the same steps); the step
+ * operators at the matrix argument act through the eigenvalues mu_k =
+ * 1/(dt lambda_k(A)) and run on Vstep and Kstep, tensors over a frequency set
+ * holding every mu_k of the steps (tdbem_march_step_points, then
+ * tdbem_freqs_points): tdbem_apply_freq for K, restarted GMRES
+ * (tdbem_solve) for V.  All four tensors: one mesh, precision and wave speed;
+ * V and Vstep single layer (P0 x P0), K and Kstep double layer (P0 x P1).
+ * The marching keeps FP64 states x(s_l) of q and g at the unique contour
+ * points (Nu * (nt + nv) * m * nrhs complex128) and weighted data in the
+ * tensors' precision (NQ * (nt + nv) * m * nrhs complex values). */
+typedef struct tdbem_march *tdbem_march_t;
+/* The distinct step frequencies 1/(dt_n lambda_k(A)) of the steps (host
+ * outputs): s (nullable) [2 * count] interleaved, *count. */
+int tdbem_march_step_points(const double *dts, int32_t N, int32_t rk, double *s, int32_t *count);
+/* m * nrhs <= 64 (m = 1 for EULER, 2 for RADAU2).  TDBEM_ERR_ARG for tensors
+ * that do not match the description above. */
+int tdbem_march_create(tdbem_tensor_t V, tdbem_tensor_t K, tdbem_tensor_t Vstep, tdbem_tensor_t Kstep,
+                       const double *dts, int32_t N, int32_t rk, int32_t nrhs, tdbem_march_t *out);
+/* One step: g device FP64 [nv][m][nrhs] (Dirichlet data at the stage times
+ * t_{n-1} + c_i dt_n), q device FP64 [nt][m][nrhs] (output, Neumann data at
+ * the stage times).  tol, maxit: GMRES of the step system (relative
+ * residual per column).  iters (nullable): GMRES steps taken.  Synchronous;
+ * TDBEM_ERR_NOT_CONVERGED from the solve, TDBEM_ERR_ARG after N steps. */
+int tdbem_march_step(tdbem_march_t mh, const double *g, double *q, double tol, int32_t maxit, int32_t *iters);
+int tdbem_march_destroy(tdbem_march_t mh);
 
 /* ---- persistence (not part of the paper) ------------------------------------
  * tdbem_tensor_save writes the compressed tensor (block list, permutations,

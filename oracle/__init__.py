@@ -45,7 +45,7 @@ def lib():
             "orc_ellipk": (d, [d]),
             "orc_ellipj": (None, [d, d, vp, vp, vp]),
             "orc_ellipj_complex": (None, [d, d, d, vp, vp, vp]),
-            "orc_freqs_gcq": (i32, [d, d, i32, i32, i32, vp, vp, vp]),
+            "orc_freqs_gcq": (i32, [d, d, i32, i32, d, i32, vp, vp, vp]),
             "orc_gcq_radius": (d, [i32, i32]),
             "orc_tree_build": (vp, [vp, i32, i32, i32, d]),
             "orc_tree_free": (None, [vp]),
@@ -187,13 +187,15 @@ def ellipj_complex(z, m):
     return complex(*sn), complex(*cn), complex(*dn)
 
 
-def freqs_gcq(dt_min, dt_max, rk, NQ, nsteps):
+def freqs_gcq(dt_min, dt_max, rk, NQ, nsteps, rho=0.0):
     """gCQ contour points and weights (App. A) for nsteps steps in
-    [dt_min, dt_max]; rk 0 implicit Euler, 1 Radau IIA (2 stages)."""
+    [dt_min, dt_max]; rk 0 implicit Euler, 1 Radau IIA (2 stages).  rho > 0:
+    the circle through 0 and 2 rho / dt_min (rho = 1: as printed); rho <= 0:
+    the radius that the marching needs (orc_gcq_radius)."""
     s = np.zeros(NQ, dtype=np.complex128)
     w = np.zeros(NQ, dtype=np.complex128)
     info = np.zeros(5)
-    rc = lib().orc_freqs_gcq(dt_min, dt_max, rk, nsteps, NQ, _p(s), _p(w), _p(info))
+    rc = lib().orc_freqs_gcq(dt_min, dt_max, rk, nsteps, float(rho), NQ, _p(s), _p(w), _p(info))
     if rc < 0:
         raise ValueError("bad gCQ parameters")
     return s, w, dict(q=info[0], k=info[1], K=info[2], Kp=info[3], rho=info[4], lifted=bool(rc))

@@ -116,13 +116,14 @@ def convolve(op, q, dts, rk, s, w):
     A, _, _ = rk_tableau(rk)
     N, n, m = q.shape
     H = History(s, w, A, (n,))
-    out = np.zeros((N, n, m), dtype=np.complex128)
+    out = []
     for k in range(N):
+        v = apply_matrix_arg(op, dts[k], A, q[k])
         if k >= 1:
             H.advance(dts[k - 1], q[k - 1])
-            out[k] = history_sum(op, s, H.weights(dts[k]))
-        out[k] += apply_matrix_arg(op, dts[k], A, q[k])
-    return out
+            v = v + history_sum(op, s, H.weights(dts[k]))
+        out.append(v)
+    return np.stack(out)
 
 
 def solve(opV, f, dts, rk, s, w):
@@ -181,3 +182,19 @@ def pulse_flux(y, n, t, x_src, c=1.0):
     r = np.linalg.norm(d, axis=-1)
     f, fp = pulse(t - r / c, c)
     return -(fp / (c * r) + f / (r * r)) * np.sum(d * n, axis=-1) / r
+
+
+class CachedOperator:
+    """s -> dense operator matrix, computed once per frequency (conjugate
+    frequencies by conjugation, A(conj s) = conj A(s))."""
+
+    def __init__(self, fn):
+        self.fn, self.cache = fn, {}
+
+    def __call__(self, s):
+        s = complex(s)
+        key = (round(s.real, 12), round(abs(s.imag), 12))
+        if key not in self.cache:
+            self.cache[key] = (s, self.fn(complex(s.real, abs(s.imag))))
+        _, M = self.cache[key]
+        return M if s.imag >= 0 else np.conj(M)

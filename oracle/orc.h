@@ -101,15 +101,16 @@ void orc_ellipj(double u, double m, double *sn, double *cn, double *dn);
 void orc_ellipj_complex(double u, double v, double m, double *sn, double *cn, double *dn);
 /* gCQ contour points and weights (App. A): rk = 0 implicit Euler, 1 Radau IIA
  * (2 stages), for nsteps steps in [dt_min, dt_max].  The circle passes through
- * 0 and 2 rho / dt_min, rho = orc_gcq_radius(rk, nsteps): it encloses every
+ * 0 and 2 rho / dt_min with rho = rho_in if rho_in > 0 (rho_in = 1: App. A as
+ * printed), else rho = orc_gcq_radius(rk, nsteps), which encloses every
  * resolvent pole 1/(dt lambda_i(A)) and keeps max |R(dt_min s)|^nsteps <= 1e4
- * along it (rho = 1, the printed contour, for implicit Euler).  s, w: [2*NQ];
+ * along the circle (rho = 1 for implicit Euler).  s, w: [2*NQ];
  * the weights are those of the positively oriented Cauchy integral.  info
  * (nullable) [5]: q, k, K(k^2), K'(k^2), rho.  Returns 0, or 1 if q had to be
  * lifted off the q = 1 degeneracy. */
 double orc_gcq_radius(int rk, int nsteps);
-int orc_freqs_gcq(double dt_min, double dt_max, int rk, int nsteps, int NQ, double *s, double *w,
-                  double *info);
+int orc_freqs_gcq(double dt_min, double dt_max, int rk, int nsteps, double rho_in, int NQ, double *s,
+                  double *w, double *info);
 
 /* ---- cluster tree and block cluster tree (Sec. 4, eq. admissible) ---- */
 typedef struct orc_tree orc_tree;

@@ -144,8 +144,8 @@ double orc_gcq_radius(int rk, int nsteps) {
     return rho;
 }
 
-int orc_freqs_gcq(double dt_min, double dt_max, int rk, int nsteps, int NQ, double *s, double *w,
-                  double *info) {
+int orc_freqs_gcq(double dt_min, double dt_max, int rk, int nsteps, double rho_in, int NQ, double *s,
+                  double *w, double *info) {
     if (!(dt_min > 0.0) || !(dt_max >= dt_min) || NQ < 2) return -1;
     double q = dt_max / dt_min;
     if (rk == 1) q *= 5.0; /* Radau IIA, 2 stages: |lambda_1| = |lambda_2| */
@@ -154,7 +154,7 @@ int orc_freqs_gcq(double dt_min, double dt_max, int rk, int nsteps, int NQ, doub
         q = 1.01;
         lifted = 1;
     }
-    const double rho = orc_gcq_radius(rk, nsteps);
+    const double rho = rho_in > 0.0 ? rho_in : orc_gcq_radius(rk, nsteps);
     const double pi = acos(-1.0);
     double r = sqrt(2.0 * q - 1.0);
     double k = (q - r) / (q + r);

@@ -19,7 +19,7 @@ from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
 
 __all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "PATH_GENERIC", "PATH_NEAR",
            "PATH_FIBRE", "compress", "harvest", "rank_bin", "autotune",
-           "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError"]
+           "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError", "March", "march_step_points"]
 NPARAMS = 5648
 
 
@@ -129,12 +129,24 @@ class Freqs:
         return cls(ctx, h)
 
     @classmethod
-    def gcq(cls, ctx, dts, rk, NQ):
+    def gcq(cls, ctx, dts, rk, NQ, rho=0.0):
         """gCQ contour of App. A for the time steps dts (host array) and the
-        Runge-Kutta method rk (EULER or RADAU2), NQ contour points."""
+        Runge-Kutta method rk (EULER or RADAU2), NQ contour points; the circle
+        through 0 and 2 rho / dt_min (rho = 1: as printed; rho <= 0: the
+        radius the time marching needs)."""
         h = C.c_void_p()
         d = np.ascontiguousarray(dts, dtype=np.float64)
-        ctx.check(ctx.L.tdbem_freqs_gcq(ctx.h, _np_ptr(d), len(d), rk, NQ, C.byref(h)), "tdbem_freqs_gcq")
+        ctx.check(ctx.L.tdbem_freqs_gcq(ctx.h, _np_ptr(d), len(d), rk, NQ, float(rho), C.byref(h)), "tdbem_freqs_gcq")
+        return cls(ctx, h)
+
+    @classmethod
+    def points(cls, ctx, s, w=None):
+        """A set of explicit points (host complex array, Re s > 0), optional weights."""
+        sv = np.ascontiguousarray(np.asarray(s, dtype=np.complex128)).view(np.float64)
+        wv = None if w is None else np.ascontiguousarray(np.asarray(w, dtype=np.complex128)).view(np.float64)
+        h = C.c_void_p()
+        ctx.check(ctx.L.tdbem_freqs_points(ctx.h, _np_ptr(sv), None if wv is None else _np_ptr(wv), len(sv) // 2,
+                                           C.byref(h)), "tdbem_freqs_points")
         return cls(ctx, h)
 
     def steps(self):
@@ -336,6 +348,50 @@ def autotune(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, n
     ch = (C.c_int32 * 2)()
     ctx.check(ctx.L.tdbem_autotune(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), ch), "tdbem_autotune")
     return int(ch[0]), int(ch[1])
+
+
+def march_step_points(dts, rk):
+    """The distinct step frequencies 1/(dt lambda_k(A)) of the steps (complex array)."""
+    L = _lib.load()
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    n = C.c_int32()
+    _lib.check(L.tdbem_march_step_points(_np_ptr(d), len(d), rk, None, C.byref(n)), None, "tdbem_march_step_points")
+    out = np.zeros(2 * n.value)
+    _lib.check(L.tdbem_march_step_points(_np_ptr(d), len(d), rk, _np_ptr(out), C.byref(n)), None,
+               "tdbem_march_step_points")
+    return out.view(np.complex128)
+
+
+class March:
+    """gCQ time marching of the direct Dirichlet problem V * q = (1/2 M + K) * g
+    (include/tdbem.h): V, K compressed over a gCQ contour, Vstep, Kstep over
+    the step frequencies."""
+
+    def __init__(self, V, K, Vstep, Kstep, dts, rk, nrhs):
+        self.ctx = V.ctx
+        self.tensors = (V, K, Vstep, Kstep)
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        h = C.c_void_p()
+        self.ctx.check(self.ctx.L.tdbem_march_create(V.h, K.h, Vstep.h, Kstep.h, _np_ptr(d), len(d), rk, nrhs,
+                                                     C.byref(h)), "tdbem_march_create")
+        self.h = h
+        self.m = 2 if rk == RADAU2 else 1
+        self.nrhs = nrhs
+
+    def step(self, g, q=None, tol=1e-8, maxit=500):
+        """g: device float64 [nv, m, nrhs]; returns q: device float64 [nt, m, nrhs] and the GMRES steps."""
+        torch = _torch()
+        if q is None:
+            q = torch.empty((self.tensors[0].nrows, self.m, self.nrhs), dtype=torch.float64, device=g.device)
+        it = C.c_int32()
+        self.ctx.check(self.ctx.L.tdbem_march_step(self.h, _ptr(g), _ptr(q), tol, maxit, C.byref(it)),
+                       "tdbem_march_step")
+        return q, it.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib._lib is not None:
+            _lib._lib.tdbem_march_destroy(self.h)
+            self.h = None
 
 
 def zgemm(ctx, A, B, D=None):

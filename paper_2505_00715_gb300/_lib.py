@@ -61,9 +61,16 @@ EXPORTS = {
     "tdbem_mesh_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_mesh_ndof": (C.c_int64, [C.c_void_p, C.c_int32]),
     "tdbem_freqs_cq_bdf2": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_void_p)]),
-    "tdbem_freqs_gcq": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+    "tdbem_freqs_gcq": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                   C.POINTER(C.c_void_p)]),
     "tdbem_freqs_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "tdbem_freqs_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "tdbem_march_step_points": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
+    "tdbem_march_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                     C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "tdbem_march_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
+                                   C.POINTER(C.c_int32)]),
+    "tdbem_march_destroy": (C.c_int, [C.c_void_p]),
     "tdbem_freqs_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), C.c_void_p]),
     "tdbem_freqs_destroy": (C.c_int, [C.c_void_p]),

@@ -452,6 +452,24 @@ int finish_freqs(tdbem_ctx *ctx, tdbem_freqs *f) {
     f->uidx.clear();
     for (int k = 0; k < NQ; ++k) {
         int partner = f->kind == 0 ? (NQ - k) % NQ : NQ - 1 - k;
+        if (f->kind == 2) {
+            // explicit points: the partner is the point equal to conj(s_k), if any
+            partner = k;
+            const double re = f->s[2 * k], im = f->s[2 * k + 1], tol = 1e-12 * std::hypot(re, im);
+            if (im != 0.0)
+                for (int p = 0; p < NQ; ++p)
+                    if (p != k && std::fabs(f->s[2 * p] - re) <= tol && std::fabs(f->s[2 * p + 1] + im) <= tol &&
+                        f->unique[p] == 0) {
+                        partner = p;
+                        break;
+                    }
+            if (f->unique[k] != 0) continue;  // already the conjugate of an earlier point
+            const int rep = (int)f->uidx.size();
+            f->uidx.push_back(k);
+            f->unique[k] = rep + 1;
+            if (partner != k) f->unique[partner] = -(rep + 1);
+            continue;
+        }
         if (partner < k) continue;  // assigned as conjugate below
         const int rep = (int)f->uidx.size();
         f->uidx.push_back(k);
@@ -492,10 +510,11 @@ extern "C" int tdbem_freqs_cq_bdf2(tdbem_ctx_t ctx, int32_t N, double dt, double
     return TDBEM_OK;
 }
 
-extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ,
+extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, int32_t rk, int32_t NQ, double rho_in,
                                tdbem_freqs_t *out) {
     cudaGetLastError();  // errors of earlier unrelated calls are not ours to report
-    if (!ctx || !out || !dts || N < 1 || NQ < 2 || NQ % 2 || NQ > 65536 || (rk != TDBEM_EULER && rk != TDBEM_RADAU2))
+    if (!ctx || !out || !dts || N < 1 || NQ < 2 || NQ % 2 || NQ > 65536 || (rk != TDBEM_EULER && rk != TDBEM_RADAU2) ||
+        !std::isfinite(rho_in))
         return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_gcq: need N >= 1 steps, even NQ >= 2, rk EULER|RADAU2");
     *out = nullptr;
     double dt_min = dts[0], dt_max = dts[0];
@@ -524,12 +543,46 @@ extern "C" int tdbem_freqs_gcq(tdbem_ctx_t ctx, const double *dts, int32_t N, in
     f->dw = f->ds + 2 * NQ;
     // the contour is built for dt_min / rho (td_gcq_radius): a circle through 0
     // and 2 rho / dt_min around every resolvent pole of the steps
-    const double rho = td_gcq_radius(rk, N);
+    const double rho = rho_in > 0.0 ? rho_in : td_gcq_radius(rk, N);
     f->rho = rho;
     if (td_launch_gcq(ctx->stream, NQ, dt_min / rho, q, f->ds, f->dw) || (rc = finish_freqs(ctx, f))) {
         cudaFree(f->ds);
         delete f;
         return rc ? rc : td_fail(ctx, TDBEM_ERR_CUDA, "gCQ frequency kernel failed");
+    }
+    *out = f;
+    return TDBEM_OK;
+}
+
+extern "C" int tdbem_freqs_points(tdbem_ctx_t ctx, const double *s, const double *w, int32_t NQ, tdbem_freqs_t *out) {
+    cudaGetLastError();
+    if (!ctx || !out || !s || NQ < 1 || NQ > 65536)
+        return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_points: need 1 <= NQ <= 65536 points");
+    *out = nullptr;
+    for (int k = 0; k < 2 * NQ; ++k)
+        if (!std::isfinite(s[k]) || (w && !std::isfinite(w[k])))
+            return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_points: non-finite value at %d", k);
+    for (int k = 0; k < NQ; ++k)
+        if (!(s[2 * k] > 0.0)) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_freqs_points: Re(s_%d) must be > 0", k);
+    tdbem_freqs *f = new (std::nothrow) tdbem_freqs();
+    if (!f) return TDBEM_ERR_OOM;
+    f->ctx = ctx;
+    f->NQ = NQ;
+    f->kind = 2;
+    f->s.assign(s, s + 2 * NQ);
+    f->w.assign(2 * NQ, 0.0);
+    if (w) f->w.assign(w, w + 2 * NQ);
+    int rc;
+    if ((rc = dalloc(ctx, &f->ds, 4 * (size_t)NQ))) {
+        delete f;
+        return rc;
+    }
+    f->dw = f->ds + 2 * NQ;
+    if ((rc = upload(ctx, f->ds, f->s.data(), 2 * NQ)) || (rc = upload(ctx, f->dw, f->w.data(), 2 * NQ)) ||
+        (rc = finish_freqs(ctx, f))) {
+        cudaFree(f->ds);
+        delete f;
+        return rc;
     }
     *out = f;
     return TDBEM_OK;

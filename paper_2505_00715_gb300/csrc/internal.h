@@ -74,7 +74,7 @@ struct tdbem_freqs {
     std::vector<int32_t> uidx;    // unique representative -> point index
     double *ds = nullptr;         // device [2*NQ]
     double *dw = nullptr;
-    int kind = 0;                 // 0 BDF2, 1 gCQ
+    int kind = 0;                 // 0 BDF2, 1 gCQ, 2 explicit points
     std::vector<double> dts;      // gCQ: the time steps the contour was built for
     double rho = 1.0;             // gCQ: radius factor of the contour (td_gcq_radius)
 };

@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                 }
                 tc_commit(bar);
             }
-            const bool ok = mbar_wait(bar, phase, max_polls);
+            // a limit below the default counts non-blocking tests (a blocking
+            // try_wait may itself wait until the MMAs are done)
+            const bool ok = max_polls < kMaxPolls ? mbar_test(bar, phase, max_polls) : mbar_wait(bar, phase, max_polls);
             phase ^= 1u;
             failed = __syncthreads_or(!ok) != 0;
             tc_fence_after();

@@ -40,6 +40,24 @@ TC_D bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_tries) {
     return false;
 }
 
+// Non-blocking variant: at most max_tests single tests of the phase (each
+// returns at once), false if none saw it complete.
+TC_D bool mbar_test(uint64_t *bar, uint32_t parity, uint32_t max_tests) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < max_tests; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // ---- fences -------------------------------------------------------------------
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
 TC_D void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -11,7 +11,7 @@ import math
 
 import numpy as np
 
-__all__ = ["icosahedron", "octahedron", "icosphere", "housing", "random_weights", "graded_steps"]
+__all__ = ["icosahedron", "octahedron", "icosphere", "housing", "cube", "random_weights", "graded_steps"]
 
 
 def octahedron(R=1.0):
@@ -214,6 +214,61 @@ def housing(n_target, radius=0.1, length=0.3, nfins=12, fin_h=0.015, fin_t=0.005
         d /= np.linalg.norm(d, axis=1, keepdims=True)
         rad = jitter * h * rng.random(len(V)) ** (1.0 / 3.0)
         V = V + d * rad[:, None]
+    return V, T
+
+
+def cube(level, L=1.0):
+    """Cube [-L/2, L/2]^3 (the paper's unit cube, Sec. 5): level 1 splits
+    every face into 2 x 2 squares and every square into 4 triangles at its
+    centre (96 triangles, 50 vertices, h = L/2); each further level splits
+    every triangle into 4 at its edge midpoints (384 / 194, 1536 / 770, ...)."""
+    verts, index = [], {}
+
+    def vid(p):
+        key = tuple(np.round(np.asarray(p) * 2 ** 20).astype(np.int64))
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(np.asarray(p, dtype=np.float64))
+        return index[key]
+
+    tris = []
+    h = L / 2.0
+    for axis in range(3):
+        for sign in (-1.0, 1.0):
+            u, w = [(axis + 1) % 3, (axis + 2) % 3]
+            for a in range(2):
+                for b in range(2):
+                    def pt(x, y):
+                        p = np.zeros(3)
+                        p[axis] = sign * h
+                        p[u] = -h + x * h
+                        p[w] = -h + y * h
+                        return p
+                    c = vid(pt(a + 0.5, b + 0.5))
+                    q = [vid(pt(a, b)), vid(pt(a + 1, b)), vid(pt(a + 1, b + 1)), vid(pt(a, b + 1))]
+                    for k in range(4):
+                        tris.append((q[k], q[(k + 1) % 4], c))
+    V = np.array(verts)
+    T = np.array(tris, dtype=np.int32)
+    for _ in range(level - 1):
+        cache, new = {}, []
+
+        def mid(i, j):
+            key = (i, j) if i < j else (j, i)
+            if key not in cache:
+                cache[key] = len(V_l)
+                V_l.append(0.5 * (V_l[i] + V_l[j]))
+            return cache[key]
+        V_l = list(V)
+        for a, b, c in T:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+        V, T = np.array(V_l), np.array(new, dtype=np.int32)
+    # outward orientation: the normal points away from the cube's centre
+    a, b, c = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    n = np.cross(b - a, c - a)
+    flip = np.einsum("ij,ij->i", n, (a + b + c) / 3.0) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
     return V, T
 
 

@@ -64,7 +64,7 @@ def hous(td, ctx, orc):
     k = Case()
     k.V, k.T = housing(2000, seed=0)
     k.gm, k.om = td.Mesh(ctx, k.V, k.T), orc.Mesh(k.V, k.T)
-    k.f = td.Freqs.gcq(ctx, graded_steps(256, 1.01, 0.015), td.RADAU2, 256)
+    k.f = td.Freqs.gcq(ctx, graded_steps(256, 1.01, 0.015), td.RADAU2, 256, rho=1.0)
     u = k.f.unique
     # 32 of the 128 unique contour points, spread over the contour (the
     # largest |Im s| and Re s among them), and two conjugate points

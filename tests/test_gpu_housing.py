@@ -36,7 +36,7 @@ def test_housing_gcq_sampled_apply(td, ctx, orc):
     V, T = housing(30000, seed=0)
     dts = graded_steps(256, 1.01, 0.015)
     gm = td.Mesh(ctx, V, T)
-    f = td.Freqs.gcq(ctx, dts, td.RADAU2, 256)
+    f = td.Freqs.gcq(ctx, dts, td.RADAU2, 256, rho=1.0)
     assert f.NQ == 256 and f.Nu == 128
     tree = td.Tree(gm, td.P0, td.P0, 64, 2.0)
     eps = 1e-4
@@ -68,7 +68,7 @@ def test_housing_gmres_per_frequency(td, ctx, orc):
     V, T = housing(2000, seed=0)
     dts = graded_steps(64, 1.01, 0.015)
     gm = td.Mesh(ctx, V, T)
-    f = td.Freqs.gcq(ctx, dts, td.RADAU2, 64)
+    f = td.Freqs.gcq(ctx, dts, td.RADAU2, 64, rho=1.0)
     tree = td.Tree(gm, td.P0, td.P0, 64, 2.0)
     eps = 1e-6
     X = td.compress(gm, td.SLP, f, tree, eps=eps, eps_aca=1e-8, prec=td.FP64, c=C_AIR)
@@ -97,7 +97,7 @@ def test_housing80k_gcq512_apply_and_gmres(td, ctx, orc):
     V, T = housing(80000, seed=0)
     dts = graded_steps(512, 1.01 ** (255.0 / 511.0), 0.015)
     gm = td.Mesh(ctx, V, T)
-    f = td.Freqs.gcq(ctx, dts, td.RADAU2, 512)
+    f = td.Freqs.gcq(ctx, dts, td.RADAU2, 512, rho=1.0)
     assert f.NQ == 512 and f.Nu == 256
     tree = td.Tree(gm, td.P0, td.P0, 64, 2.0)
     eps = 1e-4

@@ -61,11 +61,12 @@ def test_freqs_bdf2(td, ctx, orc, N, dt):
         assert np.allclose(f.s[k], f.s[rep] if u > 0 else np.conj(f.s[rep]), rtol=1e-13)
 
 
-@pytest.mark.parametrize("rk,NQ", [(1, 256), (0, 64)])
-def test_freqs_gcq(td, ctx, orc, rk, NQ):
+@pytest.mark.parametrize("rk,NQ,rho", [(1, 256, 1.0), (1, 256, 0.0), (0, 64, 0.0), (1, 128, 2.5)])
+def test_freqs_gcq(td, ctx, orc, rk, NQ, rho):
     dts = graded_steps(256, 1.01, 0.015)
-    f = td.Freqs.gcq(ctx, dts, rk, NQ)
-    s, w, _ = orc.freqs_gcq(dts.min(), dts.max(), rk, NQ, len(dts))
+    f = td.Freqs.gcq(ctx, dts, rk, NQ, rho=rho)
+    s, w, _ = orc.freqs_gcq(dts.min(), dts.max(), rk, NQ, len(dts), rho=rho)
+    assert np.array_equal(f.steps(), dts)
     assert np.max(np.abs(f.s - s)) <= 1e-12 * np.max(np.abs(s))
     assert np.max(np.abs(f.w - w)) <= 1e-12 * np.max(np.abs(w))
     assert f.Nu == NQ // 2

@@ -144,6 +144,16 @@ def test_gcq_contour_radius(orc, rk, nsteps):
     assert orc.gcq_radius(rk, nsteps) == rho
 
 
+def test_gcq_printed_contour(orc):
+    """rho = 1: the contour as printed in App. A, the circle through 0 and
+    2/dt_min whatever the method."""
+    for rk in (0, 1):
+        dt_min = 2e-3
+        s, w, info = orc.freqs_gcq(dt_min, 12.6 * dt_min, rk, 64, 256, rho=1.0)
+        assert info["rho"] == 1.0
+        assert np.max(np.abs(np.abs(s - 1.0 / dt_min) - 1.0 / dt_min)) < 1e-9 / dt_min
+
+
 def test_gcq_degenerate_q_lifted(orc):
     s, w, info = orc.freqs_gcq(1e-3, 1e-3, 0, 32, 4)
     assert info["lifted"] and info["q"] > 1.0 and np.all(np.isfinite(s))

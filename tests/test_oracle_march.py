@@ -83,3 +83,18 @@ def test_matrix_argument_is_the_operator_of_the_step_resolvent(orc):
     B = np.linalg.inv(dt * A)
     cauchy = sum(wl * np.exp(-sl) * np.linalg.solve(sl * np.eye(2) - B, data[0]) for sl, wl in zip(s, w))
     assert np.allclose(direct[0], cauchy, rtol=1e-8, atol=1e-10)
+
+
+def test_cube_dirichlet_oracle_converges(orc):
+    """The oracle's dense marching of the direct Dirichlet problem on the unit
+    cube (Sec. 5, eq. load; 2-stage Radau IIA) converges towards the exact
+    Neumann datum: the L_max error of eq. error falls by more than half from
+    level 1 (96 triangles, 10 steps) to level 2 (384, 20 steps)."""
+    from _cube import CubeProblem, oracle_solution
+    bary, w7 = orc.rule7()
+    e = []
+    for level in (1, 2):
+        P = CubeProblem(level)
+        e.append(P.lmax(oracle_solution(orc, P), bary, w7))
+    print("cube Dirichlet L_max levels 1, 2: %s, eoc %.2f" % (e, np.log2(e[0] / e[1])))
+    assert e[1] < 0.5 * e[0] and e[1] < 0.6, e
