@@ -458,7 +458,8 @@ def main():
                             "sum_face_rank": st["sum_face_rank"], "pool_growths": st["pool_growths"],
                             "aca_tests": st["aca_tests"]},
             "predictor": dict(pinfo, without=no_pred),
-            "autotuned_far_launch": tuned and {"threads_per_cta": tuned[0], "ctas_per_sm": tuned[1]},
+            "autotuned": tuned and {"far_threads_per_cta": tuned[0], "far_ctas_per_sm": tuned[1],
+                                    "touching_pair_freqs_per_pass": tuned[2], "near_freqs_per_pass": tuned[3]},
             "fp64_form": fp64,
             "e2e": e2e,
             "roofline": roof,

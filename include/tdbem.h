@@ -287,12 +287,20 @@ int tdbem_tensor_blocks(tdbem_tensor_t t, int32_t *rank, int32_t *face_rank_sum,
  * results of tdbem_tensor_blocks follow its order. */
 int tdbem_tensor_partition(tdbem_tensor_t t, int64_t *nb, int32_t *blocks);
 int tdbem_tensor_destroy(tdbem_tensor_t t);
-/* Project-written autotuner of the persistent far-field phase (Sec. 4
- * Algorithm 1 on the admissible blocks): times complete compressions of the
- * given problem with candidate launch shapes (threads per CTA x resident
- * CTAs per SM) and keeps the fastest in the context for op->prec.  chosen
- * (nullable, host int32 [2]) receives {threads per CTA, CTAs per SM}.  The
- * defaults without tuning are {128, 4}. */
+/* Project-written autotuner of the compression's launch parameters (Sec. 4
+ * Algorithm 1 and the entry kernels of Sec. 3), kept in the context for
+ * op->prec: times complete compressions of the given problem (the first of
+ * two runs warms up) and keeps, phase by phase, the fastest
+ *   - far phase: launch shape threads per CTA x resident CTAs per SM
+ *     (64/128/256 threads, 2..16 CTAs per SM);
+ *   - mixed form only: frequencies per pass of the touching-pair table
+ *     (register tiles of 36/12/24 frequencies for the single layer, 12/6/8
+ *     for the double layer) and of the near-field tensor kernel (8/4/16),
+ *     each timed on its own phase.
+ * chosen (nullable, host int32 [4]) receives {far threads per CTA, far CTAs
+ * per SM, touching-pair frequencies per pass, near-field frequencies per
+ * pass} (0 for the two mixed-form choices of an FP64 form).  Defaults without
+ * tuning: {128, 4 (FP64) / 5 (mixed), 36 or 12, 8}. */
 int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, tdbem_tree_t tree,
                    const tdbem_aca_cfg *cfg, int32_t *chosen);
 

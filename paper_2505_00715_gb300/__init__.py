@@ -340,14 +340,15 @@ def compress(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, n
 
 
 def autotune(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, ng=5, max_face_rank=64, model=None):
-    """Time the far-field phase with candidate launch shapes and keep the fastest
-    in the context; returns (threads per CTA, CTAs per SM)."""
+    """Time the compression with candidate launch parameters and keep the fastest
+    per phase in the context; returns (far threads per CTA, far CTAs per SM,
+    touching-pair frequencies per pass, near-field frequencies per pass)."""
     ctx = mesh.ctx
     o = _op(op, prec, c, ng)
     cfg = _lib.AcaCfg(eps, eps_aca, max_face_rank, 0, model.h if model is not None else None)
-    ch = (C.c_int32 * 2)()
+    ch = (C.c_int32 * 4)()
     ctx.check(ctx.L.tdbem_autotune(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), ch), "tdbem_autotune")
-    return int(ch[0]), int(ch[1])
+    return tuple(int(x) for x in ch)
 
 
 def march_step_points(dts, rk):

@@ -1081,7 +1081,8 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                 cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 4, ls);
                 cudaMemsetAsync(redo_count, 0, sizeof(unsigned int) * 4, ls);
                 cudaMemsetAsync(T->drank, 0, sizeof(int32_t) * nb, ls);
-                lrc |= td_launch_sing_table(ls, md, op->op, op->prec, pti, ptj, npairs, sig, Nu, table, ctx->num_sms);
+                lrc |= td_launch_sing_table(ls, md, op->op, op->prec, pti, ptj, npairs, sig, Nu, table, ctx->num_sms,
+                                            ctx->sing_var);
                 nlaunch += npairs > 0;
             } else if (ph == 1 || ph == 2) {
                 // one batch: entries (phase 1) and 3D-ACA (phase 2); several: both per
@@ -1097,7 +1098,8 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                     nab.nentries = batch_nent[bt];
                     const int nct = std::min(nctas_near, nab.nnear);
                     if (ph == 1) {
-                        lrc |= td_launch_near_entries(ls, md, op->op, op->prec, nab, table, ctx->num_sms);
+                        lrc |= td_launch_near_entries(ls, md, op->op, op->prec, nab, table, ctx->num_sms,
+                                                      ctx->near_var);
                         nlaunch += nab.nentries > 0;
                     }
                     if ((ph == 2 && nbt == 1) || (ph == 1 && nbt > 1)) {
@@ -1643,7 +1645,19 @@ extern "C" int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
                               tdbem_tree_t tree, const tdbem_aca_cfg *cfg, int32_t *chosen) {
     if (!ctx || !op) return TDBEM_ERR_ARG;
     const int pf = op->prec == TDBEM_MIXED ? 1 : 0;
-    // candidate shapes: threads per CTA x CTAs per SM (CTAs beyond what the
+    // times a complete compression (the first of two runs warms up) and
+    // returns its statistics
+    auto run = [&](tdbem_stats &st) {
+        for (int rep = 0; rep < 2; ++rep) {
+            tdbem_tensor_t X = nullptr;
+            const int rc = tdbem_compress(ctx, mesh, op, f, tree, cfg, &X);
+            if (rc) return rc;
+            if (rep == 1) st = X->stats;
+            tdbem_tensor_destroy(X);
+        }
+        return (int)TDBEM_OK;
+    };
+    // 1. far phase: threads per CTA x resident CTAs per SM (CTAs beyond what the
     // registers and shared memory of an SM hold start only when resident ones
     // exit, i.e. once the work queue is empty)
     static const int cand[][2] = {{256, 2}, {128, 4}, {128, 5}, {64, 8}, {64, 10}, {64, 16}};
@@ -1652,29 +1666,53 @@ extern "C" int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     for (const auto &c : cand) {
         ctx->far_nt[pf] = c[0];
         ctx->far_cps[pf] = c[1];
-        double t = 0.0;
-        for (int rep = 0; rep < 2; ++rep) {
-            tdbem_tensor_t X = nullptr;
-            int rc = tdbem_compress(ctx, mesh, op, f, tree, cfg, &X);
-            if (rc) {
-                ctx->far_nt[pf] = bnt;
-                ctx->far_cps[pf] = bcps;
-                return rc;
-            }
-            if (rep == 1) t = X->stats.ms_far;  // the first run warms up
-            tdbem_tensor_destroy(X);
+        tdbem_stats st{};
+        const int rc = run(st);
+        if (rc) {
+            ctx->far_nt[pf] = bnt;
+            ctx->far_cps[pf] = bcps;
+            return rc;
         }
-        if (t < best) {
-            best = t;
+        if (st.ms_far < best) {
+            best = st.ms_far;
             bnt = c[0];
             bcps = c[1];
         }
     }
     ctx->far_nt[pf] = bnt;
     ctx->far_cps[pf] = bcps;
+    // 2. mixed form: frequencies per pass of the touching-pair table and of the
+    // near-field tensor kernel (register tiles of FC frequencies), each phase
+    // timed on its own from the same compressions
+    int bsing = ctx->sing_var, bnear = ctx->near_var;
+    if (pf) {
+        double ts = 1e300, tn = 1e300;
+        for (int v = 0; v < 3; ++v) {
+            ctx->sing_var = ctx->near_var = v;
+            tdbem_stats st{};
+            const int rc = run(st);
+            if (rc) {
+                ctx->sing_var = bsing;
+                ctx->near_var = bnear;
+                return rc;
+            }
+            if (st.ms_singular < ts) {
+                ts = st.ms_singular;
+                bsing = v;
+            }
+            if (st.ms_near < tn) {
+                tn = st.ms_near;
+                bnear = v;
+            }
+        }
+        ctx->sing_var = bsing;
+        ctx->near_var = bnear;
+    }
     if (chosen) {
         chosen[0] = bnt;
         chosen[1] = bcps;
+        chosen[2] = pf ? td_sing_fc(op->op, bsing) : 0;
+        chosen[3] = pf ? td_near_fc(bnear) : 0;
     }
     return TDBEM_OK;
 }

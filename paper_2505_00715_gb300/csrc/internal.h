@@ -16,6 +16,9 @@ struct tdbem_ctx {
     // threads per CTA and CTAs per SM (set by tdbem_autotune)
     int far_nt[2] = {128, 128};
     int far_cps[2] = {4, 5};
+    // tuning variants of the mixed form's touching-pair table and near-field
+    // tensor kernels (frequencies per pass; 0 = default), set by tdbem_autotune
+    int sing_var = 0, near_var = 0;
     int64_t near_batch_bytes = (int64_t)16 << 30;  // buffer of the batched near-field tensor
     double pool_scale = 1.0;                       // far part of the first face-pool size
     std::string err;

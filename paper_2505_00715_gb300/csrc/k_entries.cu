@@ -416,16 +416,31 @@ int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const
     return (int)cudaGetLastError();
 }
 
+// Frequencies per pass of the mixed-form kernels, selected by the tuning
+// variant (0 = default): touching-pair table (single / double layer) and
+// near-field tensor.
+constexpr int kSingFcSlp[3] = {36, 12, 24};
+constexpr int kSingFcDlp[3] = {12, 6, 8};
+constexpr int kNearFc[3] = {8, 4, 16};
+int td_sing_fc(int op, int variant) { return op == TD_SLP ? kSingFcSlp[variant % 3] : kSingFcDlp[variant % 3]; }
+int td_near_fc(int variant) { return kNearFc[variant % 3]; }
+
 int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, const int *pti, const int *ptj,
-                         int npairs, const double *sig, int nf, c64 *table, int num_sms) {
+                         int npairs, const double *sig, int nf, c64 *table, int num_sms, int variant) {
     if (npairs == 0) return 0;
     if (nf > 256) return (int)cudaErrorInvalidValue;  // the frequencies are staged in shared memory
     int grid = std::min((npairs + 3) / 4, num_sms * 8);
     if (prec == TDBEM_MIXED) {
-        if (op == TD_SLP)
-            k_sing_table_mixed<TD_SLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-        else
-            k_sing_table_mixed<TD_DLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+        const int v = variant % 3;
+        if (op == TD_SLP) {
+            if (v == 1) k_sing_table_mixed<TD_SLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else if (v == 2) k_sing_table_mixed<TD_SLP, 24><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_SLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+        } else {
+            if (v == 1) k_sing_table_mixed<TD_DLP, 6><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else if (v == 2) k_sing_table_mixed<TD_DLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_DLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+        }
         return (int)cudaGetLastError();
     }
     if (op == TD_SLP)
@@ -436,15 +451,23 @@ int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, co
 }
 
 int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const NearArgs &a,
-                           const c64 *table, int num_sms) {
+                           const c64 *table, int num_sms, int variant) {
     if (a.nentries == 0) return 0;
     int grid = (int)std::min<int64_t>((a.nentries + 127) / 128, (int64_t)num_sms * 16);
     if (prec == TDBEM_FP64) {
         if (op == TD_SLP) k_near_entries<double, TD_SLP, 4><<<grid, 128, 0, st>>>(m, a, table);
         else k_near_entries<double, TD_DLP, 4><<<grid, 128, 0, st>>>(m, a, table);
     } else {
-        if (op == TD_SLP) k_near_entries<float, TD_SLP, 8><<<grid, 128, 0, st>>>(m, a, table);
-        else k_near_entries<float, TD_DLP, 8><<<grid, 128, 0, st>>>(m, a, table);
+        const int v = variant % 3;
+        if (op == TD_SLP) {
+            if (v == 1) k_near_entries<float, TD_SLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+            else if (v == 2) k_near_entries<float, TD_SLP, 16><<<grid, 128, 0, st>>>(m, a, table);
+            else k_near_entries<float, TD_SLP, 8><<<grid, 128, 0, st>>>(m, a, table);
+        } else {
+            if (v == 1) k_near_entries<float, TD_DLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+            else if (v == 2) k_near_entries<float, TD_DLP, 16><<<grid, 128, 0, st>>>(m, a, table);
+            else k_near_entries<float, TD_DLP, 8><<<grid, 128, 0, st>>>(m, a, table);
+        }
     }
     return (int)cudaGetLastError();
 }

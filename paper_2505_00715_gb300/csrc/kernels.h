@@ -67,10 +67,14 @@ int td_launch_peak(cudaStream_t st, int what, int grid, int iters, void *out, do
 int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const double *sig, int nq,
                       const int *rows, int64_t nr, const int *cols, int64_t nc, const int *fidx,
                       int64_t nf, void *out);
+// variant: tuning choice of the mixed form's frequencies per pass (0 = default;
+// td_sing_fc / td_near_fc give the values)
 int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, const int *pti, const int *ptj,
-                         int npairs, const double *sig, int nf, c64 *table, int num_sms);
+                         int npairs, const double *sig, int nf, c64 *table, int num_sms, int variant = 0);
 int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const NearArgs &a,
-                           const c64 *table, int num_sms);
+                           const c64 *table, int num_sms, int variant = 0);
+int td_sing_fc(int op, int variant);
+int td_near_fc(int variant);
 int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const TensorOut &o,
                        const AcaParams &p, void *scratch, int64_t scratch_per_cta, int nctas);
 int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,

@@ -197,15 +197,17 @@ def test_config2_sampled_apply(td, ctx, orc, op, prec):
 
 
 def test_autotune_keeps_results(td, ctx, orc, sphere2):
-    """The launch-shape autotuner only changes the far-phase launch; the
-    compressed tensor applies identically."""
+    """The autotuner changes launch parameters only (far launch shape,
+    frequencies per pass of the entry kernels); the compressed tensor applies
+    identically (to FP32 rounding: the entry kernels' summation order is the
+    same per frequency)."""
     import torch
     V, T, gm, om = sphere2
     f = td.Freqs.bdf2(ctx, 16, 0.1)
     tree = td.Tree(gm, td.P0, td.P0, 16, 2.0)
     X0 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
-    nt, cps = td.autotune(gm, td.SLP, f, tree, prec=td.MIXED)
-    assert nt in (64, 128, 256) and cps >= 1
+    nt, cps, sfc, nfc = td.autotune(gm, td.SLP, f, tree, prec=td.MIXED)
+    assert nt in (64, 128, 256) and cps >= 1 and sfc in (12, 24, 36) and nfc in (4, 8, 16)
     X1 = td.compress(gm, td.SLP, f, tree, prec=td.MIXED)
     W = torch.as_tensor(random_weights(16, len(T), 2, seed=3), dtype=torch.complex64, device="cuda")
     y0 = X0.apply_weighted(W).cpu().numpy()
