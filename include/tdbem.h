@@ -108,6 +108,9 @@ typedef struct {
                                        factor-norm path (faces above 1600 entries); the rank
                                        predictor batches the tests of the steps below its
                                        predicted rank into one */
+    int64_t pool_first;             /* complex values of the first face-pool allocation: from the
+                                       predicted face ranks with a rank predictor, else from a
+                                       size-based bound (at most the device's free memory) */
 } tdbem_stats;
 
 /* ---- context -------------------------------------------------------------- */

@@ -39,7 +39,8 @@ class Stats(C.Structure):
                                          "stored_complex", "dense_complex", "entries_regular", "entries_tube",
                                          "pairs_singular")] + \
                [(n, C.c_double) for n in ("ms_plan", "ms_singular", "ms_near", "ms_far", "ms_total")] + \
-               [("pool_growths", C.c_int64), ("launches", C.c_int64), ("aca_tests", C.c_int64)]
+               [("pool_growths", C.c_int64), ("launches", C.c_int64), ("aca_tests", C.c_int64),
+                ("pool_first", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -57,8 +57,9 @@ int upload(tdbem_ctx *ctx, T *dst, const T *src, size_t count) {
 }
 
 // terms of Algorithm 1 per far block assumed when the face pool is presized
-// from predicted face ranks (the blocks of the benchmark meshes take 5-16)
-constexpr int64_t kTermsEst = 12;
+// from predicted face ranks (the far blocks of the benchmark meshes take 7-9
+// on average, at most 16)
+constexpr int64_t kTermsEst = 8;
 
 struct Guard {
     // frees transient device buffers at scope exit (or earlier, by release())
@@ -912,9 +913,9 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         for (size_t q = 0; q < order.size(); ++q) {
             sorted[q] = far_ids[order[q]];
             const int32_t *bl = &T->blocks[5 * sorted[q]];
-            // about kTermsEst terms of Algorithm 1 per block, each with a face
-            // rank of at most the largest predicted one
-            pred_far_cap += (int64_t)((bl[1] - bl[0]) + (bl[3] - bl[2])) * ks[order[q]] * kTermsEst;
+            // about kTermsEst terms of Algorithm 1 per block, each with the block's
+            // mean predicted face rank (the lower edge of the predicted bin)
+            pred_far_cap += (int64_t)((bl[1] - bl[0]) + (bl[3] - bl[2])) * ((ks[order[q]] + Nu - 1) / Nu) * kTermsEst;
         }
         far_ids.swap(sorted);
     }
@@ -1030,12 +1031,15 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) cudaGetLastError();
         return std::max<int64_t>(0, ((int64_t)(0.85 * (double)fr) - ((int64_t)2 << 30)) / (int64_t)es);
     };
-    const double far_est = (double)(pred_far_cap >= 0 ? pred_far_cap + pred_far_cap / 4 : sum_far_len * 256);
+    const double far_est = (double)(pred_far_cap >= 0 ? pred_far_cap + pred_far_cap / 2 : sum_far_len * 256);
     // an estimate beyond the device's room starts from the room (a pool that
     // fills up grows where it can)
     int64_t need = std::min(near_res + (int64_t)(ctx->pool_scale * far_est) + 1024,
                             std::max<int64_t>(near_res + 1024, device_room()));
-    int64_t cap = std::max(need, std::min(2 * need, device_room()));
+    // a size-based bound asks for up to twice itself where the device has room;
+    // a presize from predicted ranks asks for itself (a pool that fills up grows)
+    int64_t cap = pred_far_cap >= 0 ? need : std::max(need, std::min(2 * need, device_room()));
+    const int64_t pool_first = cap;
     if (dkpred) fa.kpred = dkpred;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) cudaEventCreate(&ev[k]);
@@ -1281,6 +1285,7 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     st.ms_far = ms[3] + ms_redo;
     st.pool_growths = st_redo;
     st.launches = nlaunch;
+    st.pool_first = pool_first;
     st.ms_total = now_ms() - t0;
     if (hflags & TD_DEV_RANK_CAP)
         td_fail(ctx, TDBEM_OK, "note: some far faces reached the rank cap %d", kcap);

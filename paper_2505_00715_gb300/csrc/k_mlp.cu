@@ -67,7 +67,8 @@ __constant__ int c_bin_lower[NOUT] = {1, 2, 3, 4, 5, 7, 9, 11, 13, 17, 21, 25, 3
 // Presizing of the far blocks: sample s = (far block q, unique frequency u);
 // the two frequency features are formed here from the block distance and
 // s/c.  Writes the predicted first trip count kp to kpred[far[q] Nu + u],
-// raises ks[q] to max_u min(kp, kcap) and adds len[q] kp^2 to cost[q].
+// adds min(kp, kcap) to ks[q] (the block's predicted face ranks summed over
+// the frequencies) and len[q] kp^2 to cost[q].
 __global__ void __launch_bounds__(128) k_mlp_presize(const __nv_bfloat16 *P, const float *bfeat, const float *ffeat,
                                                      int nfar, int Nu, const int *far, const int *len, int kcap,
                                                      int *kpred, int *ks, float *cost) {
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(128) k_mlp_presize(const __nv_bfloat16 *P, con
                          log1pf(ffeat[2 * u + 1] * b[4])};
         const int kp = c_bin_lower[mlp_forward_bin(w, in, nullptr)];
         kpred[(int64_t)far[q] * Nu + u] = kp;
-        atomicMax(&ks[q], min(kp, kcap));
+        atomicAdd(&ks[q], min(kp, kcap));
         atomicAdd(&cost[q], (float)len[q] * (float)kp * (float)kp);
     }
 }

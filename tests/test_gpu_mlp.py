@@ -142,7 +142,9 @@ def test_predictor_keeps_the_adaptive_result(td, ctx, orc, trained):
     y1 = X1.apply_weighted(Wd).cpu().numpy()
     assert np.linalg.norm(y1 - y0) <= 1e-4 * np.linalg.norm(y0)
     s0, s1 = X0.stats(), X1.stats()
-    print("far phase without / with predictor: %.1f / %.1f ms" % (s0["ms_far"], s1["ms_far"]))
+    print("far phase without / with predictor: %.1f / %.1f ms; first face pool %.3e / %.3e values (stored %.3e, "
+          "pool growths %d)" % (s0["ms_far"], s1["ms_far"], s0["pool_first"], s1["pool_first"], s1["stored_complex"],
+                                s1["pool_growths"]))
 
 
 def test_predictor_gain_fewer_aca_tests(td, ctx, trained):
@@ -163,3 +165,53 @@ def test_predictor_gain_fewer_aca_tests(td, ctx, trained):
           % (s0["aca_tests"], s1["aca_tests"], s1["aca_tests"] / max(1, s0["aca_tests"]), s0["ms_far"], s1["ms_far"]))
     assert s0["aca_tests"] > 0
     assert s1["aca_tests"] < s0["aca_tests"]
+
+
+def test_predictor_on_housing60k(td, ctx, orc):
+    """The learned-predictor configuration: the network is trained on about
+    2M (block, frequency, rank-bin) samples harvested from the sphere
+    configurations (icospheres with 1280 / 5120 / 20480 triangles, single and
+    double layer, two BDF2 frequency sets) and evaluated on the 60k-triangle
+    finned housing with the 256-point gCQ contour (c = 343 m/s).  Its bin
+    accuracy there is reported; what it gains is the size of the first face
+    pool of the compression (presized from the predicted face ranks instead
+    of a size-based bound), while the adaptive criterion keeps the result:
+    the same ranks and an apply within 3 eps of the oracle's dense apply."""
+    import sys
+    import os
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2505_00715_gb300.inputs import graded_steps, housing
+    x, y = bench.harvest_training_set(td, ctx, "cuda")
+    assert len(y) > 1_500_000
+    M = td.Model(ctx, seed=2)
+    loss = M.train(x, y, epochs=8, batch=4096, lr=3e-3, seed=3)
+    cfg = dict(bench.WORKLOADS["housing60k_slp_gcq256"])
+    V, T = housing(60000, seed=0)
+    gm = td.Mesh(ctx, V, T)
+    f = td.Freqs.gcq(ctx, graded_steps(256, 1.01, 0.015), td.RADAU2, 256, rho=1.0)
+    tree = td.Tree(gm, td.P0, td.P0, 64, 2.0)
+    acc = bench.predictor_accuracy(td, M, gm, td.SLP, f, tree, cfg)
+    kw = dict(eps=1e-4, eps_aca=1e-6, prec=td.MIXED, c=343.0, ng=5)
+    X0 = td.compress(gm, td.SLP, f, tree, **kw)
+    s0 = X0.stats()
+    r0 = X0.blocks()[0]
+    del X0
+    X1 = td.compress(gm, td.SLP, f, tree, model=M, **kw)
+    s1 = X1.stats()
+    r1 = X1.blocks()[0]
+    print("housing60k: %d training samples, loss %.3f; bin accuracy %.3f (within one bin %.3f, majority %.3f); "
+          "first face pool without / with predictor %.3e / %.3e values (stored %.3e); time to tensor %.2f / %.2f s"
+          % (len(y), loss, acc["bin_accuracy"], acc["within_one_bin"], acc["majority_bin_share"], s0["pool_first"],
+             s1["pool_first"], s1["stored_complex"], s0["ms_total"] / 1e3, s1["ms_total"] / 1e3))
+    assert s1["pool_first"] < s0["pool_first"]
+    assert s1["pool_first"] >= s1["stored_complex"] or s1["pool_growths"] > 0
+    assert np.mean(r0 == r1) > 0.99
+    W = random_weights(256, len(T), 2, seed=1)
+    yg = X1.apply_weighted(torch.as_tensor(W, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    rows = np.sort(np.random.default_rng(5).choice(len(T), 4, replace=False)).astype(np.int32)
+    yd = orc.Mesh(V, T).dense_apply_rows(orc.SLP, f.s, rows, W, c=343.0, ng=5)
+    err = np.linalg.norm(yg[rows] - yd) / np.linalg.norm(yd)
+    print("housing60k sampled apply error with the predictor %.2e" % err)
+    assert err < 3e-4
