@@ -307,6 +307,25 @@ int tdbem_tensor_destroy(tdbem_tensor_t t);
 int tdbem_autotune(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f, tdbem_tree_t tree,
                    const tdbem_aca_cfg *cfg, int32_t *chosen);
 
+/* QR + SVD recompression of the far faces (Sec. 4, the H-matrix variant:
+ * the ACA factors of every face are recompressed): a face H = U V^T of rank
+ * k is replaced by the k' leading terms of its SVD (Householder QR of U and
+ * V, one-sided Jacobi SVD of R_U R_V^T), k' the smallest rank with
+ * sum_{i >= k'} s_i^2 <= eps^2 sum_i s_i^2, i.e. ||H - H'||_F <= eps ||H||_F
+ * per face.  Computed in the tensor's precision (FP32 in the mixed form,
+ * which resolves singular values down to ~1e-7 of the largest); the face
+ * pool is then compacted to the new sizes and the statistics
+ * (stored_complex, sum_face_rank) are updated.  Synchronous.  ERR_ARG unless
+ * 0 < eps < 1. */
+int tdbem_tensor_recompress(tdbem_tensor_t t, double eps);
+/* The same recompression of one face (no counterpart in the paper; it exists
+ * to test the kernel on its own): U device [k][nI], V device [k][nJ] (face
+ * U V^T, column t of U at U + t nI), 1 <= k <= 64, complex64 (prec MIXED) or
+ * complex128 (FP64); Uout [k][nI], Vout [k][nJ] receive the first *kout rows.
+ * Synchronous. */
+int tdbem_lowrank_recompress(tdbem_ctx_t ctx, int32_t prec, int32_t nI, int32_t nJ, int32_t k, const void *U,
+                             const void *V, double eps, void *Uout, void *Vout, int32_t *kout);
+
 /* ---- apply (eq. product) ------------------------------------------------------ */
 /* y[M][nrhs] = sum_{l < NQ} A(s_l) W_l  with W: device [NQ][ncols][nrhs]
  * complex over all NQ points of the frequency set (conjugate partners are

@@ -19,7 +19,8 @@ from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
 
 __all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "PATH_GENERIC", "PATH_NEAR",
            "PATH_FIBRE", "compress", "harvest", "rank_bin", "autotune",
-           "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError", "March", "march_step_points"]
+           "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError", "March", "march_step_points",
+           "lowrank_recompress"]
 NPARAMS = 5648
 
 
@@ -302,6 +303,11 @@ class Tensor:
         self.ctx.check(self.ctx.L.tdbem_apply_weighted_host(self.h, wp, nrhs, yp), "tdbem_apply_weighted_host")
         return y_host
 
+    def recompress(self, eps):
+        """QR + SVD recompression of every far face to ||H - H'||_F <= eps ||H||_F."""
+        self.ctx.check(self.ctx.L.tdbem_tensor_recompress(self.h, float(eps)), "tdbem_tensor_recompress")
+        return self
+
     def solve(self, fidx, b, tol=1e-6, maxit=500, restart=30, x=None, check=True):
         """x with A(s_fidx) x = b by restarted GMRES; b: device [nrows, nrhs].
         Returns (x, iterations, relative residuals).  With check=False a
@@ -349,6 +355,20 @@ def autotune(mesh, op, freqs, tree, eps=1e-4, eps_aca=1e-6, prec=MIXED, c=1.0, n
     ch = (C.c_int32 * 4)()
     ctx.check(ctx.L.tdbem_autotune(ctx.h, mesh.h, C.byref(o), freqs.h, tree.h, C.byref(cfg), ch), "tdbem_autotune")
     return tuple(int(x) for x in ch)
+
+
+def lowrank_recompress(ctx, U, V, eps):
+    """Recompress one face U V^T (device tensors U [k, nI], V [k, nJ], complex64
+    or complex128) to ||H - H'||_F <= eps ||H||_F; returns (U', V')."""
+    torch = _torch()
+    k, nI = U.shape
+    nJ = V.shape[1]
+    prec = FP64 if U.dtype == torch.complex128 else MIXED
+    Uo, Vo = torch.empty_like(U), torch.empty_like(V)
+    kn = C.c_int32()
+    ctx.check(ctx.L.tdbem_lowrank_recompress(ctx.h, prec, nI, nJ, k, _ptr(U.contiguous()), _ptr(V.contiguous()),
+                                             float(eps), _ptr(Uo), _ptr(Vo), C.byref(kn)), "tdbem_lowrank_recompress")
+    return Uo[:kn.value], Vo[:kn.value]
 
 
 def march_step_points(dts, rk):

@@ -65,6 +65,9 @@ EXPORTS = {
     "tdbem_freqs_gcq": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                   C.POINTER(C.c_void_p)]),
     "tdbem_freqs_steps": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "tdbem_tensor_recompress": (C.c_int, [C.c_void_p, C.c_double]),
+    "tdbem_lowrank_recompress": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                           C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "tdbem_freqs_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "tdbem_march_step_points": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
     "tdbem_march_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,

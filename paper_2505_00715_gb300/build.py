@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtdbem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["api.cu", "model.cu", "noalloc.cu", "solve.cu", "march.cu", "k_freq.cu", "k_entries.cu", "k_aca.cu", "k_apply.cu", "k_mlp.cu", "k_zgemm.cu", "k_peak.cu"]
+CU = ["api.cu", "model.cu", "noalloc.cu", "solve.cu", "march.cu", "k_freq.cu", "k_entries.cu", "k_aca.cu", "k_apply.cu", "k_mlp.cu", "k_zgemm.cu", "k_peak.cu", "k_recompress.cu"]
 CPP = ["planner.cpp"]
 
 
