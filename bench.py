@@ -271,6 +271,7 @@ def main():
                     "--impl reference; twice as many for cpu_baseline)")
     ap.add_argument("--no-predictor", action="store_true", help="time the form without the rank predictor")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-recompress", action="store_true", help="skip the QR + SVD recompression measurement")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -374,6 +375,31 @@ def main():
     value, total_ms = job_throughput(sum(ms), evaluated, args.steps, world, dist)
     blocks = X.partition()
     apply_gflops = apply_flops(X, blocks, NQ, nrhs) / (apply_ms / 1e3) / 1e9
+    # QR + SVD recompression of the last tensor's far faces (Sec. 4, H-matrix
+    # variant) at eps_aca: time, storage and the apply afterwards (untimed step)
+    recompression = None
+    if not args.no_recompress:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        X.recompress(cfg["eps_aca"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st_rc = X.stats()
+        for _ in range(2):
+            X.apply_weighted(W, y)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        a0.record(stream)
+        X.apply_weighted(W, y)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        recompression = {"eps": cfg["eps_aca"], "ms": e0.elapsed_time(e1),
+                         "stored_complex_before": st["stored_complex"], "stored_complex_after": st_rc["stored_complex"],
+                         "sum_face_rank_before": st["sum_face_rank"], "sum_face_rank_after": st_rc["sum_face_rank"],
+                         "apply_ms_after": a0.elapsed_time(a1)}
     X = None
     res = [r[:3] for r in res]
 
@@ -460,6 +486,7 @@ def main():
             "predictor": dict(pinfo, pool_first_values=st["pool_first"], without=no_pred),
             "autotuned": tuned and {"far_threads_per_cta": tuned[0], "far_ctas_per_sm": tuned[1],
                                     "touching_pair_freqs_per_pass": tuned[2], "near_freqs_per_pass": tuned[3]},
+            "recompression": recompression,
             "fp64_form": fp64,
             "e2e": e2e,
             "roofline": roof,
