@@ -959,19 +959,22 @@ extern "C" int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op
     unsigned int *counter;
     const int nctas_near = std::min<int64_t>(std::max<int64_t>(1, (int64_t)near_ids.size()), (int64_t)ctx->num_sms * 8);
     const int nctas_far = std::min<int64_t>(std::max<int64_t>(1, (int64_t)far_ids.size()), (int64_t)ctx->num_sms * ctx->far_cps[pf]);
-    // dense faces for far blocks up to dense_cap entries, within a scratch budget of 8 GB
+    // dense faces of far blocks (up to td_far_dense_terms per block, packed)
+    // in dense_cap entries per CTA, within a scratch budget of 35 % of the
+    // free device memory, 8 to 80 GB
     int64_t dense_cap = 0;
     for (int32_t b : far_ids) {
         const int32_t *bl = &T->blocks[5 * b];
-        dense_cap = std::max<int64_t>(dense_cap, (int64_t)(bl[1] - bl[0]) * (bl[3] - bl[2]));
+        dense_cap = std::max<int64_t>(dense_cap, (int64_t)td_far_dense_terms() * (bl[1] - bl[0]) * (bl[3] - bl[2]));
     }
     {
-        const int64_t budget = (int64_t)8 << 30;
-        const int64_t per = (int64_t)es * (Nu + 1) * std::max(1, nctas_far);
-        dense_cap = std::min<int64_t>(dense_cap, budget / per);
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) cudaGetLastError();
+        const int64_t budget = std::min<int64_t>((int64_t)80 << 30, std::max<int64_t>((int64_t)8 << 30, (int64_t)(0.35 * (double)fr)));
+        dense_cap = std::min<int64_t>(dense_cap, budget / ((int64_t)es * std::max(1, nctas_far)));
         if (cfg->flags & 2) dense_cap = 0;  // low-rank evaluation for every far block
     }
-    const int64_t sper_far = (int64_t)kcap * (maxI + maxJ) + (int64_t)(Nu + 1) * dense_cap;
+    const int64_t sper_far = (int64_t)kcap * (maxI + maxJ) + dense_cap + std::min<int64_t>(dense_cap, td_far_cd_max());
     if ((rc = dalloc(ctx, &sig, 2 * Nu, &g.p)) || (rc = upload(ctx, sig, hs.data(), hs.size())) ||
         (rc = dalloc(ctx, &table, (size_t)npairs * Nu * 3, &g.p)) || (rc = dalloc(ctx, &nearbuf, es * max_batch_tens, &g.p)) ||
         (rc = dalloc(ctx, &scr_near, es * maxIJ * nctas_near, &g.p)) ||

@@ -303,6 +303,16 @@ constexpr int kNCoef = 512;
 // S = sum_t u_t v_t^T, densely (its rank-1 updates cost |I||J| per ACA step,
 // which pays off only for small blocks)
 constexpr int kDenseS = 1600;
+// Dense-face blocks keep the rebuilt faces H_d of their first terms in the
+// CTA's scratch, packed with stride |I||J|: min(kDenseTerms, capacity / |I||J|)
+// of them.  The residual fibres
+// are then corrected by sum_d f_d[k] H_d[i*, :] (l loads per entry instead of
+// one per earlier factor column, k_1 + ... + k_{l-1}), and eq. norm's
+// <H_l, H_d> is one pass over the dense faces.  Blocks up to kCdMax entries
+// form C(k) = sum_d f_d[k] H_d once per term instead (cheaper when the face
+// ranks exceed about |I| / 5).
+constexpr int kDenseTerms = 16;
+constexpr int kCdMax = 16384;
 
 // accumulation type of the inner products: FP32 in the mixed form
 template <class T>
@@ -649,6 +659,102 @@ TD_D bool rebuild_tiled_fp32(void *smem, const cx<T> *Uw, const cx<T> *Vw, int64
     }
 }
 
+// sum_{d < l} coef[d] H_d[e] over the dense faces (stride ds), eight
+// independent loads in flight.
+template <class T>
+TD_D cx<T> dense_prev(const cx<T> *Hs, int64_t ds, const cx<T> *coef, int l, int64_t e) {
+    cx<T> a4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int d = 0;
+    for (; d + 8 <= l; d += 8) {
+        cx<T> h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] = Hs[(int64_t)(d + q) * ds + e];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(a4[q & 3], coef[d + q], h[q]);
+    }
+    for (; d < l; ++d) cfma(a4[d & 3], coef[d], Hs[(int64_t)d * ds + e]);
+    return (a4[0] + a4[1]) + (a4[2] + a4[3]);
+}
+
+// sum_{t < kf} X[t sx + fixed] Y[t sy + idx]: the current face's own terms at
+// a fixed row (X = U, Y = V) or column (X = V, Y = U), eight independent
+// pairs of loads in flight.
+template <class T>
+TD_D cx<T> own_sum(const cx<T> *X, int64_t sx, int fixed, const cx<T> *Y, int64_t sy, int idx, int kf) {
+    cx<T> a4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int t = 0;
+    for (; t + 8 <= kf; t += 8) {
+        cx<T> xv[8], yv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            xv[q] = X[(int64_t)(t + q) * sx + fixed];
+            yv[q] = Y[(int64_t)(t + q) * sy + idx];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(a4[q & 3], xv[q], yv[q]);
+    }
+    for (; t < kf; ++t) cfma(a4[t & 3], X[(int64_t)t * sx + fixed], Y[(int64_t)t * sy + idx]);
+    return (a4[0] + a4[1]) + (a4[2] + a4[3]);
+}
+
+// sum_{i < n} x[i] conj(y[i]) over the lanes of a warp (each lane its part;
+// the caller sums over the warp), four pairs of loads in flight per lane.
+template <class T>
+TD_D DotAcc<T> lane_dot(const cx<T> *x, const cx<T> *y, int n, int lane) {
+    DotAcc<T> a, b;
+    int i = lane;
+    for (; i + 96 < n; i += 128) {
+        cx<T> xv[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            xv[u] = x[i + 32 * u];
+            yv[u] = y[i + 32 * u];
+        }
+        a.add(xv[0], yv[0]);
+        b.add(xv[1], yv[1]);
+        a.add(xv[2], yv[2]);
+        b.add(xv[3], yv[3]);
+    }
+    for (; i < n; i += 32) a.add(x[i], y[i]);
+    a.re += b.re;
+    a.im += b.im;
+    return a;
+}
+
+// eq. norm's <H_l, H_d> for every d <= l (< kDenseTerms) from the dense
+// faces: each thread sums its entries for all terms at once, so that every
+// face is read once; warp sums are added to gH (zero on entry).
+template <class T>
+TD_D void dense_grams(const cx<T> *Hs, int l, int64_t nIJ, AccT<T> *gH) {
+    DotAcc<T> acc[kDenseTerms];
+    const cx<T> *Hl = Hs + (int64_t)l * nIJ;
+    const int64_t st = blockDim.x;
+    // four entries per thread and pass: four loads in flight per face
+    for (int64_t e0 = threadIdx.x; e0 < nIJ; e0 += 4 * st) {
+        cx<T> h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h[u] = e0 + u * st < nIJ ? Hl[e0 + u * st] : cx<T>{0, 0};
+#pragma unroll
+        for (int d = 0; d < kDenseTerms; ++d) {
+            if (d > l) break;
+            cx<T> g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = e0 + u * st < nIJ ? Hs[(int64_t)d * nIJ + e0 + u * st] : cx<T>{0, 0};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[d].add(h[u], g[u]);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < kDenseTerms; ++d) {
+        if (d > l) break;
+        const AccT<T> re = acc[d].warp_re(), im = acc[d].warp_im();
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&gH[2 * d], re);
+            atomicAdd(&gH[2 * d + 1], im);
+        }
+    }
+}
+
 template <class T, int OP, int NT>
 __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
     static_assert(sizeof(GramTiles<float>) >=
@@ -670,8 +776,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
     cx<T> *Uw = (cx<T> *)a.scratch + (int64_t)blockIdx.x * a.scratch_per_cta;
     cx<T> *Vw = Uw + (int64_t)p.kcap * a.maxI;
-    cx<T> *Hs = Vw + (int64_t)p.kcap * a.maxJ;  // rebuilt faces of dense-path blocks [Nu][dense_cap]
-    cx<T> *Cd = Hs + (int64_t)Nu * a.dense_cap;  // C(k) of the current term [dense_cap]
+    cx<T> *Hs = Vw + (int64_t)p.kcap * a.maxJ;  // rebuilt faces of dense-face blocks [dense_cap]
+    cx<T> *Cd = Hs + a.dense_cap;                // C(k) of the current term [min(dense_cap, kCdMax)]
     const int64_t dcap = a.dense_cap;
     cx<T> *fib = (cx<T> *)o.fib;
     cx<T> *pool = (cx<T> *)o.face;
@@ -688,8 +794,11 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         const int *rows = a.perm_r + bl[0], *cols = a.perm_c + bl[2];
         const int64_t tb = (int64_t)b * Nu;
-        const bool small = (int64_t)nI * nJ <= dcap;       // dense faces in scratch
-        const bool dense_s = small && nI * nJ <= kDenseS;  // and the face's own S kept densely
+        const int64_t nIJb = (int64_t)nI * nJ;
+        const int nd = (int)min((int64_t)kDenseTerms, dcap / max(nIJb, (int64_t)1));  // dense faces kept
+        const bool dense_b = nd > 0;
+        const bool cd_b = dense_b && nI * nJ <= kCdMax;         // and C(k) formed once per term
+        const bool dense_sb = cd_b && nI * nJ <= kDenseS;       // and the face's own S kept densely
         for (int kk = tid; kk < Nu; kk += blockDim.x) F.sel[kk] = 0;
         if (tid == 0) S.normC2 = 0.0;
         __syncthreads();
@@ -701,12 +810,16 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             // dense-path blocks: C(k) = sum_d f_d[k] H_d from the rebuilt faces, once per
             // term; dense-S blocks also start the face's own approximation S = 0 in shared
             // memory (the Gram tiles' space, unused by these blocks), copied to H_l at the end
-            cx<T> *Sd = Hs + (int64_t)l * dcap;
+            cx<T> *Sd = Hs + (int64_t)l * nIJb;
+            // terms past kDenseTerms continue on the factors of the earlier terms
+            const bool small = dense_b && l < nd, cdm = cd_b && small, dense_s = dense_sb && small;
             for (int t = tid; t < 64; t += blockDim.x) S.nrow[t] = A(0);
-            if (small) {
+            if (small && !cdm)
+                for (int d = tid; d < l; d += blockDim.x) S.coef[d] = fib[(tb + d) * Nu + k];
+            if (cdm) {
                 for (int e = tid; e < nI * nJ; e += blockDim.x) {
                     cx<T> acc = {0, 0};
-                    for (int d = 0; d < l; ++d) cfma(acc, fib[(tb + d) * Nu + k], Hs[(int64_t)d * dcap + e]);
+                    for (int d = 0; d < l; ++d) cfma(acc, fib[(tb + d) * Nu + k], Hs[(int64_t)d * nIJb + e]);
                     Cd[e] = acc;
                     if (dense_s) Ss[e] = cx<T>{0, 0};
                 }
@@ -863,16 +976,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     // (u_t[i*] broadcast, v_t[j] coalesced), no coefficient list
                     __syncthreads();
                     for (int j = tid; j < nJ; j += blockDim.x) {
-                        cx<T> v = Vw[(int64_t)kf * a.maxJ + j] - Cd[(int64_t)istar * nJ + j];
-                        cx<T> c4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-                        int t = 0;
-                        for (; t + 4 <= kf; t += 4) {
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                cfma(c4[q], Uw[(int64_t)(t + q) * a.maxI + istar], Vw[(int64_t)(t + q) * a.maxJ + j]);
-                        }
-                        for (; t < kf; ++t) cfma(c4[0], Uw[(int64_t)t * a.maxI + istar], Vw[(int64_t)t * a.maxJ + j]);
-                        v = v - ((c4[0] + c4[1]) + (c4[2] + c4[3]));
+                        const int64_t ep = (int64_t)istar * nJ + j;
+                        cx<T> v = Vw[(int64_t)kf * a.maxJ + j] - (cdm ? Cd[ep] : dense_prev(Hs, nIJb, S.coef, l, ep));
+                        v = v - own_sum(Uw, (int64_t)a.maxI, istar, Vw, (int64_t)a.maxJ, j, kf);
                         Vw[(int64_t)kf * a.maxJ + j] = v;
                         const auto key = pivot_key(v);
                         if (am_better(key, j, am.v, am.i)) am = {key, j};
@@ -938,16 +1044,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                     cx<T> u = Uw[(int64_t)kf * a.maxI + i];
                     if (small) {
                         // previous terms from C(k); the face's own terms by each thread
-                        u = u - Cd[(int64_t)i * nJ + jstar];
-                        cx<T> c4[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-                        int t = 0;
-                        for (; t + 4 <= kf; t += 4) {
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                cfma(c4[q], Vw[(int64_t)(t + q) * a.maxJ + jstar], Uw[(int64_t)(t + q) * a.maxI + i]);
-                        }
-                        for (; t < kf; ++t) cfma(c4[0], Vw[(int64_t)t * a.maxJ + jstar], Uw[(int64_t)t * a.maxI + i]);
-                        u = u - ((c4[0] + c4[1]) + (c4[2] + c4[3]));
+                        const int64_t ep = (int64_t)i * nJ + jstar;
+                        u = u - (cdm ? Cd[ep] : dense_prev(Hs, nIJb, S.coef, l, ep));
+                        u = u - own_sum(Vw, (int64_t)a.maxJ, jstar, Uw, (int64_t)a.maxI, i, kf);
                         Uw[(int64_t)kf * a.maxI + i] = u;
                     }
                     if (used[i >> 5] & (1u << (i & 31))) continue;
@@ -982,9 +1081,8 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                             ++t;
                         }
                         const int t2 = rem;
-                        DotAcc<T> au, av;
-                        for (int i = lane; i < nI; i += 32) au.add(Uw[(int64_t)t * a.maxI + i], Uw[(int64_t)t2 * a.maxI + i]);
-                        for (int j = lane; j < nJ; j += 32) av.add(Vw[(int64_t)t * a.maxJ + j], Vw[(int64_t)t2 * a.maxJ + j]);
+                        const DotAcc<T> au = lane_dot(Uw + (int64_t)t * a.maxI, Uw + (int64_t)t2 * a.maxI, nI, lane);
+                        const DotAcc<T> av = lane_dot(Vw + (int64_t)t * a.maxJ, Vw + (int64_t)t2 * a.maxJ, nJ, lane);
                         const A ur = au.warp_re(), vr = av.warp_re();
                         if (t2 < t) {
                             const A ui = au.warp_im(), vi = av.warp_im();
@@ -1096,7 +1194,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
             // previous faces at the pivot
             for (int d = tid; d < l; d += blockDim.x) {
                 if (small) {
-                    F.hd[d] = Hs[(int64_t)d * dcap + am.i];
+                    F.hd[d] = Hs[(int64_t)d * nIJb + am.i];
                 } else {
                     const cx<T> *Ud = pool + F.foff[d];
                     const cx<T> *Vd = Ud + (int64_t)F.frank[d] * nI;
@@ -1117,20 +1215,11 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, 
                 }
             }
             ev_tube += Nu;
-            // eq. norm: <H_l, H_d> for d <= l; small blocks from the dense faces (one
-            // warp per term), others from the factors:
+            // eq. norm: <H_l, H_d> for d <= l; dense-face blocks from the dense faces
+            // (one pass), others from the factors:
             // sum_{t,tau} <u_t, U_d[tau]> <v_t, V_d[tau]>
             if (small) {
-                for (int d = wid; d <= l; d += nwarps) {
-                    const cx<T> *Hl = Hs + (int64_t)l * dcap, *Hd = Hs + (int64_t)d * dcap;
-                    DotAcc<T> acc;
-                    for (int64_t e = lane; e < nIJ; e += 32) acc.add(Hl[e], Hd[e]);
-                    const A gr = acc.warp_re(), gi = acc.warp_im();
-                    if (lane == 0) {
-                        F.gH[2 * d] = gr;
-                        F.gH[2 * d + 1] = gi;
-                    }
-                }
+                dense_grams(Hs, l, nIJ, F.gH);
                 __syncthreads();
             } else {
                 gram_sums(F, *gt, l, kf, nI, nJ, pool, Uw, Vw, a.maxI, a.maxJ);
@@ -1296,6 +1385,9 @@ static int launch_far(cudaStream_t st, const MeshDev &m, const FarArgs &a, const
     if (nt <= 128) return launch_far_nt<T, OP, 128>(st, m, a, o, p, nctas);
     return launch_far_nt<T, OP, 256>(st, m, a, o, p, nctas);
 }
+
+int td_far_dense_terms() { return kDenseTerms; }
+int td_far_cd_max() { return kCdMax; }
 
 int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
                       const TensorOut &o, const AcaParams &p, int nctas, int nt) {

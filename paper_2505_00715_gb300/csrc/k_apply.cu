@@ -152,122 +152,168 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
 
 // Second phase of the tensor-core apply.  The frequency contraction
 // z_(b,d,p) = sum_l f_d(l) W_l[J] is already in Z (k_zgemm.cu); Z rows of a
-// block are (term d, half p) at zbase[b] + (rpt d + p) nJ nrhs.
-//   k_apply_t: one warp per far term: T_p = V_d^T z_p (p = 1: conj V_d),
-//              16 ranks at a time in registers, lanes over (half, rhs);
-//   k_apply_y: one CTA per block, one thread per output (row, rhs), all
-//              terms accumulated in registers: far y_I += U_d T1 + conj(U_d) T2,
-//              near y_I += H_d z1 + conj(H_d) z2; one atomic add per output
-//              and block.  No shared memory and no barriers in either kernel.
-__global__ void __launch_bounds__(256) k_apply_t(ApplyZArgs a, TensorOut o) {
-    const int nrhs = a.nrhs, Nu = a.Nu, rpt = a.rpt, lane = threadIdx.x & 31;
-    const c32 *pool = (const c32 *)o.face;
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = gw; it < a.nft; it += nwt) {
-        const int2 bd = a.ftab[it];
-        const int *bl = a.blocks + 5 * bd.x;
-        const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
-        const int64_t tb = (int64_t)bd.x * Nu + bd.y;
-        const int kd = o.frank[tb];
-        const c32 *V = pool + o.foff[tb] + (int64_t)kd * nI;
-        const int64_t L = (int64_t)nJ * nrhs;
-        const c32 *z1 = a.Z + a.zbase[bd.x] + (int64_t)rpt * bd.y * L;
-        c32 *Tout = a.T + a.toff[tb];
-        for (int pc = lane; pc < rpt * nrhs; pc += 32) {
-            const int p = pc / nrhs, c = pc - p * nrhs;
-            const c32 *z = z1 + p * L + c;
-            for (int t0 = 0; t0 < kd; t0 += 16) {
-                const int nt = min(16, kd - t0);
-                c32 acc[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) acc[q] = c32{0.f, 0.f};
-                for (int j = 0; j < nJ; ++j) {
-                    const c32 zj = z[(int64_t)j * nrhs];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (q < nt) {
-                            const c32 v = V[(int64_t)(t0 + q) * nJ + j];
-                            cfma(acc[q], p ? cconj(v) : v, zj);
-                        }
-                }
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (q < nt) Tout[((int64_t)p * kd + t0 + q) * nrhs + c] = acc[q];
-            }
-        }
-    }
-}
+// block are (term d, half p) at zbase[b] + (rpt d + p) nJ nrhs.  Both face
+// stages are small complex GEMMs out[m][(p, c)] = sum_k A_p[m][k] B[k][(p, c)]
+// with A_1 = conj(A_0) for the conjugate half, tiled through shared memory:
+//   stage 0 (one CTA per far term):  T_p = V_d^T z_p, m = tau < k_d, k = j < |J|,
+//            A = V_d (row-major), written to T;
+//   stage 1 (one CTA per block):      y_I += sum_d U_d T_(d,1) + conj(U_d) T_(d,2)
+//            (far; m = i, k = (d, tau), A = U_d^T, column-major) or
+//            y_I += sum_d H_d z_(d,1) + conj(H_d) z_(d,2) (near; k = (d, j),
+//            A = H_d row-major); both halves summed before one atomic add
+//            per output.
+// Tiles: 64 rows x (rpt nrhs) columns, k in chunks of 32; every thread holds
+// a 4 x CPT register tile (rows 4 ty .. 4 ty + 3, columns tx + 16 q).
+constexpr int kFM = 64, kFK = 32, kFPad = 65;
 
-__global__ void __launch_bounds__(256) k_apply_y(ApplyZArgs a, TensorOut o) {
-    // each thread: one row i and four consecutive right-hand sides (face
-    // loads shared by the four)
-    const int nrhs = a.nrhs, Nu = a.Nu, rpt = a.rpt;
-    const int nc4 = (nrhs + 3) >> 2;
+struct FaceSmem {
+    c32 A[kFK][kFPad];  // A[k][m] (m contiguous)
+};
+
+template <int CPT>
+__global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FaceSmem &F = *reinterpret_cast<FaceSmem *>(smem_raw);
+    c32 *Bs = reinterpret_cast<c32 *>(smem_raw + sizeof(FaceSmem));  // [kFK][ncol]
+    const int nrhs = a.nrhs, Nu = a.Nu, rpt = a.rpt, ncol = rpt * nrhs;
     const c32 *pool = (const c32 *)o.face;
-    for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // columns of this thread and their half; both halves of one right-hand side
+    // sit in the same thread (q and q + CPT / 2) when 2 nrhs = 16 CPT
+    bool conj_q[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) conj_q[q] = tx + 16 * q >= nrhs;
+    const bool pair_halves = CPT >= 2 && rpt == 2 && 2 * nrhs == 16 * CPT;
+    const int64_t njobs = stage == 0 ? a.nft : a.nb;
+    for (int64_t job = blockIdx.x; job < njobs; job += gridDim.x) {
+        int b, d0, d1, M;
+        if (stage == 0) {
+            const int2 bd = a.ftab[job];
+            b = bd.x;
+            d0 = bd.y;
+            d1 = bd.y + 1;
+        } else {
+            b = (int)job;
+            d0 = 0;
+            d1 = o.rank[b];
+            if (d1 == 0 || a.zbase[b] < 0) continue;
+        }
         const int *bl = a.blocks + 5 * b;
         const int nI = bl[1] - bl[0], nJ = bl[3] - bl[2];
         const bool far = bl[4] != 0;
-        const int r = o.rank[b];
-        if (r == 0 || a.zbase[b] < 0) continue;
         const int64_t tb = (int64_t)b * Nu, L = (int64_t)nJ * nrhs;
-        for (int e = threadIdx.x; e < nI * nc4; e += blockDim.x) {
-            const int i = e / nc4, c0 = 4 * (e - i * nc4), nc = min(4, nrhs - c0);
-            c32 acc[4];
+        M = stage == 0 ? o.frank[tb + d0] : nI;
+        for (int m0 = 0; m0 < M; m0 += kFM) {
+            c32 acc[4][CPT];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = c32{0.f, 0.f};
-            for (int d = 0; d < r; ++d) {
-                const c32 *X1, *X2, *M;
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) acc[x][q] = c32{0.f, 0.f};
+            for (int d = d0; d < d1; ++d) {
+                const int kd = o.frank[tb + d];
+                const c32 *face = pool + o.foff[tb + d];
+                // A operand, its layout and length; B operand rows (p = 0 / 1)
+                const c32 *Ab;
+                int64_t lda;
+                bool acol;
                 int K;
-                int64_t ms;
-                if (far) {
-                    K = o.frank[tb + d];
-                    M = pool + o.foff[tb + d] + i;  // U[t][i], stride nI
-                    ms = nI;
-                    X1 = a.T + a.toff[tb + d] + c0;
-                    X2 = X1 + (int64_t)K * nrhs;
-                } else {
+                const c32 *B0;
+                int64_t bstride;  // B[k][(p, c)] = B0[p * bstride + k * nrhs + c]
+                if (stage == 0) {
+                    Ab = face + (int64_t)kd * nI;  // V[tau][j]
+                    lda = nJ;
+                    acol = false;
                     K = nJ;
-                    M = pool + o.foff[tb + d] + (int64_t)i * nJ;  // H[i][j], stride 1
-                    ms = 1;
-                    X1 = a.Z + a.zbase[b] + (int64_t)rpt * d * L + c0;
-                    X2 = X1 + L;
+                    B0 = a.Z + a.zbase[b] + (int64_t)rpt * d * L;
+                    bstride = L;
+                } else if (far) {
+                    Ab = face;  // U[tau][i]: A[i][tau] column-major
+                    lda = nI;
+                    acol = true;
+                    K = kd;
+                    B0 = a.T + a.toff[tb + d];
+                    bstride = (int64_t)kd * nrhs;
+                } else {
+                    Ab = face;  // H[i][j]
+                    lda = nJ;
+                    acol = false;
+                    K = nJ;
+                    B0 = a.Z + a.zbase[b] + (int64_t)rpt * d * L;
+                    bstride = L;
                 }
-                // face entries four at a time, loaded before use (the loop is bound by
-                // the latency of these loads from HBM)
-                int t = 0;
-                for (; t + 4 <= K; t += 4) {
-                    c32 mv[4];
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) mv[s] = M[(int64_t)(t + s) * ms];
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        const c32 mc = cconj(mv[s]);
-                        const c32 *x1 = X1 + (int64_t)(t + s) * nrhs, *x2 = X2 + (int64_t)(t + s) * nrhs;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (q >= nc) continue;
-                            cfma(acc[q], mv[s], x1[q]);
-                            if (rpt == 2) cfma(acc[q], mc, x2[q]);
+                for (int k0 = 0; k0 < K; k0 += kFK) {
+                    const int kc = min(kFK, K - k0), mc = min(kFM, M - m0);
+                    __syncthreads();
+                    if (acol) {
+                        for (int e = tid; e < kFK * kFM; e += 256) {
+                            const int kk = e / kFM, mm = e - kk * kFM;
+                            F.A[kk][mm] = (kk < kc && mm < mc) ? Ab[(int64_t)(k0 + kk) * lda + m0 + mm] : c32{0.f, 0.f};
+                        }
+                    } else {
+                        for (int e = tid; e < kFK * kFM; e += 256) {
+                            const int mm = e / kFK, kk = e - mm * kFK;
+                            F.A[kk][mm] = (kk < kc && mm < mc) ? Ab[(int64_t)(m0 + mm) * lda + k0 + kk] : c32{0.f, 0.f};
                         }
                     }
-                }
-                for (; t < K; ++t) {
-                    const c32 mv = M[(int64_t)t * ms], mc = cconj(mv);
-                    const c32 *x1 = X1 + (int64_t)t * nrhs, *x2 = X2 + (int64_t)t * nrhs;
+                    for (int e = tid; e < kFK * ncol; e += 256) {
+                        const int kk = e / ncol, n = e - kk * ncol, p = n / nrhs, c = n - p * nrhs;
+                        Bs[e] = kk < kc ? B0[p * bstride + (int64_t)(k0 + kk) * nrhs + c] : c32{0.f, 0.f};
+                    }
+                    __syncthreads();
+#pragma unroll 4
+                    for (int kk = 0; kk < kFK; ++kk) {
+                        c32 av[4], bv[CPT];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (q >= nc) continue;
-                        cfma(acc[q], mv, x1[q]);
-                        if (rpt == 2) cfma(acc[q], mc, x2[q]);
+                        for (int x = 0; x < 4; ++x) av[x] = F.A[kk][4 * ty + x];
+#pragma unroll
+                        for (int q = 0; q < CPT; ++q) {
+                            const int n = tx + 16 * q;
+                            bv[q] = n < ncol ? Bs[kk * ncol + n] : c32{0.f, 0.f};
+                        }
+#pragma unroll
+                        for (int x = 0; x < 4; ++x)
+#pragma unroll
+                            for (int q = 0; q < CPT; ++q) {
+                                // conjugate half: conj(a) b
+                                const float ay = conj_q[q] ? -av[x].y : av[x].y;
+                                acc[x][q].x = fmaf(av[x].x, bv[q].x, fmaf(-ay, bv[q].y, acc[x][q].x));
+                                acc[x][q].y = fmaf(av[x].x, bv[q].y, fmaf(ay, bv[q].x, acc[x][q].y));
+                            }
                     }
                 }
             }
-            c32 *yr = a.y + (int64_t)a.perm_r[bl[0] + i] * nrhs + c0;
+            // ---- output
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < nc) atomic_add_c(yr + q, acc[q]);
+            for (int x = 0; x < 4; ++x) {
+                const int m = m0 + 4 * ty + x;
+                if (m >= M) continue;
+                if (stage == 0) {
+                    const int kd = M;
+                    c32 *Tout = a.T + a.toff[tb + d0];
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) {
+                        const int n = tx + 16 * q;
+                        if (n >= ncol) continue;
+                        const int p = n / nrhs, c = n - p * nrhs;
+                        Tout[((int64_t)p * kd + m) * nrhs + c] = acc[x][q];
+                    }
+                } else {
+                    c32 *yr = a.y + (int64_t)a.perm_r[bl[0] + m] * nrhs;
+                    if (pair_halves) {
+#pragma unroll
+                        for (int q = 0; q < CPT / 2; ++q) {
+                            const int c = tx + 16 * q;
+                            if (c < nrhs) atomic_add_c(yr + c, acc[x][q] + acc[x][q + CPT / 2]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < CPT; ++q) {
+                            const int n = tx + 16 * q;
+                            if (n < ncol) atomic_add_c(yr + n % nrhs, acc[x][q]);
+                        }
+                    }
+                }
+            }
         }
     }
 }
@@ -348,14 +394,27 @@ int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorO
     return (int)cudaGetLastError();
 }
 
-int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms) {
-    if (a.nft > 0) {
-        const int grid = (int)std::min<int64_t>(((int64_t)a.nft * 32 + 255) / 256, (int64_t)num_sms * 8);
-        k_apply_t<<<grid, 256, 0, st>>>(a, o);
-    }
-    const int grid = std::min(a.nb, num_sms * 8);
-    k_apply_y<<<grid, 256, 0, st>>>(a, o);
+template <int CPT>
+static int launch_faces(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int stage, int grid) {
+    const size_t sm = sizeof(FaceSmem) + sizeof(c32) * kFK * a.rpt * a.nrhs;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_faces<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    k_apply_faces<CPT><<<grid, 256, sm, st>>>(a, o, stage);
     return (int)cudaGetLastError();
+}
+
+int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms) {
+    const int ncol = a.rpt * a.nrhs;
+    auto run = [&](int stage, int grid) {
+        if (ncol <= 16) return launch_faces<1>(st, a, o, stage, grid);
+        if (ncol <= 32) return launch_faces<2>(st, a, o, stage, grid);
+        if (ncol <= 64) return launch_faces<4>(st, a, o, stage, grid);
+        return launch_faces<8>(st, a, o, stage, grid);
+    };
+    int e = 0;
+    if (a.nft > 0) e = run(0, (int)std::min<int64_t>(a.nft, (int64_t)num_sms * 16));
+    if (!e && a.nb > 0) e = run(1, std::min(a.nb, num_sms * 16));
+    return e;
 }
 
 int td_launch_tensor_entries(cudaStream_t st, int prec, const TensorOut &o, const int *blocks,

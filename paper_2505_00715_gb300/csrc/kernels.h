@@ -47,16 +47,17 @@ struct FarArgs {
     const double *sig;      // [2*Nu]
     int nf;
     int maxI, maxJ;
-    void *scratch;          // per-CTA workspace: U [kcap][maxI], V [kcap][maxJ], then for far
-                            // blocks with |I||J| <= dense_cap the rebuilt faces [Nu][dense_cap]
-                            // and the correction C(k) [dense_cap]
+    void *scratch;          // per-CTA workspace: U [kcap][maxI], V [kcap][maxJ], the rebuilt
+                            // dense faces of the first min(td_far_dense_terms(),
+                            // dense_cap / |I||J|) terms [dense_cap], the correction C(k)
+                            // [min(dense_cap, td_far_cd_max())]
     int64_t scratch_per_cta;  // complex units
     unsigned int *counter;  // work queue head
     int64_t *evals;         // [3] regular, tube entries evaluated; ACA stopping tests of the
                             // low-rank-norm faces (one per synchronised test round)
     int *harvest;           // non-null: record face-ACA ranks per (far block, frequency), [nfar][Nu]
     const int *kpred;       // nullable: predicted face rank per (block id, frequency) [nb][Nu]
-    int64_t dense_cap;      // largest |I||J| handled with dense faces (0: none)
+    int64_t dense_cap;      // complex entries of dense faces per CTA (0: none)
     int *redo;              // nullable: ids of blocks stopped by a full face pool [nfar]
     unsigned int *redo_count;
 };
@@ -77,6 +78,11 @@ int td_sing_fc(int op, int variant);
 int td_near_fc(int variant);
 int td_launch_near_aca(cudaStream_t st, int prec, const NearArgs &a, const TensorOut &o,
                        const AcaParams &p, void *scratch, int64_t scratch_per_cta, int nctas);
+// Dense faces a far-field CTA keeps per block at most, and the largest block
+// that forms C(k) once per term (the scratch of a CTA holds dense_cap entries
+// of packed dense faces and min(dense_cap, td_far_cd_max()) for C(k)).
+int td_far_dense_terms();
+int td_far_cd_max();
 int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const FarArgs &a,
                       const TensorOut &o, const AcaParams &p, int nctas, int nt);
 // k_aca.cu: entries by the far-field engine's point-pair groups (fibres, tubes)
