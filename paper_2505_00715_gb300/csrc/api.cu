@@ -1349,8 +1349,11 @@ extern "C" int tdbem_tensor_destroy(tdbem_tensor_t t) {
 // ============================================================================
 namespace {
 // Plan of the tensor-core apply for nrhs right-hand sides: the Z rows
-// (block, term, half) grouped by column cluster, the tile jobs of the GEMM
-// and each block's first Z row.  Host work O(nblocks * rank + jobs).
+// (block, term, half) grouped by column cluster, half 0 first (each half's
+// rows block by block, term by term), the tile jobs of the GEMM (a tile holds
+// rows of one half and contracts over that half's frequencies), the
+// frequency order of the contraction, and each block's first Z row and
+// half-1 offset.  Host work O(nblocks * rank + jobs).
 int build_apply_plan(tdbem_tensor *t, int nrhs) {
     tdbem_ctx *ctx = t->ctx;
     if (t->plan_nrhs == nrhs) return TDBEM_OK;
@@ -1359,10 +1362,17 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     int rpt = 1;
     for (int q = 0; q < t->NQ; ++q)
         if (qmap[q] < 0) rpt = 2;
+    // contraction order: the frequencies of half 0, then the conjugate half
+    std::vector<int32_t> lperm;
+    for (int q = 0; q < t->NQ; ++q)
+        if (qmap[q] > 0) lperm.push_back(q);
+    const int nq0 = (int)lperm.size();
+    for (int q = 0; q < t->NQ; ++q)
+        if (qmap[q] <= 0) lperm.push_back(q);
     const int64_t nb = t->nblocks;
     std::vector<ZGroup> groups;
-    std::vector<std::vector<int2>> rows;
-    std::vector<int64_t> zbase(nb, -1), brow(nb, -1);
+    std::vector<std::vector<int32_t>> gblocks;
+    std::vector<int64_t> zbase(nb, -1), zpstride(nb, 0), brow(nb, -1);
     std::vector<int> bgroup(nb, -1);
     std::map<std::pair<int, int>, int> gid;
     for (int64_t b = 0; b < nb; ++b) {
@@ -1379,14 +1389,14 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
             zg.J0 = bl[2];
             zg.nJ = bl[3] - bl[2];
             groups.push_back(zg);
-            rows.emplace_back();
+            gblocks.emplace_back();
         } else {
             g = it->second;
         }
         bgroup[b] = g;
-        brow[b] = (int64_t)rows[g].size();
-        for (int d = 0; d < r; ++d)
-            for (int p = 0; p < rpt; ++p) rows[g].push_back(make_int2((int)b, 2 * d + p));
+        brow[b] = groups[g].Mh;  // first half-0 row of the block within its group
+        groups[g].Mh += r;
+        gblocks[g].push_back((int32_t)b);
     }
     std::vector<int2> rowtab;
     std::vector<ZJob> jobs;
@@ -1395,16 +1405,23 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     for (size_t g = 0; g < groups.size(); ++g) {
         ZGroup &zg = groups[g];
         zg.row0 = (int)rowtab.size();
-        zg.M = (int)rows[g].size();
+        zg.M = rpt * zg.Mh;
         zg.L = zg.nJ * nrhs;
         zg.zoff = zsize;
         zsize += (int64_t)zg.M * zg.L;
-        rowtab.insert(rowtab.end(), rows[g].begin(), rows[g].end());
-        for (int m0 = 0; m0 < zg.M; m0 += TM)
-            for (int n0 = 0; n0 < zg.L; n0 += TN) jobs.push_back(ZJob{(int)g, m0, n0, 0});
+        for (int p = 0; p < rpt; ++p)
+            for (int32_t b : gblocks[g])
+                for (int d = 0; d < t->rank[b]; ++d) rowtab.push_back(make_int2((int)b, 2 * d + p));
+        for (int p = 0; p < rpt; ++p)
+            for (int m0 = p * zg.Mh; m0 < (p + 1) * zg.Mh; m0 += TM)
+                for (int n0 = 0; n0 < zg.L; n0 += TN) jobs.push_back(ZJob{(int)g, m0, n0, rpt == 2 ? p + 1 : 0});
     }
     for (int64_t b = 0; b < nb; ++b)
-        if (bgroup[b] >= 0) zbase[b] = groups[bgroup[b]].zoff + brow[b] * groups[bgroup[b]].L;
+        if (bgroup[b] >= 0) {
+            const ZGroup &zg = groups[bgroup[b]];
+            zbase[b] = zg.zoff + brow[b] * zg.L;
+            zpstride[b] = (int64_t)zg.Mh * zg.L;
+        }
     // far terms and their T offsets (k_d from the device copy of the face ranks)
     std::vector<int32_t> frank((size_t)nb * t->Nu);
     TD_CUDA(ctx, cudaMemcpy(frank.data(), t->dfrank, sizeof(int32_t) * frank.size(), cudaMemcpyDeviceToHost));
@@ -1428,7 +1445,7 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     t->plan_mem = t->plan_Z = nullptr;
     t->plan_nrhs = 0;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off[7];
+    size_t off[9];
     off[0] = 0;
     off[1] = off[0] + al(sizeof(ZGroup) * groups.size());
     off[2] = off[1] + al(sizeof(int2) * rowtab.size());
@@ -1436,8 +1453,10 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     off[4] = off[3] + al(sizeof(int64_t) * nb);
     off[5] = off[4] + al(sizeof(int2) * ftab.size());
     off[6] = off[5] + al(sizeof(int64_t) * toff.size());
+    off[7] = off[6] + al(sizeof(int64_t) * nb);
+    off[8] = off[7] + al(sizeof(int32_t) * lperm.size());
     char *mem = nullptr;
-    if (cudaMalloc(&mem, std::max<size_t>(off[6], 256)) != cudaSuccess ||
+    if (cudaMalloc(&mem, std::max<size_t>(off[8], 256)) != cudaSuccess ||
         cudaMalloc(&t->plan_Z, sizeof(c32) * (std::max<int64_t>(zsize, 1) + tsize)) != cudaSuccess) {
         cudaGetLastError();
         if (mem) cudaFree(mem);
@@ -1451,10 +1470,13 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     TD_CUDA(ctx, cudaMemcpy(mem + off[3], zbase.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice));
     TD_CUDA(ctx, cudaMemcpy(mem + off[4], ftab.data(), sizeof(int2) * ftab.size(), cudaMemcpyHostToDevice));
     TD_CUDA(ctx, cudaMemcpy(mem + off[5], toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
-    for (int k = 0; k < 6; ++k) t->plan_off[k] = off[k];
+    TD_CUDA(ctx, cudaMemcpy(mem + off[6], zpstride.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice));
+    TD_CUDA(ctx, cudaMemcpy(mem + off[7], lperm.data(), sizeof(int32_t) * lperm.size(), cudaMemcpyHostToDevice));
+    for (int k = 0; k < 8; ++k) t->plan_off[k] = off[k];
     t->plan_nft = (int)ftab.size();
     t->plan_tz = std::max<int64_t>(zsize, 1);  // T follows Z in plan_Z
     t->plan_rpt = rpt;
+    t->plan_nq0 = nq0;
     t->plan_njobs = (int)jobs.size();
     t->plan_maxI = t->plan_maxJ = 1;
     for (int64_t b = 0; b < nb; ++b) {
@@ -1476,9 +1498,10 @@ int apply_tc(tdbem_tensor *t, const void *W, int nrhs, void *y) {
     const int2 *rowtab = (const int2 *)(mem + t->plan_off[1]);
     const ZJob *jobs = (const ZJob *)(mem + t->plan_off[2]);
     const int64_t *zbase = (const int64_t *)(mem + t->plan_off[3]);
-    int e = td_launch_zgemm_apply(ctx->stream, groups, rowtab, t->dpartner, (const c32 *)t->dfib, (const c32 *)W,
-                                  t->dperm_c, (c32 *)t->plan_Z, t->Nu, nrhs, t->ncols, t->NQ, jobs, t->plan_njobs,
-                                  ctx->dflags, ctx->wait_polls, ctx->num_sms);
+    int e = td_launch_zgemm_apply(ctx->stream, groups, rowtab, t->dpartner, (const int *)(mem + t->plan_off[7]),
+                                  t->plan_nq0, (const c32 *)t->dfib, (const c32 *)W, t->dperm_c, (c32 *)t->plan_Z,
+                                  t->Nu, nrhs, t->ncols, t->NQ, jobs, t->plan_njobs, ctx->dflags, ctx->wait_polls,
+                                  ctx->num_sms);
     if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "tensor-core contraction failed: %s", cudaGetErrorString((cudaError_t)e));
     ApplyZArgs a{};
     a.nb = (int)t->nblocks;
@@ -1488,6 +1511,7 @@ int apply_tc(tdbem_tensor *t, const void *W, int nrhs, void *y) {
     a.nrhs = nrhs;
     a.rpt = t->plan_rpt;
     a.zbase = zbase;
+    a.zpstride = (const int64_t *)(mem + t->plan_off[6]);
     a.Z = (const c32 *)t->plan_Z;
     a.y = (c32 *)y;
     a.nft = t->plan_nft;

@@ -117,7 +117,8 @@ struct tdbem_tensor {
     // changes: groups | row table | jobs | per-block Z offsets, and Z itself
     int plan_nrhs = 0, plan_rpt = 1, plan_njobs = 0, plan_maxI = 1, plan_maxJ = 1;
     void *plan_mem = nullptr, *plan_Z = nullptr;
-    size_t plan_off[6] = {0, 0, 0, 0, 0, 0};
+    size_t plan_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int plan_nq0 = 0;
     int plan_nft = 0;
     int64_t plan_tz = 0;
     size_t host_buf_bytes = 0;

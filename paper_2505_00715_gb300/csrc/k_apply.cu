@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
 
 // Second phase of the tensor-core apply.  The frequency contraction
 // z_(b,d,p) = sum_l f_d(l) W_l[J] is already in Z (k_zgemm.cu); Z rows of a
-// block are (term d, half p) at zbase[b] + (rpt d + p) nJ nrhs.  Both face
+// block are (term d, half p) at zbase[b] + p zpstride[b] + d nJ nrhs.  Both face
 // stages are small complex GEMMs out[m][(p, c)] = sum_k A_p[m][k] B[k][(p, c)]
 // with A_1 = conj(A_0) for the conjugate half, tiled through shared memory:
 //   stage 0 (one CTA per far term):  T_p = V_d^T z_p, m = tau < k_d, k = j < |J|,
@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, 
                     lda = nJ;
                     acol = false;
                     K = nJ;
-                    B0 = a.Z + a.zbase[b] + (int64_t)rpt * d * L;
-                    bstride = L;
+                    B0 = a.Z + a.zbase[b] + (int64_t)d * L;
+                    bstride = a.zpstride[b];
                 } else if (far) {
                     Ab = face;  // U[tau][i]: A[i][tau] column-major
                     lda = nI;
@@ -238,8 +238,8 @@ __global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, 
                     lda = nJ;
                     acol = false;
                     K = nJ;
-                    B0 = a.Z + a.zbase[b] + (int64_t)rpt * d * L;
-                    bstride = L;
+                    B0 = a.Z + a.zbase[b] + (int64_t)d * L;
+                    bstride = a.zpstride[b];
                 }
                 for (int k0 = 0; k0 < K; k0 += kFK) {
                     const int kc = min(kFK, K - k0), mc = min(kFM, M - m0);

@@ -16,10 +16,11 @@
 // dropped), which keeps about 16 mantissa bits of every product.
 //
 // A tile is 128 complex rows (the 128 TMEM lanes) x 128 complex columns
-// (256 FP32 TMEM columns); K is consumed in chunks of 64 complex values
-// (128 real = 8 MMAs of K = 16 per split term).  One CTA of 256 threads per
-// SM (the operand tiles take 192 KB of shared memory); tiles are taken from
-// a job list in a persistent loop.  Used by the weighted apply (the
+// (256 FP32 TMEM columns); K is consumed in chunks of 32 complex values
+// (64 real = 4 MMAs of K = 16 per split term).  Two CTAs of 256 threads per
+// SM (the operand tiles take 96 KB of shared memory and 256 TMEM columns per
+// CTA), so that one CTA's operand loads overlap the other's MMAs; tiles are
+// taken from a job list in a persistent loop.  Used by the weighted apply (the
 // frequency contraction of eq. product) and exposed for testing as
 // tdbem_zgemm.
 #include <cuda_bf16.h>
@@ -32,10 +33,11 @@ namespace {
 
 constexpr int kTM = 128;                       // complex rows per tile
 constexpr int kTN = 128;                       // complex columns per tile
-constexpr int kTK = 64;                        // complex K per chunk
+constexpr int kTK = 32;                        // complex K per chunk
+constexpr int kKS = 2 * kTK / 16;              // MMA K-steps (16 real K each) per chunk
 constexpr int kThreads = 256;
-constexpr int kABytes = kTM * 2 * kTK * 2;     // one split part of A: 32 KB
-constexpr int kBBytes = 2 * kTN * 2 * kTK * 2; // one split part of B: 64 KB
+constexpr int kABytes = kTM * 2 * kTK * 2;     // one split part of A: 16 KB
+constexpr int kBBytes = 2 * kTN * 2 * kTK * 2; // one split part of B: 32 KB
 constexpr int kSmemBytes = 2 * kABytes + 2 * kBBytes + 1024 + 64;
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kMaxPolls = 1u << 24;  // default poll limit of a tensor-core wait
@@ -76,6 +78,10 @@ struct DenseOps {
     TD_D int rows(const ZJob &j) const { return min(kTM, M - j.m0); }
     TD_D int cols(const ZJob &j) const { return min(kTN, N - j.n0); }
     TD_D c32 *drow(const ZJob &, int m) const { return D + (int64_t)m * ldd; }
+    TD_D void krange(const ZJob &, int K, int &kb, int &ke) const {
+        kb = 0;
+        ke = K;
+    }
 };
 
 // Frequency contraction of the apply: rows (block b, term d, half p) of a
@@ -83,10 +89,16 @@ struct DenseOps {
 //   A[(b,d,p)][l] = f_d(l) if l belongs to half p (p = 1: conjugate half,
 //                   coefficient conj(f_d[u])), else 0
 //   Z[(b,d,p)][(j,c)] = sum_l A[(b,d,p)][l] W[l][J0 + j][c]
+// The contraction index runs over the frequencies in the order lperm (half 0
+// first); the rows of a group are ordered half 0 then half 1, and a tile of
+// one half contracts over that half's frequencies only (the other half's
+// coefficients are zero).
 struct ApplyOps {
     const ZGroup *groups;
     const int2 *rowtab;   // (block, 2 * term + half) per Z row
     const int *qmap;      // [NQ]
+    const int *lperm;     // [NQ] contraction order of the frequencies
+    int nq0;              // frequencies of half 0 (first in lperm)
     const c32 *fib;       // [nb][Nu][Nu]
     const c32 *W;         // [NQ][ncols][nrhs]
     const int *perm_c;
@@ -99,7 +111,7 @@ struct ApplyOps {
         const c32 *fr = fib + ((int64_t)rt.x * Nu + (rt.y >> 1)) * Nu;
         int qm[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) qm[e] = l + e < lend ? qmap[l + e] : 0;
+        for (int e = 0; e < 8; ++e) qm[e] = l + e < lend ? qmap[lperm[l + e]] : 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const bool on = qm[e] != 0 && (qm[e] > 0 ? 0 : 1) == half;
@@ -113,9 +125,17 @@ struct ApplyOps {
         const c32 *w = W + (int64_t)perm_c[g.J0 + jj] * nrhs + c;
         const int64_t ls = ncols * nrhs;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = l + e < lend ? w[(int64_t)(l + e) * ls] : c32{0.f, 0.f};
+        for (int e = 0; e < 8; ++e) x[e] = l + e < lend ? w[(int64_t)lperm[l + e] * ls] : c32{0.f, 0.f};
     }
-    TD_D int rows(const ZJob &j) const { return min(kTM, groups[j.g].M - j.m0); }
+    TD_D int rows(const ZJob &j) const { return min(kTM, (j.half == 1 ? groups[j.g].Mh : groups[j.g].M) - j.m0); }
+    TD_D void krange(const ZJob &j, int K, int &kb, int &ke) const {
+        kb = j.half == 2 ? nq0 : 0;
+        ke = j.half == 1 ? nq0 : K;
+        if (kb >= ke) {  // (no such job is planned) every frequency: the other half's coefficients are zero
+            kb = 0;
+            ke = K;
+        }
+    }
     TD_D int cols(const ZJob &j) const { return min(kTN, groups[j.g].L - j.n0); }
     TD_D c32 *drow(const ZJob &j, int m) const {
         const ZGroup &g = groups[j.g];
@@ -124,7 +144,7 @@ struct ApplyOps {
 };
 
 template <class Ops>
-__global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs, int njobs, int K, int *err,
+__global__ void __launch_bounds__(kThreads, 2) k_zgemm(Ops ops, const ZJob *jobs, int njobs, int K, int *err,
                                                         uint32_t max_polls) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // 1024-byte aligned operand region
@@ -145,12 +165,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
     for (int jb = blockIdx.x; jb < njobs && !failed; jb += gridDim.x) {
         const ZJob job = jobs[jb];
         const int mr = ops.rows(job), nc = ops.cols(job);
-        for (int k0 = 0; k0 < K && !failed; k0 += kTK) {
-            const int kc = min(kTK, K - k0);
+        int kb, ke;
+        ops.krange(job, K, kb, ke);
+        for (int k0 = kb; k0 < ke && !failed; k0 += kTK) {
+            const int kc = min(kTK, ke - k0);
             // ---- A tile: item it -> (kstep s, row group g, core matrix kh, row rr);
             // its 16 bytes sit at byte offset 16 * it of the canonical layout
             // two items per pass: both items' loads are issued before either is split
-            for (int it0 = tid; it0 < kTM * 16; it0 += 2 * kThreads) {
+            for (int it0 = tid; it0 < kTM * 2 * kKS; it0 += 2 * kThreads) {
                 c32 x[2][8];
                 bool imag[2];
 #pragma unroll
@@ -160,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                     const int r = g * 8 + rr, kr = s * 16 + kh * 8;  // real k of the first element
                     imag[u] = kr >= kTK;
                     const int kk = imag[u] ? kr - kTK : kr;
-                    if (it < kTM * 16 && r < mr) {
+                    if (it < kTM * 2 * kKS && r < mr) {
                         ops.a8(job, job.m0 + r, k0 + kk, k0 + kc, x[u]);
                     } else {
 #pragma unroll
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int it = it0 + u * kThreads;
-                    if (it >= kTM * 16) continue;
+                    if (it >= kTM * 2 * kKS) continue;
                     float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) v[e] = imag[u] ? x[u][e].y : x[u][e].x;
@@ -180,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                 }
             }
             // ---- B tile: 2 kTN real rows (re / im row of every complex column)
-            for (int it0 = tid; it0 < 2 * kTN * 16; it0 += 2 * kThreads) {
+            for (int it0 = tid; it0 < 2 * kTN * 2 * kKS; it0 += 2 * kThreads) {
                 c32 x[2][8];
                 bool second[2];
                 int im_row[2];
@@ -193,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                     im_row[u] = nr & 1;
                     second[u] = kr >= kTK;
                     const int kk = second[u] ? kr - kTK : kr;
-                    if (it < 2 * kTN * 16 && n < nc) {
+                    if (it < 2 * kTN * 2 * kKS && n < nc) {
                         ops.b8(job, k0 + kk, k0 + kc, job.n0 + n, x[u]);
                     } else {
 #pragma unroll
@@ -203,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int it = it0 + u * kThreads;
-                    if (it >= 2 * kTN * 16) continue;
+                    if (it >= 2 * kTN * 2 * kKS) continue;
                     float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e)
@@ -219,10 +241,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_zgemm(Ops ops, const ZJob *jobs
                 tc_fence_after();
                 const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
 #pragma unroll 1
-                for (int s = 0; s < 8; ++s) {
+                for (int s = 0; s < kKS; ++s) {
                     const uint64_t dah = smem_desc(ah + s * 4096, 128, 256), dal = smem_desc(al + s * 4096, 128, 256);
                     const uint64_t dbh = smem_desc(bh + s * 8192, 128, 256), dbl = smem_desc(bl + s * 8192, 128, 256);
-                    tc_mma_bf16(tmem, dah, dbh, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+                    tc_mma_bf16(tmem, dah, dbh, idesc, (k0 > kb || s > 0) ? 1u : 0u);
                     tc_mma_bf16(tmem, dah, dbl, idesc, 1u);
                     tc_mma_bf16(tmem, dal, dbh, idesc, 1u);
                 }
@@ -284,10 +306,11 @@ int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 
     return launch_zgemm(st, ops, jobs, njobs, K, err, max_polls, num_sms);
 }
 
-int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap, const c32 *fib,
-                          const c32 *W, const int *perm_c, c32 *Z, int Nu, int nrhs, int64_t ncols, int NQ,
-                          const ZJob *jobs, int njobs, int *err, uint32_t max_polls, int num_sms) {
-    ApplyOps ops{groups, rowtab, qmap, fib, W, perm_c, Z, Nu, nrhs, ncols};
+int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap,
+                          const int *lperm, int nq0, const c32 *fib, const c32 *W, const int *perm_c, c32 *Z, int Nu,
+                          int nrhs, int64_t ncols, int NQ, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
+                          int num_sms) {
+    ApplyOps ops{groups, rowtab, qmap, lperm, nq0, fib, W, perm_c, Z, Nu, nrhs, ncols};
     return launch_zgemm(st, ops, jobs, njobs, NQ, err, max_polls, num_sms);
 }
 

@@ -112,20 +112,24 @@ int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorO
 // max_polls: poll limit of each tensor-core wait (0: the default); a wait that
 // gives up sets TD_DEV_TIMEOUT in *err, lets its MMAs finish and returns
 struct ZJob {               // one output tile
-    int g, m0, n0, pad;     // group, first row, first complex column
+    int g, m0, n0;          // group, first row, first complex column
+    int half;               // K range: 0 every frequency, 1 the first nq0 (half 0), 2 the rest
 };
 struct ZGroup {             // rows (block, term, half) that share a column cluster
     int J0, nJ;             // column cluster (permuted column range)
     int row0, M;            // first entry in the row table, number of rows
     int64_t zoff;           // offset of the group's first Z row (complex units)
-    int L, pad;             // Z row length = nJ * nrhs
+    int L, Mh;              // Z row length = nJ * nrhs; rows of half 0 (the half-1 rows follow)
 };
 int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 *B, int64_t ldb, c32 *D, int64_t ldd,
                           int M, int N, int K, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
                           int num_sms);
-int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap, const c32 *fib,
-                          const c32 *W, const int *perm_c, c32 *Z, int Nu, int nrhs, int64_t ncols, int NQ,
-                          const ZJob *jobs, int njobs, int *err, uint32_t max_polls, int num_sms);
+// lperm: frequency order of the contraction (the nq0 frequencies of half 0
+// first, then those of the conjugate half)
+int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap,
+                          const int *lperm, int nq0, const c32 *fib, const c32 *W, const int *perm_c, c32 *Z, int Nu,
+                          int nrhs, int64_t ncols, int NQ, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
+                          int num_sms);
 int td_zgemm_tile_rows();
 int td_zgemm_tile_cols();
 
@@ -135,7 +139,9 @@ struct ApplyZArgs {
     const int *blocks;
     const int *perm_r;
     int Nu, nrhs, rpt;      // rpt: Z rows per term (2 with a conjugate half, else 1)
-    const int64_t *zbase;   // [nb] Z offset of the block's first row (-1: rank 0)
+    const int64_t *zbase;   // [nb] Z offset of the block's row (term 0, half 0) (-1: rank 0);
+                            // row (d, p) at zbase + p zpstride + d nJ nrhs
+    const int64_t *zpstride;  // [nb] offset between a block's half-0 and half-1 rows
     const c32 *Z;
     c32 *y;
     // far terms: T = V_d^T z1 and V_d^H z2, at toff[b Nu + d] + (p k_d + tau) nrhs + c
