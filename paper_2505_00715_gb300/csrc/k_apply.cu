@@ -162,28 +162,30 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs a, TensorOut o, int TJ,
 //            y_I += sum_d H_d z_(d,1) + conj(H_d) z_(d,2) (near; k = (d, j),
 //            A = H_d row-major); both halves summed before one atomic add
 //            per output.
-// Tiles: 64 rows x (rpt nrhs) columns, k in chunks of 32; every thread holds
-// a 4 x CPT register tile (rows 4 ty .. 4 ty + 3, columns tx + 16 q).
+// Tiles: 64 rows x (rpt nrhs) columns, k in chunks of 32; 16 x CG threads,
+// every thread holds a 4 x CPT register tile (rows 4 ty .. 4 ty + 3,
+// columns tx + CG q, tx < CG).
 constexpr int kFM = 64, kFK = 32, kFPad = 65;
 
 struct FaceSmem {
     c32 A[kFK][kFPad];  // A[k][m] (m contiguous)
 };
 
-template <int CPT>
-__global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, int stage) {
+template <int CG, int CPT>
+__global__ void __launch_bounds__(16 * CG) k_apply_faces(ApplyZArgs a, TensorOut o, int stage) {
+    constexpr int NT = 16 * CG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FaceSmem &F = *reinterpret_cast<FaceSmem *>(smem_raw);
     c32 *Bs = reinterpret_cast<c32 *>(smem_raw + sizeof(FaceSmem));  // [kFK][ncol]
     const int nrhs = a.nrhs, Nu = a.Nu, rpt = a.rpt, ncol = rpt * nrhs;
     const c32 *pool = (const c32 *)o.face;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % CG, ty = tid / CG;
     // columns of this thread and their half; both halves of one right-hand side
-    // sit in the same thread (q and q + CPT / 2) when 2 nrhs = 16 CPT
+    // sit in the same thread (q and q + CPT / 2) when 2 nrhs = CG CPT
     bool conj_q[CPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) conj_q[q] = tx + 16 * q >= nrhs;
-    const bool pair_halves = CPT >= 2 && rpt == 2 && 2 * nrhs == 16 * CPT;
+    for (int q = 0; q < CPT; ++q) conj_q[q] = tx + CG * q >= nrhs;
+    const bool pair_halves = CPT >= 2 && rpt == 2 && 2 * nrhs == CG * CPT;
     const int64_t njobs = stage == 0 ? a.nft : a.nb;
     for (int64_t job = blockIdx.x; job < njobs; job += gridDim.x) {
         int b, d0, d1, M;
@@ -245,17 +247,17 @@ __global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, 
                     const int kc = min(kFK, K - k0), mc = min(kFM, M - m0);
                     __syncthreads();
                     if (acol) {
-                        for (int e = tid; e < kFK * kFM; e += 256) {
+                        for (int e = tid; e < kFK * kFM; e += NT) {
                             const int kk = e / kFM, mm = e - kk * kFM;
                             F.A[kk][mm] = (kk < kc && mm < mc) ? Ab[(int64_t)(k0 + kk) * lda + m0 + mm] : c32{0.f, 0.f};
                         }
                     } else {
-                        for (int e = tid; e < kFK * kFM; e += 256) {
+                        for (int e = tid; e < kFK * kFM; e += NT) {
                             const int mm = e / kFK, kk = e - mm * kFK;
                             F.A[kk][mm] = (kk < kc && mm < mc) ? Ab[(int64_t)(m0 + mm) * lda + k0 + kk] : c32{0.f, 0.f};
                         }
                     }
-                    for (int e = tid; e < kFK * ncol; e += 256) {
+                    for (int e = tid; e < kFK * ncol; e += NT) {
                         const int kk = e / ncol, n = e - kk * ncol, p = n / nrhs, c = n - p * nrhs;
                         Bs[e] = kk < kc ? B0[p * bstride + (int64_t)(k0 + kk) * nrhs + c] : c32{0.f, 0.f};
                     }
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, 
                         for (int x = 0; x < 4; ++x) av[x] = F.A[kk][4 * ty + x];
 #pragma unroll
                         for (int q = 0; q < CPT; ++q) {
-                            const int n = tx + 16 * q;
+                            const int n = tx + CG * q;
                             bv[q] = n < ncol ? Bs[kk * ncol + n] : c32{0.f, 0.f};
                         }
 #pragma unroll
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, 
                     c32 *Tout = a.T + a.toff[tb + d0];
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
-                        const int n = tx + 16 * q;
+                        const int n = tx + CG * q;
                         if (n >= ncol) continue;
                         const int p = n / nrhs, c = n - p * nrhs;
                         Tout[((int64_t)p * kd + m) * nrhs + c] = acc[x][q];
@@ -302,13 +304,13 @@ __global__ void __launch_bounds__(256) k_apply_faces(ApplyZArgs a, TensorOut o, 
                     if (pair_halves) {
 #pragma unroll
                         for (int q = 0; q < CPT / 2; ++q) {
-                            const int c = tx + 16 * q;
+                            const int c = tx + CG * q;
                             if (c < nrhs) atomic_add_c(yr + c, acc[x][q] + acc[x][q + CPT / 2]);
                         }
                     } else {
 #pragma unroll
                         for (int q = 0; q < CPT; ++q) {
-                            const int n = tx + 16 * q;
+                            const int n = tx + CG * q;
                             if (n < ncol) atomic_add_c(yr + n % nrhs, acc[x][q]);
                         }
                     }
@@ -394,26 +396,28 @@ int td_launch_apply(cudaStream_t st, int prec, const ApplyArgs &a, const TensorO
     return (int)cudaGetLastError();
 }
 
-template <int CPT>
+template <int CG, int CPT>
 static int launch_faces(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int stage, int grid) {
     const size_t sm = sizeof(FaceSmem) + sizeof(c32) * kFK * a.rpt * a.nrhs;
-    cudaError_t e = cudaFuncSetAttribute(k_apply_faces<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_apply_faces<CG, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    k_apply_faces<CPT><<<grid, 256, sm, st>>>(a, o, stage);
+    k_apply_faces<CG, CPT><<<grid, 16 * CG, sm, st>>>(a, o, stage);
     return (int)cudaGetLastError();
 }
 
 int td_launch_apply_z(cudaStream_t st, const ApplyZArgs &a, const TensorOut &o, int num_sms) {
     const int ncol = a.rpt * a.nrhs;
     auto run = [&](int stage, int grid) {
-        if (ncol <= 16) return launch_faces<1>(st, a, o, stage, grid);
-        if (ncol <= 32) return launch_faces<2>(st, a, o, stage, grid);
-        if (ncol <= 64) return launch_faces<4>(st, a, o, stage, grid);
-        return launch_faces<8>(st, a, o, stage, grid);
+        // 8 x 4 or 16 x 4 threads' register tiles of 4 x 4 complex outputs
+        // (ncol <= 64); 16 column groups of 8 columns beyond
+        if (ncol <= 16) return launch_faces<8, 2>(st, a, o, stage, grid);
+        if (ncol <= 32) return launch_faces<8, 4>(st, a, o, stage, grid);
+        if (ncol <= 64) return launch_faces<16, 4>(st, a, o, stage, grid);
+        return launch_faces<16, 8>(st, a, o, stage, grid);
     };
     int e = 0;
-    if (a.nft > 0) e = run(0, (int)std::min<int64_t>(a.nft, (int64_t)num_sms * 16));
-    if (!e && a.nb > 0) e = run(1, std::min(a.nb, num_sms * 16));
+    if (a.nft > 0) e = run(0, (int)std::min<int64_t>(a.nft, (int64_t)num_sms * 32));
+    if (!e && a.nb > 0) e = run(1, std::min(a.nb, num_sms * 32));
     return e;
 }
 

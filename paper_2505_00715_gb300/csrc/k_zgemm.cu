@@ -169,21 +169,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_zgemm(Ops ops, const ZJob *jobs
         ops.krange(job, K, kb, ke);
         for (int k0 = kb; k0 < ke && !failed; k0 += kTK) {
             const int kc = min(kTK, ke - k0);
-            // ---- A tile: item it -> (kstep s, row group g, core matrix kh, row rr);
-            // its 16 bytes sit at byte offset 16 * it of the canonical layout
-            // two items per pass: both items' loads are issued before either is split
-            for (int it0 = tid; it0 < kTM * 2 * kKS; it0 += 2 * kThreads) {
+            // ---- A tile.  Real item it -> (kstep s, row group g, core matrix kh, row
+            // rr), its 16 bytes at byte offset 16 * it of the canonical layout.  One
+            // complex item (8 consecutive complex k of one row) gives the real item of
+            // its real parts (real k < kTK) and the one of its imaginary parts (real
+            // k + kTK, kTK / 16 ksteps = kTK * 16 items further): each value is loaded
+            // once.  Two complex items per thread and pass, loads issued first.
+            constexpr int kAItems = kTM * kTK / 8, kAImag = kTK * 16;
+            for (int c0 = tid; c0 < kAItems; c0 += 2 * kThreads) {
                 c32 x[2][8];
-                bool imag[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int it = it0 + u * kThreads;
-                    const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 15, s = it >> 8;
-                    const int r = g * 8 + rr, kr = s * 16 + kh * 8;  // real k of the first element
-                    imag[u] = kr >= kTK;
-                    const int kk = imag[u] ? kr - kTK : kr;
-                    if (it < kTM * 2 * kKS && r < mr) {
-                        ops.a8(job, job.m0 + r, k0 + kk, k0 + kc, x[u]);
+                    const int ci = c0 + u * kThreads;
+                    const int rr = ci & 7, kh = (ci >> 3) & 1, g = (ci >> 4) & 15, sk = ci >> 8;
+                    const int r = g * 8 + rr, k = sk * 16 + kh * 8;  // complex k of the first element
+                    if (ci < kAItems && r < mr) {
+                        ops.a8(job, job.m0 + r, k0 + k, k0 + kc, x[u]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) x[u][e] = c32{0.f, 0.f};
@@ -191,32 +192,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_zgemm(Ops ops, const ZJob *jobs
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int it = it0 + u * kThreads;
-                    if (it >= kTM * 2 * kKS) continue;
+                    const int ci = c0 + u * kThreads;
+                    if (ci >= kAItems) continue;
                     float v[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = imag[u] ? x[u][e].y : x[u][e].x;
-                    const SplitPack p = split8(v);
-                    *reinterpret_cast<uint4 *>(Ah + 16 * it) = p.hi;
-                    *reinterpret_cast<uint4 *>(Al + 16 * it) = p.lo;
+                    for (int e = 0; e < 8; ++e) v[e] = x[u][e].x;
+                    SplitPack p = split8(v);
+                    *reinterpret_cast<uint4 *>(Ah + 16 * ci) = p.hi;
+                    *reinterpret_cast<uint4 *>(Al + 16 * ci) = p.lo;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = x[u][e].y;
+                    p = split8(v);
+                    *reinterpret_cast<uint4 *>(Ah + 16 * (ci + kAImag)) = p.hi;
+                    *reinterpret_cast<uint4 *>(Al + 16 * (ci + kAImag)) = p.lo;
                 }
             }
-            // ---- B tile: 2 kTN real rows (re / im row of every complex column)
-            for (int it0 = tid; it0 < 2 * kTN * 2 * kKS; it0 += 2 * kThreads) {
+            // ---- B tile: 2 kTN real rows (re / im row of every complex column).
+            // Real item it -> (kstep s = it >> 9, row group g, kh, row rr).  One
+            // complex item (8 consecutive k of complex column n) gives four real
+            // items: rows 2n / 2n + 1 (rr = 2 (n & 3), + 1) in the first K half
+            // (Re B, Im B) and in the second (-Im B, Re B, kTK / 16 ksteps further).
+            constexpr int kBItems = kTN * kTK / 8, kBSecond = kTK * 32;
+            for (int c0 = tid; c0 < kBItems; c0 += 2 * kThreads) {
                 c32 x[2][8];
-                bool second[2];
-                int im_row[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int it = it0 + u * kThreads;
-                    const int rr = it & 7, kh = (it >> 3) & 1, g = (it >> 4) & 31, s = it >> 9;
-                    const int nr = g * 8 + rr, kr = s * 16 + kh * 8;
-                    const int n = nr >> 1;
-                    im_row[u] = nr & 1;
-                    second[u] = kr >= kTK;
-                    const int kk = second[u] ? kr - kTK : kr;
-                    if (it < 2 * kTN * 2 * kKS && n < nc) {
-                        ops.b8(job, k0 + kk, k0 + kc, job.n0 + n, x[u]);
+                    const int ci = c0 + u * kThreads;
+                    const int n4 = ci & 3, kh = (ci >> 2) & 1, g = (ci >> 3) & 31, sk = ci >> 8;
+                    const int n = g * 4 + n4, k = sk * 16 + kh * 8;
+                    if (ci < kBItems && n < nc) {
+                        ops.b8(job, k0 + k, k0 + kc, job.n0 + n, x[u]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) x[u][e] = c32{0.f, 0.f};
@@ -224,15 +229,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_zgemm(Ops ops, const ZJob *jobs
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int it = it0 + u * kThreads;
-                    if (it >= 2 * kTN * 2 * kKS) continue;
+                    const int ci = c0 + u * kThreads;
+                    if (ci >= kBItems) continue;
+                    const int n4 = ci & 3, kh = (ci >> 2) & 1, g = (ci >> 3) & 31, sk = ci >> 8;
+                    const int it = sk * 512 + g * 16 + kh * 8 + 2 * n4;
                     float v[8];
+                    SplitPack p;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        v[e] = im_row[u] ? (second[u] ? x[u][e].x : x[u][e].y) : (second[u] ? -x[u][e].y : x[u][e].x);
-                    const SplitPack p = split8(v);
+                    for (int e = 0; e < 8; ++e) v[e] = x[u][e].x;  // row 2n, first half; row 2n + 1, second
+                    p = split8(v);
                     *reinterpret_cast<uint4 *>(Bh + 16 * it) = p.hi;
                     *reinterpret_cast<uint4 *>(Bl + 16 * it) = p.lo;
+                    *reinterpret_cast<uint4 *>(Bh + 16 * (it + kBSecond + 1)) = p.hi;
+                    *reinterpret_cast<uint4 *>(Bl + 16 * (it + kBSecond + 1)) = p.lo;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = x[u][e].y;  // row 2n + 1, first half
+                    p = split8(v);
+                    *reinterpret_cast<uint4 *>(Bh + 16 * (it + 1)) = p.hi;
+                    *reinterpret_cast<uint4 *>(Bl + 16 * (it + 1)) = p.lo;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = -x[u][e].y;  // row 2n, second half
+                    p = split8(v);
+                    *reinterpret_cast<uint4 *>(Bh + 16 * (it + kBSecond)) = p.hi;
+                    *reinterpret_cast<uint4 *>(Bl + 16 * (it + kBSecond)) = p.lo;
                 }
             }
             fence_async_shared();
@@ -292,7 +311,7 @@ int launch_zgemm(cudaStream_t st, const Ops &ops, const ZJob *jobs, int njobs, i
     if (njobs == 0) return 0;
     cudaError_t e = cudaFuncSetAttribute(k_zgemm<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return (int)e;
-    const int grid = std::min(njobs, num_sms);
+    const int grid = std::min(njobs, 2 * num_sms);  // two CTAs per SM
     k_zgemm<Ops><<<grid, kThreads, kSmemBytes, st>>>(ops, jobs, njobs, K, err, max_polls ? max_polls : kMaxPolls);
     return (int)cudaGetLastError();
 }
