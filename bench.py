@@ -619,11 +619,13 @@ def apply_flops(X, blocks, NQ, nrhs):
     return flops_a + face_entries * 8.0 * nrhs * 2.0
 
 
-# DRAM bytes (read + write) of one far-kernel launch on the 5120-triangle
-# sphere, from a one-pass ncu capture of the kernel built from the sources
-# whose digest is recorded; reported only while those sources are unchanged.
-FAR_TRAFFIC = {"workload": "sphere5120_slp_bdf2_N64", "bytes": 24.04e9 + 5.99e9,
-               "sources": ("k_aca.cu", "pair.cuh", "kernels.h", "internal.h"), "sha256_16": "4a5963f7a8507971"}
+# DRAM bytes (read + write) of one far-kernel launch on the benchmark workload
+# (the 30k-triangle housing, default launch shape), from a one-pass ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, -k k_far_aca -c 1) of
+# the kernel built from the sources whose digest is recorded; reported only
+# while those sources are unchanged.
+FAR_TRAFFIC = {"workload": "housing30k_slp_gcq256", "bytes": 1.18e12 + 92.42e9,
+               "sources": ("k_aca.cu", "pair.cuh", "common.cuh"), "sha256_16": "9dd7fc527238db7a"}
 
 
 def far_traffic(workload):

@@ -20,7 +20,7 @@ def test_workloads_are_complete():
 
 
 def test_far_traffic_only_for_the_measured_workload():
-    assert bench.far_traffic("housing30k_slp_gcq256") is None
+    assert bench.far_traffic("sphere5120_slp_bdf2_N64") is None
     t = bench.far_traffic(bench.FAR_TRAFFIC["workload"])
     assert t is None or t == bench.FAR_TRAFFIC["bytes"]
 
