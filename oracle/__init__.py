@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-SLP, DLP = 0, 1
+SLP, DLP, ADLP = 0, 1, 2
 P0, P1 = 0, 1
 EULER, RADAU2 = 0, 1
 
@@ -340,5 +340,5 @@ def conj_partner_apply(apply_fn, W_unique, W_partner):
 
 __all__ = ["Mesh", "Tree", "Tensor", "rule7", "gauss01", "freqs_bdf2", "freqs_gcq", "ellipk", "ellipj",
            "ellipj_complex", "aca_dense", "aca3d_dense", "mlp_nparams", "mlp_forward", "mlp_loss_grad",
-           "adam_step", "SLP", "DLP", "P0", "P1", "EULER", "RADAU2", "lib"]
+           "adam_step", "SLP", "DLP", "ADLP", "P0", "P1", "EULER", "RADAU2", "lib"]
 os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")

@@ -15,8 +15,10 @@
  *   - triangles are vertex-index triples, counter-clockwise seen from outside,
  *     so (v1-v0)x(v2-v0) points out of the domain (Sec. 2, outward normal n);
  *   - operators: ORC_SLP = single layer V, Galerkin P0 test x P0 trial;
- *                ORC_DLP = double layer K, Galerkin P0 test x P1 trial
- *     (Sec. 2 eqs. slp/dlp, Sec. 3 spaces X_D = P1, X_N = P0);
+ *                ORC_DLP = double layer K, Galerkin P0 test x P1 trial;
+ *                ORC_ADLP = adjoint double layer K', Galerkin P0 test x P0
+ *                trial (the conormal derivative at x of the single layer)
+ *     (Sec. 2 eqs. slp/dlp/adlp, Sec. 3 spaces X_D = P1, X_N = P0);
  *   - Laplace-domain kernel exp(-s r / c) / (4 pi r) (fundamental solution of
  *     Sec. 2 transformed to the Laplace domain, Sec. 3 "Temporal
  *     discretisation").
@@ -33,7 +35,7 @@
 extern "C" {
 #endif
 
-enum { ORC_SLP = 0, ORC_DLP = 1 };
+enum { ORC_SLP = 0, ORC_DLP = 1, ORC_ADLP = 2 };
 enum { ORC_P0 = 0, ORC_P1 = 1 };
 
 typedef struct orc_mesh orc_mesh;
@@ -54,7 +56,9 @@ int orc_gauss01(int n, double *x, double *w);
 /* Pair integral over test triangle ti and trial triangle tj at frequency s:
  *   SLP: out[0]      = int_ti int_tj  exp(-s r/c)/(4 pi r)
  *   DLP: out[m], m<3 = int_ti int_tj  phi_m(y) d/dn_y [exp(-s r/c)/(4 pi r)]
- *        where phi_m is the P1 hat of tj's m-th vertex restricted to tj.
+ *        where phi_m is the P1 hat of tj's m-th vertex restricted to tj;
+ *   ADLP: out[0]     = int_ti int_tj  d/dn_x [exp(-s r/c)/(4 pi r)]
+ *        (n_x the normal of ti).
  * Touching pairs (identical / common edge / common vertex) use the
  * regularising coordinate transforms of Sauter and Schwab with an ng-point
  * Gauss-Legendre rule in every transformed variable; other pairs the 7x7 rule.

@@ -183,6 +183,12 @@ static cplx k_dlp(const double *d, const double *ny, cplx sc) {
     double r = sqrt(dot3(d, d));
     return cexp(-sc * r) * (1.0 + sc * r) * (-dot3(d, ny)) / (FOUR_PI * r * r * r);
 }
+/* Adjoint double-layer kernel d/dn_x exp(-s r/c)/(4 pi r) =
+ * exp(-s r/c)(1 + s r/c)(y-x).n_x/(4 pi r^3); d = y - x, sc = s/c. */
+static cplx k_adlp(const double *d, const double *nx, cplx sc) {
+    double r = sqrt(dot3(d, d));
+    return cexp(-sc * r) * (1.0 + sc * r) * dot3(d, nx) / (FOUR_PI * r * r * r);
+}
 /* Modulus bounds of the kernels (for the magnitude sums, see orc_entries_mag):
  * |exp(-s r/c)| / (4 pi r), and |exp(-s r/c)(1 + s r/c)| r / (4 pi r^3), the
  * double layer with |(x-y).n_y| replaced by its bound |x - y|. */
@@ -263,12 +269,16 @@ static void chi(const param_tri *p, double x1, double x2, double *o) {
 }
 
 /* Accumulate weight * kernel * basis into out[3] (mesh-local trial vertex).
- * For SLP only out[0] is used. */
-static void accum(int op, int mag, const double *d, const double *ny, cplx sc, double wgt,
+ * For SLP and ADLP only out[0] is used; nn is the trial normal (DLP) or the
+ * test normal (ADLP). */
+static void accum(int op, int mag, const double *d, const double *nn, cplx sc, double wgt,
                   const param_tri *pb, double y1, double y2, cplx *out) {
     if (op == ORC_SLP) {
         out[0] += mag ? wgt * k_slp_mag(d, sc) : wgt * k_slp(d, sc);
+    } else if (op == ORC_ADLP) {
+        out[0] += mag ? wgt * k_dlp_mag(d, sc) : wgt * k_adlp(d, nn, sc);
     } else {
+        const double *ny = nn;
         cplx k = mag ? wgt * k_dlp_mag(d, sc) : wgt * k_dlp(d, ny, sc);
         double lam[3] = {1.0 - y1, y1 - y2, y2};
         for (int q = 0; q < 3; ++q) out[pb->loc[q]] += k * lam[q];
@@ -329,7 +339,7 @@ static void pair_edge(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj
                       const param_tri *pb, cplx sc, int ng, const double *gx, const double *gw,
                       cplx *out) {
     double g = 4.0 * m->area[ti] * m->area[tj];
-    const double *ny = m->nrm + 3 * tj;
+    const double *ny = m->nrm + 3 * (op == ORC_ADLP ? ti : tj);
     double eu[3], ep[3], eq[3];
     sub3(pa->P[1], pa->P[0], eu);
     sub3(pa->P[2], pa->P[1], ep);
@@ -367,7 +377,7 @@ static void pair_vertex(const orc_mesh *m, int op, int mag, int64_t ti, int64_t 
                         const param_tri *pb, cplx sc, int ng, const double *gx, const double *gw,
                         cplx *out) {
     double g = 4.0 * m->area[ti] * m->area[tj];
-    const double *ny = m->nrm + 3 * tj;
+    const double *ny = m->nrm + 3 * (op == ORC_ADLP ? ti : tj);
     cplx acc[3] = {0, 0, 0};
     for (int reg = 0; reg < 2; ++reg)
         for (int a = 0; a < ng; ++a)
@@ -401,7 +411,7 @@ static void pair_vertex(const orc_mesh *m, int op, int mag, int64_t ti, int64_t 
 static void pair_regular(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj, cplx sc, cplx *out) {
     double bary[7][3], w[7];
     orc_rule7(&bary[0][0], w);
-    const double *ny = m->nrm + 3 * tj;
+    const double *ny = m->nrm + 3 * tj, *nx = m->nrm + 3 * ti;
     const int32_t *A = m->t + 3 * ti, *B = m->t + 3 * tj;
     double scale = m->area[ti] * m->area[tj];
     for (int a = 0; a < 7; ++a) {
@@ -416,6 +426,8 @@ static void pair_regular(const orc_mesh *m, int op, int mag, int64_t ti, int64_t
             double wgt = w[a] * w[b] * scale;
             if (op == ORC_SLP) {
                 out[0] += mag ? wgt * k_slp_mag(d, sc) : wgt * k_slp(d, sc);
+            } else if (op == ORC_ADLP) {
+                out[0] += mag ? wgt * k_dlp_mag(d, sc) : wgt * k_adlp(d, nx, sc);
             } else {
                 cplx k = mag ? wgt * k_dlp_mag(d, sc) : wgt * k_dlp(d, ny, sc);
                 for (int q = 0; q < 3; ++q) out[q] += k * bary[b][q];
@@ -449,7 +461,7 @@ static int pair_any(const orc_mesh *m, int op, int mag, int64_t ti, int64_t tj, 
     if (cls > 0 && orc_gauss01(ng, gx, gw) != 0) return -1;
     switch (cls) {
     case 3:
-        /* flat panel: (x - y).n_y = 0, the double layer vanishes identically */
+        /* flat panel: (x - y).n = 0, the double layer and its adjoint vanish identically */
         if (op == ORC_SLP) pair_identical(m, op, mag, ti, &pa, sc, ng, gx, gw, out);
         break;
     case 2: pair_edge(m, op, mag, ti, tj, &pa, &pb, sc, ng, gx, gw, out); break;
@@ -473,7 +485,7 @@ int orc_pair(const orc_mesh *m, int op, int64_t ti, int64_t tj, double s_re, dou
 void orc_entry(const orc_mesh *m, int op, int64_t row, int64_t col, double s_re, double s_im,
                double c, int ng, double *o) {
     double acc_re = 0.0, acc_im = 0.0, pr[6];
-    if (op == ORC_SLP) {
+    if (op == ORC_SLP || op == ORC_ADLP) {
         orc_pair(m, op, row, col, s_re, s_im, c, ng, pr);
         acc_re = pr[0];
         acc_im = pr[1];
@@ -506,7 +518,7 @@ void orc_entries(const orc_mesh *m, int op, const int32_t *rows, int64_t nr, con
  * layer and |exp(-s r/c)(1 + s r/c)| / (4 pi r^2) for the double layer (the
  * factor |(x - y).n_y| bounded by |x - y|). */
 static double entry_mag(const orc_mesh *m, int op, int64_t row, int64_t col, cplx sc, int ng) {
-    if (op == ORC_SLP) {
+    if (op == ORC_SLP || op == ORC_ADLP) {
         cplx out[3] = {0, 0, 0};
         pair_any(m, op, 1, row, col, sc, ng, out);
         return creal(out[0]);

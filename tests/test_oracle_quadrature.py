@@ -113,11 +113,16 @@ def test_slp_symmetric(orc, sphere1):
     assert np.max(np.abs(a - a.T)) <= 1e-15 * np.max(np.abs(a))
 
 
-@pytest.mark.parametrize("op", ["slp", "dlp"])
+@pytest.mark.parametrize("op", ["slp", "dlp", "adlp"])
 def test_sphere_closed_form_order2(orc, op):
     """Row sums of the Galerkin matrices on icospheres converge at O(h^2) to
     (1 - e^{-2sR/c})/(2s/c)      (SLP applied to 1, per unit test area) and
-    e^{-2sR/c}/2 - (1-e^{-2sR/c})/(2sR/c)  (DLP applied to 1)."""
+    e^{-2sR/c}/2 - (1-e^{-2sR/c})/(2sR/c)  (DLP and its adjoint applied to 1:
+    on a sphere (x - y).n_y = (y - x).n_x, so both kernels coincide there).
+    The adjoint converges at O(h) only: its row sum weighs the facet normal
+    n_x, which deviates by O(h) from the sphere's, while the double layer's
+    row sum is a solid angle of the polyhedron (Gauss' law at s = 0) and
+    keeps O(h^2)."""
     s, R = 2.0 + 1.0j, 1.0
     errs = []
     for lev in (2, 3, 4):
@@ -130,10 +135,15 @@ def test_sphere_closed_form_order2(orc, op):
             A = m.entries(orc.SLP, rows, np.arange(n), [s], ng=6)[0]
             cf = (1 - np.exp(-2 * s * R)) / (2 * s)
         else:
-            A = m.entries(orc.DLP, rows, np.arange(len(V)), [s], ng=6)[0]
+            op_, ncol = (orc.DLP, len(V)) if op == "dlp" else (orc.ADLP, n)
+            A = m.entries(op_, rows, np.arange(ncol), [s], ng=6)[0]
             cf = np.exp(-2 * s * R) / 2 - (1 - np.exp(-2 * s * R)) / (2 * s * R)
         errs.append(np.max(np.abs(A.sum(1) / area[rows] - cf)) / abs(cf))
     order = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    if op == "adlp":
+        assert order[0] > 0.95 and order[1] > 0.95, (errs, order)
+        assert errs[0] < 0.04, errs
+        return
     assert order[0] > 1.7 and order[1] > 1.85, (errs, order)
     assert errs[0] < (0.005 if op == "slp" else 0.02)
 
@@ -228,3 +238,31 @@ def test_dlp_magnitude_of_stacked_small_triangles(orc):
     far = area * area * abs(np.exp(-s * R) * (1 + s * R)) / (4 * np.pi * R * R)
     assert abs(abs(ent) - mag) <= 1e-3 * mag
     assert abs(mag - far) <= 1e-3 * far
+
+
+def test_adjoint_double_layer_is_the_transposed_p0_double_layer(orc):
+    """K' (eq. adlp, conormal derivative at x) with P0 x P0 is the transpose of
+    the P0 x P0 double layer: swapping test and trial triangles turns
+    (x - y).n_y into (y - x).n_x.  The oracle forms the two by different code
+    paths (test normal vs trial normal, the P1 hat weights of the double layer
+    summed to the P0 trial function, touching pairs parametrised from the other
+    triangle), so a dropped sign, the wrong normal or a transposed operand
+    fails here.  Checked on a jittered sphere (no symmetry) for regular,
+    vertex, edge and identical pairs at a complex frequency."""
+    V, T = icosphere(1)
+    rng = np.random.default_rng(3)
+    V = V * (1.0 + 0.08 * rng.standard_normal((len(V), 1)))
+    m = orc.Mesh(V, T)
+    s = 1.3 + 2.1j
+    seen = set()
+    for ti in range(len(T)):
+        for tj in range(len(T)):
+            cls, kp = m.pair(orc.ADLP, ti, tj, s, ng=12)
+            cls2, kt = m.pair(orc.DLP, tj, ti, s, ng=12)
+            assert cls == cls2
+            seen.add(cls)
+            ref = kt.sum()  # P1 hats of the trial triangle sum to its P0 function
+            assert abs(kp[0] - ref) <= 1e-8 * max(abs(ref), 1e-3), (ti, tj, cls, kp[0], ref)
+            if cls == 3:
+                assert kp[0] == 0.0
+    assert seen == {0, 1, 2, 3}
