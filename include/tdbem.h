@@ -45,7 +45,7 @@ extern "C" {
 #define TDBEM_ERR_CAPACITY (-5)       /* a device pool overflowed (retried internally) */
 
 /* ---- enumerations ------------------------------------------------------- */
-enum { TDBEM_SLP = 0, TDBEM_DLP = 1 };        /* single layer V, double layer K (Sec. 2) */
+enum { TDBEM_SLP = 0, TDBEM_DLP = 1, TDBEM_ADLP = 2 }; /* single layer V, double layer K, adjoint K' (Sec. 2) */
 enum { TDBEM_P0 = 0, TDBEM_P1 = 1 };          /* piecewise constant / linear (Sec. 3) */
 enum { TDBEM_FP64 = 0, TDBEM_MIXED = 1 };     /* precision forms, see tdbem_op */
 enum { TDBEM_EULER = 0, TDBEM_RADAU2 = 1 };   /* Runge-Kutta method of the gCQ (App. A) */
@@ -57,11 +57,15 @@ typedef struct tdbem_tree *tdbem_tree_t;
 typedef struct tdbem_tensor *tdbem_tensor_t;
 typedef struct tdbem_model *tdbem_model_t;
 
-/* Operator and discretisation (Sec. 2 eqs. slp/dlp, Sec. 3):
+/* Operator and discretisation (Sec. 2 eqs. slp/dlp/adlp, Sec. 3):
  *   op = TDBEM_SLP: A[i,j](s) = int_{tau_i} int_{tau_j} exp(-s r/c)/(4 pi r),
  *        test P0 x trial P0 (Galerkin single layer);
  *   op = TDBEM_DLP: A[i,v](s) = int_{tau_i} int_Gamma phi_v(y) d/dn_y
- *        [exp(-s r/c)/(4 pi r)], test P0 x trial P1 (Galerkin double layer).
+ *        [exp(-s r/c)/(4 pi r)], test P0 x trial P1 (Galerkin double layer);
+ *   op = TDBEM_ADLP: A[i,j](s) = int_{tau_i} d/dn_x int_{tau_j}
+ *        exp(-s r/c)/(4 pi r), test P0 x trial P0 (Galerkin adjoint double
+ *        layer K', the conormal derivative at x of the single layer; its
+ *        column tree is built on P0 like the single layer's).
  * Regular pairs use the 7-point degree-5 triangle rule in x and y (49
  * points); pairs of triangles that share a vertex, an edge or coincide use
  * the Sauter-Schwab regularising transforms with an ng-point Gauss-Legendre

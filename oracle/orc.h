@@ -83,7 +83,8 @@ void orc_entries(const orc_mesh *m, int op, const int32_t *rows, int64_t nr,
 /* Magnitude sums out[f][r][c] (real): the quadrature of orc_entries with
  * every term replaced by a bound of its modulus, |exp(-s r/c)|/(4 pi r) for
  * the single layer and |exp(-s r/c)(1 + s r/c)|/(4 pi r^2) for the double
- * layer (|(x - y).n_y| <= |x - y|).  A floating-point evaluation of an entry
+ * layer and its adjoint (|(x - y).n| <= |x - y|; a flat panel with itself
+ * contributes 0, as to the entry).  A floating-point evaluation of an entry
  * can only be accurate relative to this sum: rounding in each term is
  * relative to its bound, and the terms may cancel.  For the single layer at
  * real s every term is positive and the sum equals |entry|. */

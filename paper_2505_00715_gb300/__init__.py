@@ -15,11 +15,11 @@ import os
 import numpy as np
 
 from . import _lib
-from ._lib import DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
+from ._lib import ADLP, DLP, EULER, FP64, MIXED, P0, P1, RADAU2, SLP, TdbemError
 
 __all__ = ["Context", "Mesh", "Freqs", "Tree", "Tensor", "Model", "entries", "PATH_GENERIC", "PATH_NEAR",
            "PATH_FIBRE", "compress", "harvest", "rank_bin", "autotune",
-           "SLP", "DLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError", "March", "march_step_points",
+           "SLP", "DLP", "ADLP", "P0", "P1", "FP64", "MIXED", "EULER", "RADAU2", "TdbemError", "March", "march_step_points",
            "lowrank_recompress"]
 NPARAMS = 5648
 

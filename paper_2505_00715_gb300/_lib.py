@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libtdbem.so")
 
 OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_CAPACITY = -1, -2, -3, -4, -5
-SLP, DLP = 0, 1
+SLP, DLP, ADLP = 0, 1, 2
 P0, P1 = 0, 1
 FP64, MIXED = 0, 1
 EULER, RADAU2 = 0, 1

@@ -109,7 +109,8 @@ MeshDev td_mesh_dev(const tdbem_mesh *m, int ng, const double *gx, const double 
 
 int td_check_op(tdbem_ctx *ctx, const tdbem_op *op) {
     if (!op) return td_fail(ctx, TDBEM_ERR_ARG, "op is NULL");
-    if (op->op != TDBEM_SLP && op->op != TDBEM_DLP) return td_fail(ctx, TDBEM_ERR_ARG, "unknown operator %d", op->op);
+    if (op->op != TDBEM_SLP && op->op != TDBEM_DLP && op->op != TDBEM_ADLP)
+        return td_fail(ctx, TDBEM_ERR_ARG, "unknown operator %d", op->op);
     if (op->prec != TDBEM_FP64 && op->prec != TDBEM_MIXED) return td_fail(ctx, TDBEM_ERR_ARG, "unknown precision %d", op->prec);
     if (!(op->c > 0.0) || !std::isfinite(op->c)) return td_fail(ctx, TDBEM_ERR_ARG, "wave speed must be > 0");
     if (op->ng < 1 || op->ng > 16) return td_fail(ctx, TDBEM_ERR_ARG, "ng must be in 1..16");
@@ -132,7 +133,7 @@ int prepare_sing(tdbem_ctx *ctx, const tdbem_mesh *m, int op, int ng, std::vecto
     for (int64_t i = 0; i < m->nt; ++i)
         for (int32_t p = m->tp_ptr[i]; p < m->tp_ptr[i + 1]; ++p) {
             const int32_t j = m->tp_tri[p];
-            if (op == TDBEM_DLP || i <= j) {
+            if (op != TDBEM_SLP || i <= j) {  // the single layer is symmetric: unordered pairs
                 slot[p] = (int32_t)ti.size();
                 ti.push_back((int32_t)i);
                 tj.push_back(j);
@@ -704,7 +705,7 @@ extern "C" int tdbem_entries_path(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_f
     TD_CUDA(ctx, cudaMemcpyAsync(hc.data(), cols, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, ctx->stream));
     TD_CUDA(ctx, cudaMemcpyAsync(hf.data(), fidx, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost, ctx->stream));
     TD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const int64_t ncol_max = op->op == TDBEM_SLP ? mesh->nt : mesh->nv;
+    const int64_t ncol_max = op->op == TDBEM_DLP ? mesh->nv : mesh->nt;
     for (int32_t v : hr)
         if (v < 0 || v >= mesh->nt) return td_fail(ctx, TDBEM_ERR_ARG, "tdbem_entries_path: row %d out of range", v);
     for (int32_t v : hc)

@@ -238,8 +238,13 @@ TD_D c32 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int 
     const c32 e = expm_sr(sr, si, r);
     float w = xa.w * yb.w * rinv;
     if (op == TD_SLP) return {w * e.x, w * e.y};
-    const float4 n = __ldg(&m.nrm4[tj]);
-    w *= bary7f(b, loc) * -(dx * n.x + dy * n.y + dz * n.z) * rinv * rinv;
+    if (op == TD_DLP) {
+        const float4 n = __ldg(&m.nrm4[tj]);  // (x - y).n_y, P1 hat of the trial vertex
+        w *= bary7f(b, loc) * -(dx * n.x + dy * n.y + dz * n.z) * rinv * rinv;
+    } else {
+        const float4 n = __ldg(&m.nrm4[ti]);  // (y - x).n_x
+        w *= (dx * n.x + dy * n.y + dz * n.z) * rinv * rinv;
+    }
     const float pr = fmaf(sr, r, 1.0f), pi = si * r;
     return {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
 }
@@ -250,7 +255,10 @@ TD_D c64 point_pair(const MeshDev &m, int op, int ti, int a, int tj, int b, int 
     c64 e = expm_sr(sr, si, r);
     double w = m.qw[oa] * m.qw[ob] / r;
     if (op == TD_SLP) return {w * e.x, w * e.y};
-    w *= bary7d(b, loc) * -(dx * m.n64[tj] + dy * m.n64[m.nt + tj] + dz * m.n64[2 * m.nt + tj]) / (r * r);
+    if (op == TD_DLP)
+        w *= bary7d(b, loc) * -(dx * m.n64[tj] + dy * m.n64[m.nt + tj] + dz * m.n64[2 * m.nt + tj]) / (r * r);
+    else
+        w *= (dx * m.n64[ti] + dy * m.n64[m.nt + ti] + dz * m.n64[2 * m.nt + ti]) / (r * r);
     double pr = 1.0 + sr * r, pi = si * r;
     return {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
 }
@@ -264,7 +272,7 @@ TD_D cx<T> group_entry(const MeshDev &m, int row, int col, T sr, T si, bool vali
     const int sub = threadIdx.x & 7;
     cx<T> acc = {0, 0};
     if (valid && sub < 7) {
-        if (OP == TD_SLP) {
+        if (!TD_P1_TRIAL(OP)) {
             // independent point pairs in flight: 3 + 3 + 1
             cx<T> acc2 = {0, 0}, acc3 = {0, 0};
 #pragma unroll 1
@@ -1328,7 +1336,7 @@ template <class T, int OP>
 __global__ void __launch_bounds__(128) k_fibre_entries(MeshDev m, const double *sig, const int *rows, int64_t nr,
                                                        const int *cols, int64_t nc, int64_t nf, cx<T> *out) {
     const int64_t n = nr * nc * nf;
-    const int ncol_max = OP == TD_SLP ? m.nt : m.nv;
+    const int ncol_max = TD_P1_TRIAL(OP) ? m.nv : m.nt;
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 3;
     for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; base < n; base += stride) {
         const int64_t t = base + ((threadIdx.x & 31) >> 3);
@@ -1349,10 +1357,12 @@ int td_launch_fibre_entries(cudaStream_t st, const MeshDev &m, int op, int prec,
     const int grid = (int)std::min<int64_t>((n + 15) / 16, (int64_t)num_sms * 16);
     if (prec == TDBEM_FP64) {
         if (op == TD_SLP) k_fibre_entries<double, TD_SLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c64 *)out);
-        else k_fibre_entries<double, TD_DLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c64 *)out);
+        else if (op == TD_DLP) k_fibre_entries<double, TD_DLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c64 *)out);
+        else k_fibre_entries<double, TD_ADLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c64 *)out);
     } else {
         if (op == TD_SLP) k_fibre_entries<float, TD_SLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c32 *)out);
-        else k_fibre_entries<float, TD_DLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c32 *)out);
+        else if (op == TD_DLP) k_fibre_entries<float, TD_DLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c32 *)out);
+        else k_fibre_entries<float, TD_ADLP><<<grid, 128, 0, st>>>(m, sig, rows, nr, cols, nc, nf, (c32 *)out);
     }
     return (int)cudaGetLastError();
 }
@@ -1394,8 +1404,10 @@ int td_launch_far_aca(cudaStream_t st, const MeshDev &m, int op, int prec, const
     const int nitems = a.harvest ? a.nfar * a.nf : a.nfar;
     if (nitems == 0) return 0;
     if (prec == TDBEM_FP64)
-        return op == TD_SLP ? launch_far<double, TD_SLP>(st, m, a, o, p, nctas, nt)
-                            : launch_far<double, TD_DLP>(st, m, a, o, p, nctas, nt);
-    return op == TD_SLP ? launch_far<float, TD_SLP>(st, m, a, o, p, nctas, nt)
-                        : launch_far<float, TD_DLP>(st, m, a, o, p, nctas, nt);
+        return op == TD_SLP   ? launch_far<double, TD_SLP>(st, m, a, o, p, nctas, nt)
+               : op == TD_DLP ? launch_far<double, TD_DLP>(st, m, a, o, p, nctas, nt)
+                              : launch_far<double, TD_ADLP>(st, m, a, o, p, nctas, nt);
+    return op == TD_SLP   ? launch_far<float, TD_SLP>(st, m, a, o, p, nctas, nt)
+           : op == TD_DLP ? launch_far<float, TD_DLP>(st, m, a, o, p, nctas, nt)
+                          : launch_far<float, TD_ADLP>(st, m, a, o, p, nctas, nt);
 }

@@ -1,5 +1,6 @@
 // Entry kernels (Sec. 3; the ENTRY function of Algorithm 1):
 //   k_entries_generic : arbitrary rows x cols x frequencies (C-ABI tdbem_entries)
+//   (operators: single layer, double layer, adjoint double layer K')
 //   k_sing_table      : touching pairs (Sauter-Schwab, FP64) at all unique
 //                       frequencies, one warp per pair
 //   k_near_entries    : every entry of every near-field block at all unique
@@ -21,14 +22,14 @@ TD_D cx<T> entry_one(const MeshDev &m, int row, int col, double sr, double si) {
     load_test(m, row, X);
     cx<T> acc = {0, 0};
     c64 accs = {0.0, 0.0};
-    if (OP == TD_SLP) {
+    if (!TD_P1_TRIAL(OP)) {
         if (touching_slot(m, row, col) >= 0) {
             c64 o[3] = {};
-            pair_singular_f64<TD_SLP>(m, row, col, sr, si, o);
+            pair_singular_f64<OP>(m, row, col, sr, si, o);
             accs = o[0];
         } else {
             cx<T> o[3] = {};
-            R::template pair<TD_SLP>(X, m, col, (T)sr, (T)si, o);
+            R::template pair<OP>(X, m, col, (T)sr, (T)si, o);
             acc = o[0];
         }
     } else {
@@ -54,7 +55,7 @@ __global__ void k_entries_generic(MeshDev m, const double *sig, int nq, const in
                                   const int *cols, int64_t nc, const int *fidx, int64_t nf,
                                   cx<T> *out) {
     int64_t n = nr * nc * nf;
-    const int ncols = OP == TD_SLP ? m.nt : m.nv;
+    const int ncols = TD_P1_TRIAL(OP) ? m.nv : m.nt;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t c = t % nc, r = (t / nc) % nr, f = t / (nc * nr);
@@ -85,7 +86,7 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
         SingGeom G;
         classify_pair(m, ti, tj, G);
         const int nq = ss_npoints(G.cls, m.ng);
-        const bool zero = (OP == TD_DLP && G.cls == 3) || G.cls == 0;
+        const bool zero = (OP != TD_SLP && G.cls == 3) || G.cls == 0;
         for (int f0 = 0; f0 < nf; f0 += FC) {
             c64 acc[FC][3];
 #pragma unroll
@@ -100,8 +101,7 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
                     if (OP == TD_SLP) {
                         base = w / r;
                     } else {
-                        double dn = -(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]);
-                        base = w * dn / (r * r * r);
+                        base = w * ss_dn<OP>(G, d) / (r * r * r);
                     }
                     (void)pre;
 #pragma unroll
@@ -115,10 +115,15 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
                             } else {
                                 double pr = 1.0 + sr * r, pi = si * r;
                                 c64 v = {base * (pr * e.x - pi * e.y), base * (pr * e.y + pi * e.x)};
+                                if (OP == TD_ADLP) {
+                                    acc[j][0].x += v.x;
+                                    acc[j][0].y += v.y;
+                                } else {
 #pragma unroll
-                                for (int k = 0; k < 3; ++k) {
-                                    acc[j][k].x += lam[k] * v.x;
-                                    acc[j][k].y += lam[k] * v.y;
+                                    for (int k = 0; k < 3; ++k) {
+                                        acc[j][k].x += lam[k] * v.x;
+                                        acc[j][k].y += lam[k] * v.y;
+                                    }
                                 }
                             }
                         }
@@ -134,8 +139,8 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
                     outv[k] = {warp_sum(acc[j][k].x) * inv4pi, warp_sum(acc[j][k].y) * inv4pi};
                 if (lane == 0 && f0 + j < nf) {
                     c64 *o = table + ((int64_t)p * nf + f0 + j) * 3;
-                    if (OP == TD_SLP) {
-                        o[0] = outv[0];
+                    if (!TD_P1_TRIAL(OP)) {
+                        o[0] = zero ? c64{0.0, 0.0} : outv[0];
                         o[1] = o[2] = {0.0, 0.0};
                     } else {
                         // parametrisation order -> mesh-local trial vertex
@@ -161,7 +166,7 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    constexpr int NV = OP == TD_SLP ? 1 : 3;
+    constexpr int NV = TD_P1_TRIAL(OP) ? 3 : 1;
     // s / c of every frequency in shared memory (nf <= 256, checked by the caller):
     // a pass over FC frequencies reads them by broadcast instead of holding them
     __shared__ float2 s_sig[256];
@@ -177,7 +182,7 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
         SingGeom G;
         classify_pair(m, ti, tj, G);
         const int nq = ss_npoints(G.cls, m.ng);
-        const bool zero = (OP == TD_DLP && G.cls == 3) || G.cls == 0;
+        const bool zero = (OP != TD_SLP && G.cls == 3) || G.cls == 0;
         for (int f0 = 0; f0 < nf; f0 += FC) {
             c32 acc[FC][NV];
 #pragma unroll
@@ -198,7 +203,7 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
                     if (OP == TD_SLP) {
                         bf = (float)w * rinv;
                     } else {
-                        const float dn = (float)(-(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]));
+                        const float dn = (float)ss_dn<OP>(G, d);
                         bf = (float)w * dn * rinv * rinv * rinv;
                     }
                     float lf[3] = {(float)lam[0], (float)lam[1], (float)lam[2]};
@@ -215,7 +220,7 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
                         }
 #pragma unroll
                         for (int k = 0; k < NV; ++k) {
-                            const float lk = OP == TD_SLP ? 1.0f : lf[k];
+                            const float lk = TD_P1_TRIAL(OP) ? lf[k] : 1.0f;
                             acc[j][k].x = fmaf(lk, v.x, acc[j][k].x);
                             acc[j][k].y = fmaf(lk, v.y, acc[j][k].y);
                         }
@@ -234,8 +239,8 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
                     c64 *o = table + ((int64_t)p * nf + f0 + j) * 3;
                     const c64 z = {0.0, 0.0};
                     o[0] = o[1] = o[2] = z;
-                    if (OP == TD_SLP)
-                        o[0] = outv[0];
+                    if (!TD_P1_TRIAL(OP))
+                        o[0] = zero ? z : outv[0];
                     else
                         for (int k = 0; k < NV; ++k) o[G.loc[k]] = zero ? z : outv[k];
                 }
@@ -249,11 +254,16 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
 // pair (test triangle in registers, trial points streamed from the tables).
 template <int OP, int FC>
 TD_D void pair_multi(const TestF &X, const MeshDev &m, int tj, const float *sg, int nfc, c32 *acc, int loc) {
+    // signed kernel normal: -n_y (DLP) or +n_x (ADLP), multiplied by d = y - x
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (OP == TD_DLP) {
-        nx = m.n32[tj];
-        ny = m.n32[m.nt + tj];
-        nz = m.n32[2 * m.nt + tj];
+        nx = -m.n32[tj];
+        ny = -m.n32[m.nt + tj];
+        nz = -m.n32[2 * m.nt + tj];
+    } else if (OP == TD_ADLP) {
+        nx = X.nx;
+        ny = X.ny;
+        nz = X.nz;
     }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
@@ -270,7 +280,7 @@ TD_D void pair_multi(const TestF &X, const MeshDev &m, int tj, const float *sg, 
             const float rinv = rsqrtf(r2);
             const float r = r2 * rinv;
             float w = X.w[a] * wyb * rinv;
-            if (OP == TD_DLP) w *= -(dx * nx + dy * ny + dz * nz) * rinv * rinv;
+            if (OP != TD_SLP) w *= (dx * nx + dy * ny + dz * nz) * rinv * rinv;
 #pragma unroll
             for (int j = 0; j < FC; ++j) {
                 if (j < nfc) {
@@ -292,11 +302,15 @@ TD_D void pair_multi(const TestF &X, const MeshDev &m, int tj, const float *sg, 
 
 template <int OP, int FC>
 TD_D void pair_multi(const TestD &X, const MeshDev &m, int tj, const double *sg, int nfc, c64 *acc, int loc) {
-    double nx = 0.0, ny = 0.0, nz = 0.0;
+    double nx = 0.0, ny = 0.0, nz = 0.0;  // signed kernel normal, as in the FP32 version
     if (OP == TD_DLP) {
-        nx = m.n64[tj];
-        ny = m.n64[m.nt + tj];
-        nz = m.n64[2 * m.nt + tj];
+        nx = -m.n64[tj];
+        ny = -m.n64[m.nt + tj];
+        nz = -m.n64[2 * m.nt + tj];
+    } else if (OP == TD_ADLP) {
+        nx = X.nx;
+        ny = X.ny;
+        nz = X.nz;
     }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
@@ -308,7 +322,7 @@ TD_D void pair_multi(const TestD &X, const MeshDev &m, int tj, const double *sg,
             const double dx = yx - X.x[a], dy = yy - X.y[a], dz = yz - X.z[a];
             const double r = sqrt(dx * dx + dy * dy + dz * dz);
             double w = X.w[a] * wyb / r;
-            if (OP == TD_DLP) w *= -(dx * nx + dy * ny + dz * nz) / (r * r);
+            if (OP != TD_SLP) w *= (dx * nx + dy * ny + dz * nz) / (r * r);
 #pragma unroll
             for (int j = 0; j < FC; ++j) {
                 if (j < nfc) {
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(128) k_near_entries(MeshDev m, NearArgs a, con
         const int64_t fstride = (int64_t)nI * nJ;
         typename Reg<T>::Test X;
         load_test(m, row, X);
-        const int nsup = OP == TD_SLP ? 1 : m.v2t_ptr[col + 1] - m.v2t_ptr[col];
+        const int nsup = TD_P1_TRIAL(OP) ? m.v2t_ptr[col + 1] - m.v2t_ptr[col] : 1;
         for (int f0 = 0; f0 < nf; f0 += FC) {
             const int nfc = min(FC, nf - f0);
             cx<T> acc[FC];
@@ -366,7 +380,7 @@ __global__ void __launch_bounds__(128) k_near_entries(MeshDev m, NearArgs a, con
             for (int jj = 0; jj < FC; ++jj) sing[jj] = {0.0, 0.0};
             for (int sidx = 0; sidx < nsup; ++sidx) {
                 int e, l;
-                if (OP == TD_SLP) {
+                if (!TD_P1_TRIAL(OP)) {
                     e = col;
                     l = 0;
                 } else {
@@ -405,24 +419,29 @@ int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const
     if (prec == TDBEM_FP64) {
         if (op == TD_SLP)
             k_entries_generic<double, TD_SLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c64 *)out);
-        else
+        else if (op == TD_DLP)
             k_entries_generic<double, TD_DLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c64 *)out);
+        else
+            k_entries_generic<double, TD_ADLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c64 *)out);
     } else {
         if (op == TD_SLP)
             k_entries_generic<float, TD_SLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c32 *)out);
-        else
+        else if (op == TD_DLP)
             k_entries_generic<float, TD_DLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c32 *)out);
+        else
+            k_entries_generic<float, TD_ADLP><<<grid, 128, 0, st>>>(m, sig, nq, rows, nr, cols, nc, fidx, nf, (c32 *)out);
     }
     return (int)cudaGetLastError();
 }
 
 // Frequencies per pass of the mixed-form kernels, selected by the tuning
-// variant (0 = default): touching-pair table (single / double layer) and
-// near-field tensor.
+// variant (0 = default): touching-pair table (single layer / double layer /
+// adjoint double layer: one value per pair and frequency like the single
+// layer) and near-field tensor.
 constexpr int kSingFcSlp[3] = {36, 12, 24};
 constexpr int kSingFcDlp[3] = {12, 6, 8};
 constexpr int kNearFc[3] = {8, 4, 16};
-int td_sing_fc(int op, int variant) { return op == TD_SLP ? kSingFcSlp[variant % 3] : kSingFcDlp[variant % 3]; }
+int td_sing_fc(int op, int variant) { return op == TD_DLP ? kSingFcDlp[variant % 3] : kSingFcSlp[variant % 3]; }
 int td_near_fc(int variant) { return kNearFc[variant % 3]; }
 
 int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, const int *pti, const int *ptj,
@@ -436,17 +455,23 @@ int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, co
             if (v == 1) k_sing_table_mixed<TD_SLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else if (v == 2) k_sing_table_mixed<TD_SLP, 24><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else k_sing_table_mixed<TD_SLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-        } else {
+        } else if (op == TD_DLP) {
             if (v == 1) k_sing_table_mixed<TD_DLP, 6><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else if (v == 2) k_sing_table_mixed<TD_DLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else k_sing_table_mixed<TD_DLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+        } else {
+            if (v == 1) k_sing_table_mixed<TD_ADLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else if (v == 2) k_sing_table_mixed<TD_ADLP, 24><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_ADLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         }
         return (int)cudaGetLastError();
     }
     if (op == TD_SLP)
         k_sing_table<TD_SLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-    else
+    else if (op == TD_DLP)
         k_sing_table<TD_DLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+    else
+        k_sing_table<TD_ADLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
     return (int)cudaGetLastError();
 }
 
@@ -456,17 +481,22 @@ int td_launch_near_entries(cudaStream_t st, const MeshDev &m, int op, int prec, 
     int grid = (int)std::min<int64_t>((a.nentries + 127) / 128, (int64_t)num_sms * 16);
     if (prec == TDBEM_FP64) {
         if (op == TD_SLP) k_near_entries<double, TD_SLP, 4><<<grid, 128, 0, st>>>(m, a, table);
-        else k_near_entries<double, TD_DLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+        else if (op == TD_DLP) k_near_entries<double, TD_DLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+        else k_near_entries<double, TD_ADLP, 4><<<grid, 128, 0, st>>>(m, a, table);
     } else {
         const int v = variant % 3;
         if (op == TD_SLP) {
             if (v == 1) k_near_entries<float, TD_SLP, 4><<<grid, 128, 0, st>>>(m, a, table);
             else if (v == 2) k_near_entries<float, TD_SLP, 16><<<grid, 128, 0, st>>>(m, a, table);
             else k_near_entries<float, TD_SLP, 8><<<grid, 128, 0, st>>>(m, a, table);
-        } else {
+        } else if (op == TD_DLP) {
             if (v == 1) k_near_entries<float, TD_DLP, 4><<<grid, 128, 0, st>>>(m, a, table);
             else if (v == 2) k_near_entries<float, TD_DLP, 16><<<grid, 128, 0, st>>>(m, a, table);
             else k_near_entries<float, TD_DLP, 8><<<grid, 128, 0, st>>>(m, a, table);
+        } else {
+            if (v == 1) k_near_entries<float, TD_ADLP, 4><<<grid, 128, 0, st>>>(m, a, table);
+            else if (v == 2) k_near_entries<float, TD_ADLP, 16><<<grid, 128, 0, st>>>(m, a, table);
+            else k_near_entries<float, TD_ADLP, 8><<<grid, 128, 0, st>>>(m, a, table);
         }
     }
     return (int)cudaGetLastError();

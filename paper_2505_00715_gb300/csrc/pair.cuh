@@ -1,9 +1,11 @@
 // Galerkin pair integrals of the Laplace-domain layer operators on flat
 // triangles (Sec. 2 eqs. slp/dlp, Sec. 3 "Spatial discretisation").
 //
-//   SLP: int_x int_y exp(-s r/c) / (4 pi r)                       (P0 x P0)
-//   DLP: int_x int_y phi_m(y) exp(-s r/c)(1 + s r/c)(x-y).n_y / (4 pi r^3)
-//        for the three P1 hats phi_m of the trial triangle          (P0 x P1)
+//   SLP:  int_x int_y exp(-s r/c) / (4 pi r)                      (P0 x P0)
+//   DLP:  int_x int_y phi_m(y) exp(-s r/c)(1 + s r/c)(x-y).n_y / (4 pi r^3)
+//         for the three P1 hats phi_m of the trial triangle         (P0 x P1)
+//   ADLP: int_x int_y exp(-s r/c)(1 + s r/c)(y-x).n_x / (4 pi r^3)
+//         (K', eq. adlp: the conormal derivative at x)              (P0 x P0)
 //
 // Regular pairs: 7-point degree-5 rule in x and in y.  FP32 form: the
 // quadrature-point coordinates are split into hi + lo floats so that the
@@ -23,7 +25,10 @@
 #define TD_FOUR_PI 12.566370614359172953850573533118
 #define TD_INV_FOUR_PI_F 0.079577471545947667884f
 
-enum { TD_SLP = 0, TD_DLP = 1 };
+enum { TD_SLP = 0, TD_DLP = 1, TD_ADLP = 2 };
+// The double layer's trial space is P1 (a column is a vertex and its
+// triangles); the single layer and the adjoint double layer have P0 columns.
+#define TD_P1_TRIAL(OP) ((OP) == TD_DLP)
 
 struct MeshDev {
     int nt, nv;
@@ -74,6 +79,7 @@ TD_HD float bary7f(int b, int k) {
 // ---------------------------------------------------------------------------
 struct TestF {
     float xh[7], yh[7], zh[7], xl[7], yl[7], zl[7], w[7];
+    float nx, ny, nz;  // unit normal of the test triangle (adjoint double layer)
 };
 
 TD_D void load_test(const MeshDev &m, int t, TestF &T) {
@@ -88,6 +94,9 @@ TD_D void load_test(const MeshDev &m, int t, TestF &T) {
         T.zl[q] = m.qzl[o];
         T.w[q] = m.qw32[o];
     }
+    T.nx = m.n32[t];
+    T.ny = m.n32[m.nt + t];
+    T.nz = m.n32[2 * m.nt + t];
 }
 
 // e^{-sigma r} = e^{-sr r} (cos(si r) - i sin(si r)) for sigma = (sr, si), FP32
@@ -122,11 +131,16 @@ TD_D c32 expm_sr(float sr, float si, float r) {
 // over test X and trial triangle tj, sigma = s / c.  Unscaled by 1/(4 pi).
 template <int OP>
 TD_D void pair_f32(const TestF &X, const MeshDev &m, int tj, float sr, float si, c32 *out) {
+    // kernel normal: the trial normal with -d.n (DLP) or the test normal with +d.n (ADLP)
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (OP == TD_DLP) {
-        nx = m.n32[tj];
-        ny = m.n32[m.nt + tj];
-        nz = m.n32[2 * m.nt + tj];
+        nx = -m.n32[tj];
+        ny = -m.n32[m.nt + tj];
+        nz = -m.n32[2 * m.nt + tj];
+    } else if (OP == TD_ADLP) {
+        nx = X.nx;
+        ny = X.ny;
+        nz = X.nz;
     }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
@@ -149,15 +163,15 @@ TD_D void pair_f32(const TestF &X, const MeshDev &m, int tj, float sr, float si,
                 acc.x = fmaf(w, e.x, acc.x);
                 acc.y = fmaf(w, e.y, acc.y);
             } else {
-                // (1 + sigma r) e^{-sigma r} (-d.n) / r^3
-                const float dn = -(dx * nx + dy * ny + dz * nz);
+                // (1 + sigma r) e^{-sigma r} (d.n) / r^3, n signed as above
+                const float dn = dx * nx + dy * ny + dz * nz;
                 const float w = X.w[a] * dn * rinv * rinv * rinv;
                 const float pr = fmaf(sr, r, 1.0f), pi = si * r;
                 acc.x = fmaf(w, pr * e.x - pi * e.y, acc.x);
                 acc.y = fmaf(w, pr * e.y + pi * e.x, acc.y);
             }
         }
-        if (OP == TD_SLP) {
+        if (!TD_P1_TRIAL(OP)) {
             out[0].x = fmaf(wy, acc.x, out[0].x);
             out[0].y = fmaf(wy, acc.y, out[0].y);
         } else {
@@ -173,6 +187,7 @@ TD_D void pair_f32(const TestF &X, const MeshDev &m, int tj, float sr, float si,
 
 struct TestD {
     double x[7], y[7], z[7], w[7];
+    double nx, ny, nz;  // unit normal of the test triangle (adjoint double layer)
 };
 
 TD_D void load_test(const MeshDev &m, int t, TestD &T) {
@@ -184,6 +199,9 @@ TD_D void load_test(const MeshDev &m, int t, TestD &T) {
         T.z[q] = m.qz[o];
         T.w[q] = m.qw[o];
     }
+    T.nx = m.n64[t];
+    T.ny = m.n64[m.nt + t];
+    T.nz = m.n64[2 * m.nt + t];
 }
 
 TD_D c64 expm_sr(double sr, double si, double r) {
@@ -195,11 +213,15 @@ TD_D c64 expm_sr(double sr, double si, double r) {
 
 template <int OP>
 TD_D void pair_f64(const TestD &X, const MeshDev &m, int tj, double sr, double si, c64 *out) {
-    double nx = 0.0, ny = 0.0, nz = 0.0;
+    double nx = 0.0, ny = 0.0, nz = 0.0;  // signed kernel normal, as in pair_f32
     if (OP == TD_DLP) {
-        nx = m.n64[tj];
-        ny = m.n64[m.nt + tj];
-        nz = m.n64[2 * m.nt + tj];
+        nx = -m.n64[tj];
+        ny = -m.n64[m.nt + tj];
+        nz = -m.n64[2 * m.nt + tj];
+    } else if (OP == TD_ADLP) {
+        nx = X.nx;
+        ny = X.ny;
+        nz = X.nz;
     }
 #pragma unroll 1
     for (int b = 0; b < 7; ++b) {
@@ -216,14 +238,14 @@ TD_D void pair_f64(const TestD &X, const MeshDev &m, int tj, double sr, double s
                 acc.x += w * e.x;
                 acc.y += w * e.y;
             } else {
-                const double dn = -(dx * nx + dy * ny + dz * nz);
+                const double dn = dx * nx + dy * ny + dz * nz;
                 const double w = X.w[a] * dn / (r * r * r);
                 const double pr = 1.0 + sr * r, pi = si * r;
                 acc.x += w * (pr * e.x - pi * e.y);
                 acc.y += w * (pr * e.y + pi * e.x);
             }
         }
-        if (OP == TD_SLP) {
+        if (!TD_P1_TRIAL(OP)) {
             out[0].x += wy * acc.x;
             out[0].y += wy * acc.y;
         } else {
@@ -262,6 +284,7 @@ struct SingGeom {
     int loc[3];        // mesh-local index of trial parametrisation vertex k
     double g;          // Jacobian factor (2|ti|)(2|tj|)
     double ny[3];      // trial unit normal
+    double nx[3];      // test unit normal
 };
 
 // Shared vertices of ti and tj decide the class; the parametrisations follow
@@ -311,6 +334,9 @@ TD_D int classify_pair(const MeshDev &m, int ti, int tj, SingGeom &G) {
     G.ny[0] = m.n64[tj];
     G.ny[1] = m.n64[m.nt + tj];
     G.ny[2] = m.n64[2 * m.nt + tj];
+    G.nx[0] = m.n64[ti];
+    G.nx[1] = m.n64[m.nt + ti];
+    G.nx[2] = m.n64[2 * m.nt + ti];
     return ns;
 }
 
@@ -389,6 +415,14 @@ TD_D void ss_point(const SingGeom &G, int q, int ng, const double *gx, const dou
     }
 }
 
+// Signed normal factor of the double-layer kernels at difference d = y - x:
+// (x - y).n_y (DLP) or (y - x).n_x (ADLP).
+template <int OP>
+TD_HD double ss_dn(const SingGeom &G, const double d[3]) {
+    return OP == TD_DLP ? -(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2])
+                        : d[0] * G.nx[0] + d[1] * G.nx[1] + d[2] * G.nx[2];
+}
+
 // Kernel value times weight at one transformed point, accumulated into out
 // (mesh-local trial vertex order for DLP).  sigma = s / c.
 template <int OP>
@@ -401,13 +435,18 @@ TD_D void ss_accum(const SingGeom &G, const double d[3], double wgt, const doubl
         out[0].x += w * e.x;
         out[0].y += w * e.y;
     } else {
-        double dn = -(d[0] * G.ny[0] + d[1] * G.ny[1] + d[2] * G.ny[2]);
+        double dn = ss_dn<OP>(G, d);
         double w = wgt * dn / (r * r * r);
         double pr = 1.0 + sr * r, pi = si * r;
         c64 v = {w * (pr * e.x - pi * e.y), w * (pr * e.y + pi * e.x)};
-        for (int k = 0; k < 3; ++k) {
-            out[G.loc[k]].x += lam[k] * v.x;
-            out[G.loc[k]].y += lam[k] * v.y;
+        if (OP == TD_ADLP) {
+            out[0].x += v.x;
+            out[0].y += v.y;
+        } else {
+            for (int k = 0; k < 3; ++k) {
+                out[G.loc[k]].x += lam[k] * v.x;
+                out[G.loc[k]].y += lam[k] * v.y;
+            }
         }
     }
 }
@@ -424,7 +463,7 @@ TD_D int pair_singular_f64(const MeshDev &m, int ti, int tj, double sr, double s
     }
     SingGeom G;
     if (classify_pair(m, ti, tj, G) == 0) return 0;
-    if (OP == TD_DLP && G.cls == 3) return 3;  // flat panel: (x - y).n_y = 0
+    if (OP != TD_SLP && G.cls == 3) return 3;  // flat panel: (x - y).n = 0
     int nq = ss_npoints(G.cls, m.ng);
     for (int q = 0; q < nq; ++q) {
         double d[3], w, lam[3];

@@ -331,7 +331,7 @@ extern "C" int tdbem_tensor_load(tdbem_ctx_t ctx, const char *path, tdbem_tensor
     {
         const int64_t nb = hl[2], nr = hl[0], nc = hl[1], used = hl[3];
         const int Nu = hi[3], NQ = hi[4];
-        const bool sane = (hi[0] == TDBEM_SLP || hi[0] == TDBEM_DLP) && (hi[1] == TDBEM_FP64 || hi[1] == TDBEM_MIXED) &&
+        const bool sane = (hi[0] == TDBEM_SLP || hi[0] == TDBEM_DLP || hi[0] == TDBEM_ADLP) && (hi[1] == TDBEM_FP64 || hi[1] == TDBEM_MIXED) &&
                           Nu >= 1 && Nu <= 256 && NQ >= Nu && NQ <= (1 << 20) && nb >= 1 && nb < (1LL << 31) &&
                           nr >= 1 && nr < (1LL << 31) && nc >= 1 && nc < (1LL << 31) && used >= 0 && used < (1LL << 40);
         const long here = ftell(f);

@@ -77,11 +77,20 @@ def hous(td, ctx, orc):
 def _own_dof(k, op, rows):
     if op == "SLP":
         return np.asarray(rows, dtype=np.int32)
-    return k.T[np.asarray(rows), 0].astype(np.int32)
+    if op == "DLP":
+        return k.T[np.asarray(rows), 0].astype(np.int32)
+    # K' of a flat panel with itself is zero: a neighbour across vertex 0 instead
+    out = []
+    for r in rows:
+        v = k.T[r, 0]
+        out.append(next(t for t in np.nonzero((k.T == v).any(axis=1))[0] if t != r))
+    return np.asarray(out, dtype=np.int32)
 
 
 def _scale(k, orc, op, rows, fidx):
-    """Largest magnitude sum over the self-interaction entries of the rows."""
+    """Largest magnitude sum over the self-interaction entries of the rows
+    (for K', whose self-interaction vanishes, over entries of a neighbour
+    across the row's first vertex)."""
     own = _own_dof(k, op, rows)
     diag = np.stack([k.om.entries_mag(getattr(orc, op), [r], [q], k.f.s[fidx], c=k.c, ng=5)[:, 0, 0]
                      for r, q in zip(rows[:8], own[:8])], axis=1)
@@ -101,7 +110,7 @@ def _oracle(k, orc, op, rows, cols, fidx):
 
 def _near_strip(td, k, op):
     """A row leaf of the tree and every column of its near-field blocks."""
-    cols_b = td.P0 if op == "SLP" else td.P1
+    cols_b = td.P1 if op == "DLP" else td.P0
     tree = td.Tree(k.gm, td.P0, cols_b, k.leaf, 2.0)
     b = tree.blocks
     near = b[b[:, 4] == 0]
@@ -119,7 +128,7 @@ def _touch_mask(k, rows, cols, op):
     """True where test triangle rows[r] touches (shares a vertex with) the
     support of column cols[c]."""
     tv = [set(k.T[r]) for r in rows]
-    if op == "SLP":
+    if op != "DLP":
         cv = [set(k.T[c]) for c in cols]
     else:
         sup = {}
@@ -131,7 +140,7 @@ def _touch_mask(k, rows, cols, op):
 
 
 @pytest.mark.parametrize("prec", ["MIXED", "FP64"])
-@pytest.mark.parametrize("op", ["SLP", "DLP"])
+@pytest.mark.parametrize("op", ["SLP", "DLP", "ADLP"])
 @pytest.mark.parametrize("mesh", ["sphere", "housing"])
 def test_near_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     """Touching-pair table + near-field tensor kernel on a near-field row
@@ -140,7 +149,7 @@ def test_near_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     7 x 7 rule)."""
     k = sphere if mesh == "sphere" else hous
     rows, cols = _near_strip(td, k, op)
-    fidx = k.fidx if (mesh == "sphere" or op == "SLP") else k.fidx[::2]
+    fidx = k.fidx if (mesh == "sphere" or op != "DLP") else k.fidx[::2]
     g = td.entries(k.gm, getattr(td, op), k.f, rows, cols, fidx, prec=getattr(td, prec), c=k.c, ng=5,
                    path=td.PATH_NEAR).cpu().numpy()
     o, mag, sc = _oracle(k, orc, op, rows, cols, fidx)
@@ -154,7 +163,7 @@ def test_near_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
 
 
 @pytest.mark.parametrize("prec", ["MIXED", "FP64"])
-@pytest.mark.parametrize("op", ["SLP", "DLP"])
+@pytest.mark.parametrize("op", ["SLP", "DLP", "ADLP"])
 @pytest.mark.parametrize("mesh", ["sphere", "housing"])
 def test_generic_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     """tdbem_entries on the same near-field strip (its touching pairs are
@@ -171,7 +180,7 @@ def test_generic_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
 
 
 @pytest.mark.parametrize("prec", ["MIXED", "FP64"])
-@pytest.mark.parametrize("op", ["SLP", "DLP"])
+@pytest.mark.parametrize("op", ["SLP", "DLP", "ADLP"])
 @pytest.mark.parametrize("mesh", ["sphere", "housing"])
 def test_fibre_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     """The far-field engine's point-pair groups on rows x columns of
@@ -179,7 +188,7 @@ def test_fibre_path_vs_oracle(td, orc, sphere, hous, mesh, op, prec):
     s r / c is largest), every listed frequency: the entries of its row and
     column fibres and of its frequency tubes."""
     k = sphere if mesh == "sphere" else hous
-    cols_b = td.P0 if op == "SLP" else td.P1
+    cols_b = td.P1 if op == "DLP" else td.P0
     tree = td.Tree(k.gm, td.P0, cols_b, k.leaf, 2.0)
     b = tree.blocks
     far = b[b[:, 4] == 1]

@@ -80,13 +80,13 @@ def sphere2(td, ctx, orc):
 
 
 @pytest.mark.parametrize("prec,tol", [("FP64", 1e-12), ("MIXED", 1e-5)])
-@pytest.mark.parametrize("op", ["SLP", "DLP"])
+@pytest.mark.parametrize("op", ["SLP", "DLP", "ADLP"])
 def test_entries_vs_oracle(td, ctx, orc, sphere2, prec, tol, op):
     V, T, gm, om = sphere2
     f = td.Freqs.bdf2(ctx, 16, 0.1)
     fidx = f.unique
     rows = np.arange(len(T))
-    cols = np.arange(len(T) if op == "SLP" else len(V))
+    cols = np.arange(len(V) if op == "DLP" else len(T))
     opc = getattr(td, op)
     g = td.entries(gm, opc, f, rows, cols, fidx, prec=getattr(td, prec), ng=5).cpu().numpy()
     o = om.entries(getattr(orc, op), rows, cols, f.s[fidx], ng=5)
@@ -130,7 +130,7 @@ def _dense_all(om, orc, op, f, nrows, ncols):
 
 @pytest.mark.parametrize("dense_faces", [True, False])
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
-@pytest.mark.parametrize("op", ["SLP", "DLP"])
+@pytest.mark.parametrize("op", ["SLP", "DLP", "ADLP"])
 def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op, dense_faces):
     """320-triangle sphere, leaf 16 (leaf 32 has no admissible block here),
     eta 2, BDF2 N = 16: rebuilt tensor and apply vs the dense oracle, with the
@@ -138,14 +138,14 @@ def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op, dense_faces):
     import torch
     V, T, gm, om = sphere2
     f = td.Freqs.bdf2(ctx, 16, 0.1)
-    cols_b = td.P0 if op == "SLP" else td.P1
+    cols_b = td.P1 if op == "DLP" else td.P0
     tree = td.Tree(gm, td.P0, cols_b, 16, 2.0)
     eps = 1e-4
     X = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec),
                     dense_faces=dense_faces)
     st = X.stats()
     assert st["nfar"] > 0 and st["nnear"] > 0
-    nr, nc = len(T), (len(T) if op == "SLP" else len(V))
+    nr, nc = len(T), (len(V) if op == "DLP" else len(T))
     dense = _dense_all(om, orc, op, f, nr, nc)  # all 16 frequencies
     rr, cc = np.meshgrid(np.arange(nr), np.arange(nc), indexing="ij")
     reb = np.stack([X.entries(rr.ravel(), cc.ravel(), np.full(rr.size, k)).cpu().numpy().reshape(nr, nc)
@@ -167,17 +167,17 @@ def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op, dense_faces):
     assert np.linalg.norm(yh - y) <= 1e-5 * np.linalg.norm(y)
 
 
-@pytest.mark.parametrize("op,prec", [("SLP", "MIXED"), ("SLP", "FP64"), ("DLP", "MIXED")])
+@pytest.mark.parametrize("op,prec", [("SLP", "MIXED"), ("SLP", "FP64"), ("DLP", "MIXED"), ("ADLP", "MIXED")])
 def test_config2_sampled_apply(td, ctx, orc, op, prec):
-    """5120-triangle sphere, SLP (P0 x P0) and DLP (P0 x P1), BDF2 N = 64,
+    """5120-triangle sphere, SLP (P0 x P0), DLP (P0 x P1) and K' (P0 x P0), BDF2 N = 64,
     dt = 0.05, leaf 32, eta 2, eps 1e-4: apply on sampled rows vs the dense
     FP64 oracle apply."""
     import torch
     V, T = icosphere(4)
     gm, om = td.Mesh(ctx, V, T), orc.Mesh(V, T)
     f = td.Freqs.bdf2(ctx, 64, 0.05)
-    cols_b = td.P0 if op == "SLP" else td.P1
-    ncols = len(T) if op == "SLP" else len(V)
+    cols_b = td.P1 if op == "DLP" else td.P0
+    ncols = len(V) if op == "DLP" else len(T)
     tree = td.Tree(gm, td.P0, cols_b, 32, 2.0)
     eps = 1e-4
     X = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec))
