@@ -104,22 +104,32 @@ TD_D void load_test(const MeshDev &m, int t, TestF &T) {
 //   exponent: e^{-x} = 2^{t}, t = -x log2(e) formed as a rounded product plus
 //     its FMA-recovered rounding error and the low part of log2(e), then
 //     2^{t_hi} (1 + t_lo ln 2);
-//   phase: Cody-Waite additive reduction y - k 2pi with k = rint(y / 2pi) and
-//     2pi split into a float head and tail (two FMAs), then the SFU sin/cos,
-//     whose absolute error is below 4e-7 on [-pi, pi].
+//   phase: Cody-Waite additive reduction y - k 2pi with k the nearest integer
+//     to y / 2pi (formed by adding and subtracting 1.5 * 2^23, which rounds
+//     to an integer in round-to-nearest for |y / 2pi| < 2^22, on the FMA pipe
+//     instead of a separate rounding instruction) and 2pi split into a float
+//     head and tail (two FMAs), then the SFU sin/cos, whose absolute error is
+//     below 4e-7 on [-pi, pi].
+// The power of two is the SFU's ex2 with subnormal results flushed to zero
+// (values below 1.2e-38, far below the entries' resolution).
 #define TD_L2E_HI 1.44269502162933349609375f
 #define TD_L2E_LO 1.92596298909109e-08f
 #define TD_LN2_F 0.693147180559945309417f
 #define TD_2PI_HI 6.28318548202514648438f
 #define TD_2PI_LO (-1.7484556025237907e-07f)
 #define TD_INV_2PI_F 0.159154943091895335769f
+TD_D float ex2_ftz(float t) {
+    float v;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(v) : "f"(t));
+    return v;
+}
 TD_D c32 expm_sr(float sr, float si, float r) {
     const float x = sr * r;
     const float th = -x * TD_L2E_HI;
     const float tl = fmaf(-x, TD_L2E_HI, -th) - x * TD_L2E_LO;
-    const float ea = exp2f(th) * fmaf(tl, TD_LN2_F, 1.0f);
+    const float ea = ex2_ftz(th) * fmaf(tl, TD_LN2_F, 1.0f);
     const float y = si * r;
-    const float k = rintf(y * TD_INV_2PI_F);
+    const float k = __fsub_rn(__fadd_rn(y * TD_INV_2PI_F, 12582912.0f), 12582912.0f);
     float yr = fmaf(-k, TD_2PI_HI, y);
     yr = fmaf(-k, TD_2PI_LO, yr);
     float sn, cs;
