@@ -1456,9 +1456,16 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     off[6] = off[5] + al(sizeof(int64_t) * toff.size());
     off[7] = off[6] + al(sizeof(int64_t) * nb);
     off[8] = off[7] + al(sizeof(int32_t) * lperm.size());
+    // plan_Z: Z | T | packed coefficient rows Fp | packed weights Wk, each
+    // segment starting on a 32-value (256-byte) boundary
+    const int nq1 = t->NQ - nq0;
+    auto r32 = [](int64_t x) { return (x + 31) & ~(int64_t)31; };
+    const int KW0 = (int)r32(nq0), KW1 = (int)r32(nq1), FW = std::max(KW0, KW1), WS = KW0 + KW1;
+    const int64_t z_al = r32(std::max<int64_t>(zsize, 1)), t_al = r32(tsize);
+    const int64_t fp_size = (int64_t)rowtab.size() * FW, wk_size = t->ncols * nrhs * WS;
     char *mem = nullptr;
     if (cudaMalloc(&mem, std::max<size_t>(off[8], 256)) != cudaSuccess ||
-        cudaMalloc(&t->plan_Z, sizeof(c32) * (std::max<int64_t>(zsize, 1) + tsize)) != cudaSuccess) {
+        cudaMalloc(&t->plan_Z, sizeof(c32) * (z_al + t_al + fp_size + wk_size)) != cudaSuccess) {
         cudaGetLastError();
         if (mem) cudaFree(mem);
         t->plan_Z = nullptr;
@@ -1475,7 +1482,16 @@ int build_apply_plan(tdbem_tensor *t, int nrhs) {
     TD_CUDA(ctx, cudaMemcpy(mem + off[7], lperm.data(), sizeof(int32_t) * lperm.size(), cudaMemcpyHostToDevice));
     for (int k = 0; k < 8; ++k) t->plan_off[k] = off[k];
     t->plan_nft = (int)ftab.size();
-    t->plan_tz = std::max<int64_t>(zsize, 1);  // T follows Z in plan_Z
+    t->plan_tz = z_al;  // T follows Z in plan_Z
+    t->plan_fp = z_al + t_al;
+    t->plan_wk = z_al + t_al + fp_size;
+    t->plan_fw = FW;
+    t->plan_kw0 = KW0;
+    t->plan_kw1 = KW1;
+    if (td_launch_pack_fibres(ctx->stream, (const int2 *)(mem + off[1]), (int64_t)rowtab.size(), t->dpartner,
+                              (const int *)(mem + off[7]), nq0, nq1, (const c32 *)t->dfib, t->Nu,
+                              (c32 *)t->plan_Z + t->plan_fp, FW, ctx->num_sms))
+        return td_fail(ctx, TDBEM_ERR_CUDA, "apply plan: packing the coefficients failed");
     t->plan_rpt = rpt;
     t->plan_nq0 = nq0;
     t->plan_njobs = (int)jobs.size();
@@ -1496,13 +1512,16 @@ int apply_tc(tdbem_tensor *t, const void *W, int nrhs, void *y) {
     if (rc) return rc;
     char *mem = (char *)t->plan_mem;
     const ZGroup *groups = (const ZGroup *)(mem + t->plan_off[0]);
-    const int2 *rowtab = (const int2 *)(mem + t->plan_off[1]);
     const ZJob *jobs = (const ZJob *)(mem + t->plan_off[2]);
     const int64_t *zbase = (const int64_t *)(mem + t->plan_off[3]);
-    int e = td_launch_zgemm_apply(ctx->stream, groups, rowtab, t->dpartner, (const int *)(mem + t->plan_off[7]),
-                                  t->plan_nq0, (const c32 *)t->dfib, (const c32 *)W, t->dperm_c, (c32 *)t->plan_Z,
-                                  t->Nu, nrhs, t->ncols, t->NQ, jobs, t->plan_njobs, ctx->dflags, ctx->wait_polls,
-                                  ctx->num_sms);
+    const int nq1 = t->NQ - t->plan_nq0, WS = t->plan_kw0 + t->plan_kw1;
+    c32 *Wk = (c32 *)t->plan_Z + t->plan_wk;
+    int e = td_launch_pack_weights(ctx->stream, (const c32 *)W, t->dperm_c, (const int *)(mem + t->plan_off[7]),
+                                   t->ncols, nrhs, t->plan_nq0, nq1, t->plan_kw0, t->plan_kw1, Wk, ctx->num_sms);
+    if (!e)
+        e = td_launch_zgemm_apply(ctx->stream, groups, (const c32 *)t->plan_Z + t->plan_fp, t->plan_fw, Wk, WS,
+                                  t->plan_kw0, t->plan_nq0, nq1, (c32 *)t->plan_Z, nrhs, jobs, t->plan_njobs,
+                                  ctx->dflags, ctx->wait_polls, ctx->num_sms);
     if (e) return td_fail(ctx, TDBEM_ERR_CUDA, "tensor-core contraction failed: %s", cudaGetErrorString((cudaError_t)e));
     ApplyZArgs a{};
     a.nb = (int)t->nblocks;

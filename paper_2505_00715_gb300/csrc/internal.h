@@ -119,6 +119,10 @@ struct tdbem_tensor {
     void *plan_mem = nullptr, *plan_Z = nullptr;
     size_t plan_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int plan_nq0 = 0;
+    // packed contraction operands inside plan_Z (complex offsets), their row
+    // strides and half widths (see td_launch_pack_fibres / _weights)
+    int64_t plan_fp = 0, plan_wk = 0;
+    int plan_fw = 0, plan_kw0 = 0, plan_kw1 = 0;
     int plan_nft = 0;
     int64_t plan_tz = 0;
     size_t host_buf_bytes = 0;

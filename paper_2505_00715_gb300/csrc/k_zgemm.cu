@@ -89,57 +89,43 @@ struct DenseOps {
 //   A[(b,d,p)][l] = f_d(l) if l belongs to half p (p = 1: conjugate half,
 //                   coefficient conj(f_d[u])), else 0
 //   Z[(b,d,p)][(j,c)] = sum_l A[(b,d,p)][l] W[l][J0 + j][c]
-// The contraction index runs over the frequencies in the order lperm (half 0
-// first); the rows of a group are ordered half 0 then half 1, and a tile of
-// one half contracts over that half's frequencies only (the other half's
-// coefficients are zero).
+// The rows of a group are ordered half 0 then half 1, and a tile of one half
+// contracts over that half's frequencies only (the other half's coefficients
+// are zero).  Both operands come packed (td_launch_pack_fibres / _weights):
+// the 8 frequencies of a load item are 64 contiguous bytes, read as four
+// 16-byte loads; the zero padding of each half covers the last chunk.
 struct ApplyOps {
     const ZGroup *groups;
-    const int2 *rowtab;   // (block, 2 * term + half) per Z row
-    const int *qmap;      // [NQ]
-    const int *lperm;     // [NQ] contraction order of the frequencies
-    int nq0;              // frequencies of half 0 (first in lperm)
-    const c32 *fib;       // [nb][Nu][Nu]
-    const c32 *W;         // [NQ][ncols][nrhs]
-    const int *perm_c;
+    const c32 *Fp;        // packed coefficient rows, stride FW
+    const c32 *Wk;        // packed weights, stride WS
     c32 *Z;
-    int Nu, nrhs;
-    int64_t ncols;
-    TD_D void a8(const ZJob &j, int m, int l, int lend, c32 *x) const {
-        const int2 rt = rowtab[groups[j.g].row0 + m];
-        const int half = rt.y & 1;
-        const c32 *fr = fib + ((int64_t)rt.x * Nu + (rt.y >> 1)) * Nu;
-        int qm[8];
+    int FW, WS, hoff1, nq0, nq1, nrhs;
+    TD_D static void load8(const c32 *p, c32 *x) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) qm[e] = l + e < lend ? qmap[lperm[l + e]] : 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const bool on = qm[e] != 0 && (qm[e] > 0 ? 0 : 1) == half;
-            const c32 f = on ? fr[qm[e] > 0 ? qm[e] - 1 : -qm[e] - 1] : c32{0.f, 0.f};
-            x[e] = half ? cconj(f) : f;
+        for (int e = 0; e < 4; ++e) {
+            const float4 v = q[e];
+            x[2 * e] = c32{v.x, v.y};
+            x[2 * e + 1] = c32{v.z, v.w};
         }
     }
-    TD_D void b8(const ZJob &j, int l, int lend, int n, c32 *x) const {
+    TD_D void a8(const ZJob &j, int m, int k, int, c32 *x) const {
+        load8(Fp + (int64_t)(groups[j.g].row0 + m) * FW + k, x);
+    }
+    TD_D void b8(const ZJob &j, int k, int, int n, c32 *x) const {
         const ZGroup &g = groups[j.g];
-        const int jj = n / nrhs, c = n - jj * nrhs;
-        const c32 *w = W + (int64_t)perm_c[g.J0 + jj] * nrhs + c;
-        const int64_t ls = ncols * nrhs;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = l + e < lend ? w[(int64_t)lperm[l + e] * ls] : c32{0.f, 0.f};
+        load8(Wk + ((int64_t)g.J0 * nrhs + n) * WS + (j.half == 2 ? hoff1 : 0) + k, x);
     }
     TD_D int rows(const ZJob &j) const { return min(kTM, (j.half == 1 ? groups[j.g].Mh : groups[j.g].M) - j.m0); }
-    TD_D void krange(const ZJob &j, int K, int &kb, int &ke) const {
-        kb = j.half == 2 ? nq0 : 0;
-        ke = j.half == 1 ? nq0 : K;
-        if (kb >= ke) {  // (no such job is planned) every frequency: the other half's coefficients are zero
-            kb = 0;
-            ke = K;
-        }
-    }
     TD_D int cols(const ZJob &j) const { return min(kTN, groups[j.g].L - j.n0); }
     TD_D c32 *drow(const ZJob &j, int m) const {
         const ZGroup &g = groups[j.g];
         return Z + g.zoff + (int64_t)m * g.L;
+    }
+    // the frequencies of the tile's half, in packed (local) numbering
+    TD_D void krange(const ZJob &j, int, int &kb, int &ke) const {
+        kb = 0;
+        ke = j.half == 2 ? nq1 : nq0;
     }
 };
 
@@ -325,12 +311,84 @@ int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 
     return launch_zgemm(st, ops, jobs, njobs, K, err, max_polls, num_sms);
 }
 
-int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap,
-                          const int *lperm, int nq0, const c32 *fib, const c32 *W, const int *perm_c, c32 *Z, int Nu,
-                          int nrhs, int64_t ncols, int NQ, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
-                          int num_sms) {
-    ApplyOps ops{groups, rowtab, qmap, lperm, nq0, fib, W, perm_c, Z, Nu, nrhs, ncols};
-    return launch_zgemm(st, ops, jobs, njobs, NQ, err, max_polls, num_sms);
+int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const c32 *Fp, int FW, const c32 *Wk, int WS,
+                          int hoff1, int nq0, int nq1, c32 *Z, int nrhs, const ZJob *jobs, int njobs, int *err,
+                          uint32_t max_polls, int num_sms) {
+    ApplyOps ops{groups, Fp, Wk, Z, FW, WS, hoff1, nq0, nq1, nrhs};
+    return launch_zgemm(st, ops, jobs, njobs, nq0 + nq1, err, max_polls, num_sms);
+}
+
+namespace {
+__global__ void k_pack_fibres(const int2 *rowtab, int64_t nrows, const int *qmap, const int *lperm, int nq0,
+                              int nq1, const c32 *fib, int Nu, c32 *Fp, int FW) {
+    const int64_t n = nrows * FW;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / FW;
+        const int k = (int)(e - r * FW);
+        const int2 rt = rowtab[r];
+        const int p = rt.y & 1, d = rt.y >> 1;
+        c32 v = {0.f, 0.f};
+        if (k < (p ? nq1 : nq0)) {
+            const int mp = qmap[lperm[(p ? nq0 : 0) + k]];  // > 0 in half 0, < 0 in half 1
+            const c32 f = fib[((int64_t)rt.x * Nu + d) * Nu + (mp > 0 ? mp - 1 : -mp - 1)];
+            v = p ? cconj(f) : f;
+        }
+        Fp[e] = v;
+    }
+}
+
+// 32 frequencies x 32 columns (j', c) per tile, transposed through shared
+// memory: W rows read and Wk rows written 256 bytes at a time.
+__global__ void __launch_bounds__(256) k_pack_weights(const c32 *W, const int *perm_c, const int *lperm,
+                                                      int64_t ncols, int nrhs, int nq0, int nq1, int KW0, int KW1,
+                                                      c32 *Wk) {
+    __shared__ c32 tile[32][33];
+    const int64_t ncolr = ncols * nrhs;
+    const int WS = KW0 + KW1, nkt0 = KW0 / 32, nkt = nkt0 + KW1 / 32;
+    const int64_t nnt = (ncolr + 31) / 32;
+    for (int64_t job = blockIdx.x; job < nnt * nkt; job += gridDim.x) {
+        const int kt = (int)(job % nkt);
+        const int64_t nt = job / nkt;
+        const int p = kt >= nkt0 ? 1 : 0;
+        const int k0 = (p ? kt - nkt0 : kt) * 32, nqp = p ? nq1 : nq0, kb = p ? nq0 : 0, hoff = p ? KW0 : 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int kk = e >> 5, nn = e & 31;
+            const int64_t n = nt * 32 + nn;
+            const int k = k0 + kk;
+            c32 v = {0.f, 0.f};
+            if (n < ncolr && k < nqp) {
+                const int64_t jp = n / nrhs;
+                const int c = (int)(n - jp * nrhs);
+                v = W[((int64_t)lperm[kb + k] * ncols + perm_c[jp]) * nrhs + c];
+            }
+            tile[kk][nn] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int nn = e >> 5, kk = e & 31;
+            const int64_t n = nt * 32 + nn;
+            if (n < ncolr) Wk[n * WS + hoff + k0 + kk] = tile[kk][nn];
+        }
+    }
+}
+}  // namespace
+
+int td_launch_pack_fibres(cudaStream_t st, const int2 *rowtab, int64_t nrows, const int *qmap, const int *lperm,
+                          int nq0, int nq1, const c32 *fib, int Nu, c32 *Fp, int FW, int num_sms) {
+    if (nrows == 0) return 0;
+    const int grid = (int)std::min<int64_t>((nrows * FW + 255) / 256, (int64_t)num_sms * 16);
+    k_pack_fibres<<<grid, 256, 0, st>>>(rowtab, nrows, qmap, lperm, nq0, nq1, fib, Nu, Fp, FW);
+    return (int)cudaGetLastError();
+}
+
+int td_launch_pack_weights(cudaStream_t st, const c32 *W, const int *perm_c, const int *lperm, int64_t ncols,
+                           int nrhs, int nq0, int nq1, int KW0, int KW1, c32 *Wk, int num_sms) {
+    const int64_t jobs = ((ncols * nrhs + 31) / 32) * ((KW0 + KW1) / 32);
+    if (jobs == 0) return 0;
+    const int grid = (int)std::min<int64_t>(jobs, (int64_t)num_sms * 8);
+    k_pack_weights<<<grid, 256, 0, st>>>(W, perm_c, lperm, ncols, nrhs, nq0, nq1, KW0, KW1, Wk);
+    return (int)cudaGetLastError();
 }
 
 int td_zgemm_tile_rows() { return kTM; }

@@ -124,12 +124,22 @@ struct ZGroup {             // rows (block, term, half) that share a column clus
 int td_launch_zgemm_dense(cudaStream_t st, const c32 *A, int64_t lda, const c32 *B, int64_t ldb, c32 *D, int64_t ldd,
                           int M, int N, int K, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
                           int num_sms);
-// lperm: frequency order of the contraction (the nq0 frequencies of half 0
-// first, then those of the conjugate half)
-int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const int2 *rowtab, const int *qmap,
-                          const int *lperm, int nq0, const c32 *fib, const c32 *W, const int *perm_c, c32 *Z, int Nu,
-                          int nrhs, int64_t ncols, int NQ, const ZJob *jobs, int njobs, int *err, uint32_t max_polls,
-                          int num_sms);
+// Operands of the apply contraction, packed so that a tile's 8 consecutive
+// frequencies of a row are 64 contiguous bytes.  Frequency order lperm: the
+// nq0 frequencies of half 0 first, then the nq1 of the conjugate half; each
+// half padded with zeros to KW0 / KW1 (multiples of 32) values.
+//   Fp[r][k'] (row stride FW = max(KW0, KW1)): Z row r = (block, term, half p)
+//     -> its coefficient at frequency lperm[(p ? nq0 : 0) + k'] (conjugated for
+//     p = 1), once per apply plan;
+//   Wk[j' nrhs + c][hoff_p + k'] (row stride WS = KW0 + KW1, hoff_1 = KW0):
+//     W[lperm[(p ? nq0 : 0) + k']][perm_c[j']][c], once per apply.
+int td_launch_pack_fibres(cudaStream_t st, const int2 *rowtab, int64_t nrows, const int *qmap, const int *lperm,
+                          int nq0, int nq1, const c32 *fib, int Nu, c32 *Fp, int FW, int num_sms);
+int td_launch_pack_weights(cudaStream_t st, const c32 *W, const int *perm_c, const int *lperm, int64_t ncols,
+                           int nrhs, int nq0, int nq1, int KW0, int KW1, c32 *Wk, int num_sms);
+int td_launch_zgemm_apply(cudaStream_t st, const ZGroup *groups, const c32 *Fp, int FW, const c32 *Wk, int WS,
+                          int hoff1, int nq0, int nq1, c32 *Z, int nrhs, const ZJob *jobs, int njobs, int *err,
+                          uint32_t max_polls, int num_sms);
 int td_zgemm_tile_rows();
 int td_zgemm_tile_cols();
 
