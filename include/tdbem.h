@@ -340,8 +340,11 @@ int tdbem_apply_weighted(tdbem_tensor_t t, const void *W, int32_t nrhs, void *y)
  * term as complex GEMMs on the tensor cores (tcgen05, BF16 operands split in
  * a high and a low part, FP32 accumulation; see tdbem_zgemm), keeps the
  * result in a device buffer of 2 * nrhs * sum_b rank_b * |J_b| complex values
- * owned by the tensor (reallocated when nrhs changes), and then applies the
- * faces on the FP32 cores.  The FP64 form runs every step in FP64. */
+ * owned by the tensor (reallocated when nrhs changes; with it a packed copy
+ * of the fibre coefficients, and of W for each call, NQ * ncols * nrhs
+ * complex values), and then applies the faces on the FP32 cores.  The first
+ * call for a tensor and nrhs builds this plan on the host and synchronises
+ * the stream.  The FP64 form runs every step in FP64. */
 /* y = A(s_fidx) x for one point of the full list: x device [ncols][nrhs]. */
 int tdbem_apply_freq(tdbem_tensor_t t, int32_t fidx, const void *x, int32_t nrhs, void *y);
 /* Same as tdbem_apply_weighted with host W and y (pinned or pageable): the
