@@ -584,24 +584,38 @@ TD_D void gram_sums(const FarFreq<T> &F, GramTiles<T> &G, int l, int kf, int nI,
     __syncthreads();
 }
 
+// Asynchronous 8-byte copy global -> shared (zero-filled when !valid; src
+// must still be a valid address), commit and wait of copy groups.
+TD_D void cp_async8(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+TD_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+TD_D void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Rebuild of a large face H = sum_{t<kf} u_t v_t^T with its arg-max (FP32
 // form).  The face is swept in tiles of (NT/16)*4 rows x 64 columns; chunks
-// of KC factor columns are staged in shared memory (the Gram tiles' space),
-// and every thread accumulates a 4 x 4 register tile: rows 4*ty .. 4*ty+3
-// and columns tx, tx+16, tx+32, tx+48 (8 shared loads per 16 complex MACs,
-// conflict-free).  Entries are summed over t in the same order as the plain
-// rebuild.  Dense-face blocks also store the face to Sd.
+// of KC factor columns are staged in shared memory (the Gram tiles' space)
+// in two stages, the next chunk's asynchronous copies in flight while the
+// current one is multiplied; every thread accumulates a 4 x 4 register tile:
+// rows 4*ty .. 4*ty+3 and columns tx, tx+16, tx+32, tx+48 (8 shared loads
+// per 16 complex MACs, conflict-free).  Entries are summed over t in the
+// same order as the plain rebuild.  Dense-face blocks also store the face to
+// Sd.
 template <int NT>
 struct RebuildTile {
-    static constexpr int TI = NT / 16 * 4, TJ = 64, KC = NT <= 128 ? 16 : 8;
+    static constexpr int TI = NT / 16 * 4, TJ = 64, KC = NT <= 128 ? 8 : 4;
 };
 
 template <int NT, class AM>
 TD_D void rebuild_tiled(void *smem, const c32 *Uw, const c32 *Vw, int64_t maxI, int64_t maxJ, int kf, int nI, int nJ,
                         c32 *Sd, AM &am) {
     constexpr int TI = RebuildTile<NT>::TI, TJ = RebuildTile<NT>::TJ, KC = RebuildTile<NT>::KC;
-    c32(*su)[TI] = reinterpret_cast<c32(*)[TI]>(smem);
-    c32(*sv)[TJ] = reinterpret_cast<c32(*)[TJ]>(reinterpret_cast<c32 *>(smem) + KC * TI);
+    constexpr int SSTAGE = KC * (TI + TJ);  // complex values per stage: U chunk [KC][TI], V chunk [KC][TJ]
+    c32 *base = reinterpret_cast<c32 *>(smem);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (int i0 = 0; i0 < nI; i0 += TI) {
         for (int j0 = 0; j0 < nJ; j0 += TJ) {
@@ -610,29 +624,45 @@ TD_D void rebuild_tiled(void *smem, const c32 *Uw, const c32 *Vw, int64_t maxI, 
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) h[x][y] = c32{0.f, 0.f};
-            for (int t0 = 0; t0 < kf; t0 += KC) {
-                const int kc = min(KC, kf - t0);
-                __syncthreads();
+            auto stage = [&](int st, int t0) {
+                c32 *u = base + st * SSTAGE, *v = u + KC * TI;
                 for (int e = tid; e < KC * TI; e += NT) {
                     const int t = e / TI, x = e - t * TI;
-                    su[t][x] = (t < kc && i0 + x < nI) ? Uw[(int64_t)(t0 + t) * maxI + i0 + x] : c32{0.f, 0.f};
+                    const bool ok = t0 + t < kf && i0 + x < nI;
+                    cp_async8(u + e, ok ? Uw + (int64_t)(t0 + t) * maxI + i0 + x : Uw, ok);
                 }
                 for (int e = tid; e < KC * TJ; e += NT) {
                     const int t = e / TJ, y = e - t * TJ;
-                    sv[t][y] = (t < kc && j0 + y < nJ) ? Vw[(int64_t)(t0 + t) * maxJ + j0 + y] : c32{0.f, 0.f};
+                    const bool ok = t0 + t < kf && j0 + y < nJ;
+                    cp_async8(v + e, ok ? Vw + (int64_t)(t0 + t) * maxJ + j0 + y : Vw, ok);
+                }
+                cp_async_commit();
+            };
+            __syncthreads();  // the shared space is free (caller, previous tile)
+            if (kf > 0) stage(0, 0);  // (kf = 0: zero face, no copies in flight)
+            int st = 0;
+            for (int t0 = 0; t0 < kf; t0 += KC, st ^= 1) {
+                if (t0 + KC < kf) {
+                    stage(st ^ 1, t0 + KC);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
                 __syncthreads();
+                const c32 *su = base + st * SSTAGE, *sv = su + KC * TI;
+                const int kc = min(KC, kf - t0);
                 for (int t = 0; t < kc; ++t) {
                     c32 u[4], v[4];
 #pragma unroll
-                    for (int x = 0; x < 4; ++x) u[x] = su[t][4 * ty + x];
+                    for (int x = 0; x < 4; ++x) u[x] = su[t * TI + 4 * ty + x];
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) v[y] = sv[t][tx + 16 * y];
+                    for (int y = 0; y < 4; ++y) v[y] = sv[t * TJ + tx + 16 * y];
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) cfma(h[x][y], u[x], v[y]);
                 }
+                __syncthreads();  // this stage is refilled two chunks later
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
@@ -766,8 +796,8 @@ TD_D void dense_grams(const cx<T> *Hs, int l, int64_t nIJ, AccT<T> *gH) {
 template <class T, int OP, int NT>
 __global__ void __launch_bounds__(NT, 640 / NT) k_far_aca(MeshDev m, FarArgs a, TensorOut o, AcaParams p) {
     static_assert(sizeof(GramTiles<float>) >=
-                      RebuildTile<NT>::KC * (RebuildTile<NT>::TI + RebuildTile<NT>::TJ) * sizeof(c32),
-                  "rebuild tiles must fit in the Gram tiles' shared memory");
+                      2 * RebuildTile<NT>::KC * (RebuildTile<NT>::TI + RebuildTile<NT>::TJ) * sizeof(c32),
+                  "both rebuild stages must fit in the Gram tiles' shared memory");
     static_assert(sizeof(GramTiles<T>) >= kDenseS * sizeof(cx<T>), "S of a dense-S face must fit in the Gram tiles");
     using AM = typename AmOf<T>::type;
     using A = AccT<T>;
