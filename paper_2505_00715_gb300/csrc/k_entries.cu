@@ -155,11 +155,14 @@ __global__ void k_sing_table(MeshDev m, const int *pti, const int *ptj, int npai
 }
 
 // Mixed form of the touching-pair table: the transformed coordinates, the
-// Jacobian weights and the cross-lane sums are FP64; the smooth factor
-// e^{-sigma r} (SLP) or e^{-sigma r}(1 + sigma r) (DLP) of every point and
-// frequency runs on the FP32 special-function path (relative error about
-// 3e-7), and each lane's partial sums over its points are FP32.  All FC
-// frequencies of a pass share one evaluation of the point geometry.
+// Jacobian weights and the chunk sums in the table are FP64; the smooth
+// factor e^{-sigma r} (SLP) or e^{-sigma r}(1 + sigma r) (DLP, ADLP) of
+// every point and frequency runs on the FP32 special-function path
+// (relative error about 3e-7), and each lane's partial sums over its points
+// are FP32.  The points of a pair are taken in chunks of 32 P (P per lane,
+// held in registers): the FP64 point geometry of a chunk is formed once and
+// reused by every frequency, FC frequencies per pass; each pass's lane sums
+// are reduced over the warp and added to the pair's table rows.
 template <int OP, int FC>
 __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, int npairs, const double *sig,
                                    int nf, c64 *table) {
@@ -167,11 +170,12 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     constexpr int NV = TD_P1_TRIAL(OP) ? 3 : 1;
-    // s / c of every frequency in shared memory (nf <= 256, checked by the caller):
-    // a pass over FC frequencies reads them by broadcast instead of holding them
+    constexpr int P = TD_P1_TRIAL(OP) ? 8 : 16;  // points per lane and chunk
+    // s / c of every frequency in shared memory (nf <= 256, checked by the caller)
     __shared__ float2 s_sig[256];
     for (int k = threadIdx.x; k < nf; k += blockDim.x) s_sig[k] = make_float2((float)sig[2 * k], (float)sig[2 * k + 1]);
     __syncthreads();
+    const double inv4pi = 1.0 / TD_FOUR_PI;
     for (int p = warp; p < npairs; p += nwarps) {
         int ti = pti[p], tj = ptj[p];
         if (OP == TD_SLP && ti > tj) {
@@ -183,66 +187,72 @@ __global__ void k_sing_table_mixed(MeshDev m, const int *pti, const int *ptj, in
         classify_pair(m, ti, tj, G);
         const int nq = ss_npoints(G.cls, m.ng);
         const bool zero = (OP != TD_SLP && G.cls == 3) || G.cls == 0;
-        for (int f0 = 0; f0 < nf; f0 += FC) {
-            c32 acc[FC][NV];
+        c64 *o = table + (int64_t)p * nf * 3;
+        for (int e = lane; e < nf * 3; e += 32) o[e] = c64{0.0, 0.0};
+        __syncwarp();
+        if (zero) continue;
+        for (int q0 = 0; q0 < nq; q0 += 32 * P) {
+            // the transformed point and the difference x - y in FP64 (no
+            // cancellation near the singularity); |d|^2 is exact to FP64
+            // rounding, so the square root, the division and the rest run in
+            // FP32 at FP32 relative accuracy
+            float rf[P], bf[P], lf[P][NV];
 #pragma unroll
-            for (int j = 0; j < FC; ++j)
+            for (int i = 0; i < P; ++i) {
+                const int q = q0 + 32 * i + lane;
+                rf[i] = 1.0f;
+                bf[i] = 0.0f;
 #pragma unroll
-                for (int k = 0; k < NV; ++k) acc[j][k] = {0.f, 0.f};
-            if (!zero) {
-                for (int q = lane; q < nq; q += 32) {
+                for (int k = 0; k < NV; ++k) lf[i][k] = 0.0f;
+                if (q < nq) {
                     double d[3], w, lam[3];
                     ss_point(G, q, m.ng, m.gx, m.gw, d, w, lam);
-                    // the transformed point and the difference x - y in FP64 (no
-                    // cancellation near the singularity); |d|^2 is exact to FP64
-                    // rounding, so the square root, the division and the rest run
-                    // in FP32 at FP32 relative accuracy
                     const float r2 = (float)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                    const float rinv = rsqrtf(r2), rf = r2 * rinv;
-                    float bf;
-                    if (OP == TD_SLP) {
-                        bf = (float)w * rinv;
-                    } else {
-                        const float dn = (float)ss_dn<OP>(G, d);
-                        bf = (float)w * dn * rinv * rinv * rinv;
-                    }
-                    float lf[3] = {(float)lam[0], (float)lam[1], (float)lam[2]};
+                    const float rinv = rsqrtf(r2);
+                    rf[i] = r2 * rinv;
+                    bf[i] = OP == TD_SLP ? (float)w * rinv : (float)w * (float)ss_dn<OP>(G, d) * rinv * rinv * rinv;
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) lf[i][k] = TD_P1_TRIAL(OP) ? (float)lam[k] : 1.0f;
+                }
+            }
+            for (int f0 = 0; f0 < nf; f0 += FC) {
+                c32 acc[FC][NV];
+#pragma unroll
+                for (int j = 0; j < FC; ++j)
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) acc[j][k] = {0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
 #pragma unroll
                     for (int j = 0; j < FC; ++j) {
                         const float2 sgj = s_sig[min(f0 + j, nf - 1)];
-                        const c32 e = expm_sr(sgj.x, sgj.y, rf);
+                        const c32 e = expm_sr(sgj.x, sgj.y, rf[i]);
                         c32 v;
                         if (OP == TD_SLP) {
-                            v = {bf * e.x, bf * e.y};
+                            v = {bf[i] * e.x, bf[i] * e.y};
                         } else {
-                            const float pr = fmaf(sgj.x, rf, 1.0f), pi = sgj.y * rf;
-                            v = {bf * (pr * e.x - pi * e.y), bf * (pr * e.y + pi * e.x)};
+                            const float pr = fmaf(sgj.x, rf[i], 1.0f), pi = sgj.y * rf[i];
+                            v = {bf[i] * (pr * e.x - pi * e.y), bf[i] * (pr * e.y + pi * e.x)};
                         }
 #pragma unroll
                         for (int k = 0; k < NV; ++k) {
-                            const float lk = TD_P1_TRIAL(OP) ? lf[k] : 1.0f;
-                            acc[j][k].x = fmaf(lk, v.x, acc[j][k].x);
-                            acc[j][k].y = fmaf(lk, v.y, acc[j][k].y);
+                            acc[j][k].x = fmaf(lf[i][k], v.x, acc[j][k].x);
+                            acc[j][k].y = fmaf(lf[i][k], v.y, acc[j][k].y);
                         }
                     }
                 }
-            }
-            const double inv4pi = 1.0 / TD_FOUR_PI;
+                // lane sums over the warp in FP32, chunk sums into the FP64 table
 #pragma unroll
-            for (int j = 0; j < FC; ++j) {
-                c64 outv[NV];
-                // the lane partial sums are FP32: reduce them in FP32 (no FP64 shuffles)
+                for (int j = 0; j < FC; ++j) {
 #pragma unroll
-                for (int k = 0; k < NV; ++k)
-                    outv[k] = {(double)warp_sum(acc[j][k].x) * inv4pi, (double)warp_sum(acc[j][k].y) * inv4pi};
-                if (lane == 0 && f0 + j < nf) {
-                    c64 *o = table + ((int64_t)p * nf + f0 + j) * 3;
-                    const c64 z = {0.0, 0.0};
-                    o[0] = o[1] = o[2] = z;
-                    if (!TD_P1_TRIAL(OP))
-                        o[0] = zero ? z : outv[0];
-                    else
-                        for (int k = 0; k < NV; ++k) o[G.loc[k]] = zero ? z : outv[k];
+                    for (int k = 0; k < NV; ++k) {
+                        const float sx = warp_sum(acc[j][k].x), sy = warp_sum(acc[j][k].y);
+                        if (lane == 0 && f0 + j < nf) {
+                            c64 &t = o[(int64_t)(f0 + j) * 3 + (TD_P1_TRIAL(OP) ? G.loc[k] : 0)];
+                            t.x += (double)sx * inv4pi;
+                            t.y += (double)sy * inv4pi;
+                        }
+                    }
                 }
             }
         }
@@ -438,8 +448,8 @@ int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const
 // variant (0 = default): touching-pair table (single layer / double layer /
 // adjoint double layer: one value per pair and frequency like the single
 // layer) and near-field tensor.
-constexpr int kSingFcSlp[3] = {36, 12, 24};
-constexpr int kSingFcDlp[3] = {12, 6, 8};
+constexpr int kSingFcSlp[3] = {8, 4, 16};
+constexpr int kSingFcDlp[3] = {4, 2, 8};
 constexpr int kNearFc[3] = {8, 4, 16};
 int td_sing_fc(int op, int variant) { return op == TD_DLP ? kSingFcDlp[variant % 3] : kSingFcSlp[variant % 3]; }
 int td_near_fc(int variant) { return kNearFc[variant % 3]; }
@@ -452,17 +462,17 @@ int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, co
     if (prec == TDBEM_MIXED) {
         const int v = variant % 3;
         if (op == TD_SLP) {
-            if (v == 1) k_sing_table_mixed<TD_SLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else if (v == 2) k_sing_table_mixed<TD_SLP, 24><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else k_sing_table_mixed<TD_SLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            if (v == 1) k_sing_table_mixed<TD_SLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else if (v == 2) k_sing_table_mixed<TD_SLP, 16><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_SLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         } else if (op == TD_DLP) {
-            if (v == 1) k_sing_table_mixed<TD_DLP, 6><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            if (v == 1) k_sing_table_mixed<TD_DLP, 2><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else if (v == 2) k_sing_table_mixed<TD_DLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else k_sing_table_mixed<TD_DLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_DLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         } else {
-            if (v == 1) k_sing_table_mixed<TD_ADLP, 12><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else if (v == 2) k_sing_table_mixed<TD_ADLP, 24><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else k_sing_table_mixed<TD_ADLP, 36><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            if (v == 1) k_sing_table_mixed<TD_ADLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else if (v == 2) k_sing_table_mixed<TD_ADLP, 16><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_ADLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         }
         return (int)cudaGetLastError();
     }
