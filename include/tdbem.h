@@ -301,7 +301,7 @@ int tdbem_tensor_destroy(tdbem_tensor_t t);
  *   - far phase: launch shape threads per CTA x resident CTAs per SM
  *     (64/128/256 threads, 2..16 CTAs per SM);
  *   - mixed form only: frequencies per pass of the touching-pair table
- *     (register tiles of 8/4/16 frequencies for the single layer and its adjoint, 4/2/8
+ *     (register tiles of 4/8/16 frequencies for the single layer and its adjoint, 2/4/8
  *     for the double layer) and of the near-field tensor kernel (8/4/16),
  *     each timed on its own phase.
  * chosen (nullable, host int32 [4]) receives {far threads per CTA, far CTAs

@@ -448,8 +448,8 @@ int td_launch_entries(cudaStream_t st, const MeshDev &m, int op, int prec, const
 // variant (0 = default): touching-pair table (single layer / double layer /
 // adjoint double layer: one value per pair and frequency like the single
 // layer) and near-field tensor.
-constexpr int kSingFcSlp[3] = {8, 4, 16};
-constexpr int kSingFcDlp[3] = {4, 2, 8};
+constexpr int kSingFcSlp[3] = {4, 8, 16};
+constexpr int kSingFcDlp[3] = {2, 4, 8};
 constexpr int kNearFc[3] = {8, 4, 16};
 int td_sing_fc(int op, int variant) { return op == TD_DLP ? kSingFcDlp[variant % 3] : kSingFcSlp[variant % 3]; }
 int td_near_fc(int variant) { return kNearFc[variant % 3]; }
@@ -462,17 +462,17 @@ int td_launch_sing_table(cudaStream_t st, const MeshDev &m, int op, int prec, co
     if (prec == TDBEM_MIXED) {
         const int v = variant % 3;
         if (op == TD_SLP) {
-            if (v == 1) k_sing_table_mixed<TD_SLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            if (v == 1) k_sing_table_mixed<TD_SLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else if (v == 2) k_sing_table_mixed<TD_SLP, 16><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else k_sing_table_mixed<TD_SLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_SLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         } else if (op == TD_DLP) {
-            if (v == 1) k_sing_table_mixed<TD_DLP, 2><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            if (v == 1) k_sing_table_mixed<TD_DLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else if (v == 2) k_sing_table_mixed<TD_DLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else k_sing_table_mixed<TD_DLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_DLP, 2><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         } else {
-            if (v == 1) k_sing_table_mixed<TD_ADLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            if (v == 1) k_sing_table_mixed<TD_ADLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
             else if (v == 2) k_sing_table_mixed<TD_ADLP, 16><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
-            else k_sing_table_mixed<TD_ADLP, 8><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
+            else k_sing_table_mixed<TD_ADLP, 4><<<grid, 128, 0, st>>>(m, pti, ptj, npairs, sig, nf, table);
         }
         return (int)cudaGetLastError();
     }
