@@ -168,7 +168,7 @@ def test_compress_small_vs_dense(td, ctx, orc, sphere2, prec, op, dense_faces):
 
 
 @pytest.mark.parametrize("op,prec", [("SLP", "MIXED"), ("SLP", "FP64"), ("DLP", "MIXED"), ("ADLP", "MIXED")])
-def test_config2_sampled_apply(td, ctx, orc, op, prec):
+def test_sphere5120_sampled_apply(td, ctx, orc, op, prec):
     """5120-triangle sphere, SLP (P0 x P0), DLP (P0 x P1) and K' (P0 x P0), BDF2 N = 64,
     dt = 0.05, leaf 32, eta 2, eps 1e-4: apply on sampled rows vs the dense
     FP64 oracle apply."""
@@ -182,7 +182,7 @@ def test_config2_sampled_apply(td, ctx, orc, op, prec):
     eps = 1e-4
     X = td.compress(gm, getattr(td, op), f, tree, eps=eps, eps_aca=1e-6, prec=getattr(td, prec))
     st = X.stats()
-    print("config2 %s %s stats: %s" % (op, prec, st))
+    print("sphere5120 %s %s stats: %s" % (op, prec, st))
     assert st["stored_complex"] < 0.5 * st["dense_complex"]
     nrhs = 2
     W = random_weights(64, ncols, nrhs, seed=1)
@@ -192,7 +192,7 @@ def test_config2_sampled_apply(td, ctx, orc, op, prec):
     rows = np.sort(rng.choice(len(T), 12, replace=False)).astype(np.int32)
     yd = om.dense_apply_rows(getattr(orc, op), f.s, rows, W, ng=5)
     err = np.linalg.norm(y[rows] - yd) / np.linalg.norm(yd)
-    print("config2 %s %s sampled apply error %.2e" % (op, prec, err))
+    print("sphere5120 %s %s sampled apply error %.2e" % (op, prec, err))
     assert err < 3 * eps, err
 
 
