@@ -273,7 +273,7 @@ int tdbem_entries_noalloc(tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f
 /* ---- compression (Sec. 4, Algorithm 1 per block, eq. norm) ------------------- */
 /* 3D-ACA of the operator tensor over the Nu unique frequencies of f on every
  * block of `tree` (which must have been built with test P0 and trial P0 for
- * SLP, P1 for DLP).  Near-field blocks: dense residual faces; far-field
+ * SLP and ADLP, P1 for DLP).  Near-field blocks: dense residual faces; far-field
  * blocks: residual faces compressed by ACA with partial pivoting to eps_aca,
  * rebuilt to find the pivot (Sec. 4).  The result stays in device memory. */
 int tdbem_compress(tdbem_ctx_t ctx, tdbem_mesh_t mesh, const tdbem_op *op, tdbem_freqs_t f,
