@@ -205,19 +205,26 @@ def test_magnitude_sums_equal_modulus_for_positive_terms(orc, sphere1):
         assert np.max(np.abs(g - np.abs(a)) / np.abs(a)) < 1e-13
 
 
-@pytest.mark.parametrize("op", ["SLP", "DLP"])
+@pytest.mark.parametrize("op", ["SLP", "DLP", "ADLP"])
 def test_magnitude_sums_bound_the_entries(orc, sphere1, op):
     """Triangle inequality: the magnitude sum bounds |entry| at complex s,
-    and for the double layer the bound is strict on curved neighbours."""
+    and for the double layer and its adjoint the bound is strict on curved
+    neighbours; a flat panel with itself contributes nothing to K' (entry
+    and magnitude sum both zero)."""
     V, T, m = sphere1
     rows = np.array([0, 5, 11], dtype=np.int32)
-    cols = np.arange(len(T) if op == "SLP" else len(V), dtype=np.int32)
+    cols = np.arange(len(V) if op == "DLP" else len(T), dtype=np.int32)
     s = [1.5 + 7.0j, 0.3 - 2.0j]
     a = m.entries(getattr(orc, op), rows, cols, s, c=1.0, ng=6)
     g = m.entries_mag(getattr(orc, op), rows, cols, s, c=1.0, ng=6)
     assert np.all(g >= np.abs(a) * (1 - 1e-12))
+    if op == "ADLP":
+        own = np.zeros(g.shape, dtype=bool)
+        own[:, np.arange(len(rows)), rows] = True
+        assert np.all(g[own] == 0) and np.all(a[own] == 0)
+        g, a = g[~own], a[~own]
     assert np.all(g > 0)
-    if op == "DLP":
+    if op != "SLP":
         assert np.median(g / np.maximum(np.abs(a), 1e-300)) > 1.5
 
 
